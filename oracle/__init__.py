@@ -1,0 +1,23 @@
+"""CPU oracle for the ESP electrostatics solve -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, FP64 NumPy/SciPy code written from the paper (Methods section:
+Eqs. task, kernelsplitting, localpart, hS, spectralpart, spread...interp, pk,
+pswf, pswfparameters, cem, cemparameters, Deltadef; Table 2). Only the tests,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import it. The product path (the CUDA library and its Python binding) never
+imports, links or calls anything here, and nothing here imports the product.
+
+Modules
+  pswf    prolate spheroidal wave function psi_0^c and the splitting functions
+  ewald   classical Ewald summation (erfc split, explicit k-space sum)
+  images  brute-force spherical image sums for tiny systems
+  esp     plain CPU ESP: five-step spectral part, local part, self/background
+  params  the paper's parameter rules and Table 2
+  metrics relative RMS force error (Eq. Deltadef)
+
+Parity status: every function here is pinned by tests under ``tests/`` that
+do not use the CUDA path (``-m "not gpu"``), except the parameter *planner
+calibration* (how far n_f is raised above the paper's minimum), which the
+paper leaves open; it is "parity unpinned" and only measured force errors
+against classical Ewald pin it.
+"""
