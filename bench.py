@@ -1,0 +1,345 @@
+"""Benchmark: atoms/s of the ESP long-range electrostatics solve on one GB300.
+
+Workload (default): SPC/E-shaped water, 1e5 molecules = 3e5 atoms, L = 14.413
+nm (33.4 molecules/nm^3), r_c = 1.0 nm, tolerance 1e-4 relative RMS force
+error, FP32 production path with FP64 corrections and energy.
+
+One step = the whole hot path: ingest + bin sort (esp_set_positions), then
+spread, R2C FFT, fused scale + spectral energy, C2R FFT, gather, local part,
+corrections and energy (esp_compute). `value` times steps with inputs and
+outputs resident in device memory; `e2e` times the same calls with pinned host
+buffers (host->device positions, device->host energy, forces, potential).
+
+The inputs (3.6 MB) fit in L2, so L2 is flushed (a 512 MB write) between timed
+steps, outside the timed events.
+
+`--impl reference` times the FP64 CPU oracle instead (see --help).
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of the
+workload (the single-system solve has no data-parallel split without an
+exchange step), no collective on the data path; value = total atoms / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atoms/s long-range forces at 1e-4 err: batched+served vs plain; p50/p99 ms"
+UNIT = "atoms/s"
+WORKLOAD = dict(workload="spce_water_1e5_molecules", molecules=100_000, atoms=300_000,
+                density_per_nm3=33.4, r_c_nm=1.0, tolerance=1e-4, seed=2505)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--molecules", type=int, default=WORKLOAD["molecules"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline(phases: dict, info: dict, n_atoms: int, L: float, clocks, n_steps: int):
+    """Roofline of the dominant kernel (largest average duration).
+
+    Algorithmic work per launch:
+      near    FP32 ALU: pairs within r_c (N * 4/3 pi r_c^3 rho, full list) x
+              NEAR_FLOPS_PER_PAIR, against 152 SMs x 128 FP32 lanes x 2 flop x
+              the median SM clock seen during the run
+      spread  HBM: 16 B/atom (sorted atoms) + 4 B per grid point (grid write)
+      gather  HBM: 16 B/atom in + 16 B/atom out + 4 B per grid point
+      scale   HBM: 16 B per complex mode (read + write)
+    """
+    near_flops_per_pair = 90.0
+    rho = n_atoms / L ** 3
+    pairs = n_atoms * 4.0 / 3.0 * math.pi * info["r_c"] ** 3 * rho
+    n_f = info["n_f"]
+    grid = n_f ** 3
+    modes = n_f * n_f * (n_f // 2 + 1)
+    algo = {
+        "near": ("alu", pairs * near_flops_per_pair, "TFLOP/s"),
+        "spread": ("hbm", 16.0 * n_atoms + 4.0 * grid, "GB/s"),
+        "gather": ("hbm", 32.0 * n_atoms + 4.0 * grid, "GB/s"),
+        "scale": ("hbm", 16.0 * modes, "GB/s"),
+    }
+    kernel = max(algo, key=lambda k: phases.get(k, 0.0))
+    bound, work, unit = algo[kernel]
+    t = phases[kernel] * 1e-3
+    peaks, source = measured_peaks()
+    if bound == "alu":
+        mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1492.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        achieved = work / t / 1e12
+        peak_note = f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median SM clock in the run)"
+    else:
+        peak = peaks["hbm_gbs"]
+        achieved = work / t / 1e9
+        peak_note = f"{source} HBM copy bandwidth"
+    return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+            "algorithmic_per_launch": work, "avg_launch_ms": phases[kernel]}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2505_09727_gb300 import esp, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = inputs.spce_water(args.molecules, seed=WORKLOAD["seed"])
+    N, L = s.n, s.L
+    stream = torch.cuda.current_stream(dev)
+    h = esp.esp_plan(L, N, WORKLOAD["tolerance"], r_c=WORKLOAD["r_c_nm"], device=local,
+                     stream=stream.cuda_stream)
+    info = esp.esp_plan_info(h)
+    q = torch.tensor(s.q, device=dev)
+    x = torch.tensor(s.pos, device=dev)
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    f = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    esp.esp_set_charges(h, q)
+    esp.esp_set_timing(h, True)
+
+    def step():
+        esp.esp_set_positions(h, x)
+        esp.esp_compute(h, e, f, u)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phase_acc = {k: 0.0 for k in esp.PHASES}
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+        ph = esp.esp_phase_times(h)      # waits for this step; events are on the plan's streams
+        for k, v in ph.items():
+            phase_acc[k] += v
+    torch.cuda.synchronize(dev)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    clocks = sampler.stop()
+    esp.esp_set_timing(h, False)
+
+    # end to end through the C-ABI with pinned host buffers
+    xh = torch.tensor(s.pos).pin_memory()
+    fh = torch.zeros((N, 3), dtype=torch.float64).pin_memory()
+    uh = torch.zeros(N, dtype=torch.float64).pin_memory()
+    eh = np.zeros(1)
+    for _ in range(3):
+        esp.esp_set_positions(h, xh)
+        esp.esp_compute(h, eh, fh, uh, esp.ESP_HOST)
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(5, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        esp.esp_set_positions(h, xh)
+        esp.esp_compute(h, eh, fh, uh, esp.ESP_HOST)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    esp.esp_destroy(h)
+
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+    phases = {k: v / args.steps for k, v in phase_acc.items()}
+    return dict(N=N, L=L, info=info, total_ms=total_ms, step_ms=step_ms, e2e_s=e2e_s,
+                e2e_steps=e2e_steps, phases=phases, clocks=clocks, energy=float(e.cpu()[0]))
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_baseline(molecules: int, budget_atoms: int = 1500):
+    """Time the FP64 CPU oracle on a bounded sample of the workload.
+
+    Per step the oracle spreads all N atoms and runs the FFT pair (timed in
+    full); interpolation and the local pair sum are per atom (timed on
+    `budget_atoms` sampled atoms and scaled to N).
+    """
+    from oracle import esp as oesp
+    from oracle import params as oparams
+    from oracle import pswf
+    from paper_2505_09727_gb300 import inputs
+
+    s = inputs.spce_water(molecules, seed=WORKLOAD["seed"])
+    eps, r_c = WORKLOAD["tolerance"], WORKLOAD["r_c_nm"]
+    pl = oparams.plan(eps, s.L, r_c)
+    p = oesp.ESPParams(eps, r_c, pl["P"], pl["n_f"], pl["c"], pl["c1"])
+    split = p.split()
+    window = pswf.PSWFWindow(p.c1, p.P)
+    idx = np.sort(np.random.default_rng(0).choice(s.n, size=min(budget_atoms, s.n), replace=False))
+    t0 = time.perf_counter()
+    oesp.far_field(s.pos, s.q, s.L, p.n_f, r_c, split, window, idx[:0])
+    t_fixed = time.perf_counter() - t0                 # spread of all atoms + FFT pair
+    t0 = time.perf_counter()
+    oesp.far_field(s.pos, s.q, s.L, p.n_f, r_c, split, window, idx)
+    t_gather = max(time.perf_counter() - t0 - t_fixed, 0.0)
+    t0 = time.perf_counter()
+    oesp.near_field(s.pos, s.q, s.L, r_c, split, idx)
+    t_near = time.perf_counter() - t0
+    t_step = t_fixed + (t_gather + t_near) / len(idx) * s.n
+    return {"value": s.n / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, same {s.n}-atom water box and parameters: spread of all "
+                       f"atoms + FFT pair timed in full ({t_fixed:.2f} s); interpolation and local part "
+                       f"timed on {len(idx)} sampled atoms ({t_gather + t_near:.2f} s) and scaled to N; "
+                       f"single-threaded"),
+            "seconds_per_step": t_step}
+
+
+# --------------------------------------------------------------------- main
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        vals = []
+        base = None
+        for _ in range(max(1, min(args.steps, 3))):
+            base = cpu_baseline(args.molecules)
+            vals.append(base["value"])
+        value = statistics.median(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+                "steps": len(vals), "warmup": args.warmup, "ms_per_step": base["seconds_per_step"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": dict(WORKLOAD, molecules=args.molecules),
+                "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_gpu(args, world, rank, local)
+    N = r["N"]
+    atoms_total = N * args.steps * world
+    value = atoms_total / (r["total_ms"] * 1e-3)
+    e2e_value = N * r["e2e_steps"] * world / r["e2e_s"]
+    kernels_per_step = 9       # ingest, scan, scatter, near, spread, scale, gather, finalize, energy
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, molecules=args.molecules, atoms=N, L_nm=r["L"], n_f=r["info"]["n_f"],
+                       P=r["info"]["P"], c=r["info"]["c"], c1=r["info"]["c1"], l2="flushed_between_steps",
+                       parallelism=f"replicas{world}"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 3 * 8,
+                "d2h_bytes_per_step": N * 3 * 8 + N * 8 + 8},
+        "gpu_launches": kernels_per_step * args.steps,
+        "phases_ms": {k: round(v, 5) for k, v in r["phases"].items()},
+        "step_ms_p50": statistics.median(r["step_ms"]),
+        "step_ms_p99": float(np.percentile(r["step_ms"], 99)),
+        "clocks": r["clocks"],
+    }
+    line["roofline"] = roofline(r["phases"], r["info"], N, r["L"], r["clocks"], args.steps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(args.molecules)
+        line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

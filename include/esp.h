@@ -1,0 +1,178 @@
+/*
+ * esp.h -- C-ABI of the GB300 ESP electrostatics library (libesp_gb300.so).
+ *
+ * ESP ("Ewald summation with prolates") computes, for N point charges q_i at
+ * r_i in a cubic periodic box of edge L, the quantities of the paper's
+ * problem statement (Methods, Eq. task):
+ *     u_i = sum'_{j,n} q_j / (4 pi |r_i - r_j - n L|)   (k = 0 mode dropped),
+ *     E   = 1/2 sum_i q_i u_i,          F_i = -grad_{r_i} E,
+ * through the split 1/(4 pi r) = S(r) + L(r) of Eq. kernelsplitting with the
+ * prolate spheroidal wave function (PSWF) of Eq. pswf as splitting kernel:
+ *   - the local part (Eq. localpart) is a cell-list pair sum within r_c;
+ *   - the spectral part is the five-step method of Eqs. spread ... interp:
+ *     spread on an n_f^3 grid with a P-point-per-axis PSWF stencil, R2C FFT,
+ *     scaling by the influence function p_k of Eq. pk, C2R FFT, interpolation
+ *     of potentials and (analytic-derivative) forces;
+ *   - the self term q_i chi(0)/(4 pi r_c) is removed and, for non-neutral
+ *     systems, a neutralising background is added.
+ * Parameter choice follows Eq. pswfparameters, Table 2 and the aliasing
+ * estimate Eq. errorformula. A Gaussian split (Eq. cem) runs on the same
+ * machinery for comparison.
+ *
+ * Units: the kernel is 1/(4 pi r) (the paper's nondimensionalised form);
+ * `prefactor` rescales every output (e.g. 138.935458 kJ mol^-1 nm e^-2 for
+ * GROMACS units gives prefactor = 4 pi * 138.935458).
+ *
+ * Conventions
+ *  - Positions: N x 3 array-of-structs (x0 y0 z0 x1 ...), any real values;
+ *    they are wrapped into [0, L). Forces: N x 3, same layout. Potential: N.
+ *    Outputs are in the caller's atom order.
+ *  - `where` = ESP_HOST: pointers are host memory; the call copies, computes
+ *    and returns after the results are in the caller's buffers.
+ *    `where` = ESP_DEVICE: pointers are device memory of the plan's device;
+ *    the call enqueues the work on the plan's stream and returns without
+ *    waiting (use esp_synchronize). `energy` is then a device double.
+ *  - The caller owns every buffer it passes; the library copies inputs and
+ *    never keeps a caller pointer after a call returns.
+ *  - Errors: every call returns an esp_status; esp_last_error() gives a
+ *    thread-local message for the last failing call on this thread. No call
+ *    aborts the process. Device-side faults detected by the kernels (a
+ *    non-finite coordinate, an out-of-range tile index) set a flag that is
+ *    reported by the next synchronising call as ESP_ERR_NONFINITE or
+ *    ESP_ERR_INTERNAL.
+ *  - Thread safety: a plan is used by one thread at a time. Distinct plans
+ *    may be used concurrently from distinct threads.
+ */
+#ifndef ESP_GB300_H
+#define ESP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct esp_plan_s* esp_plan_t;
+
+typedef enum {
+  ESP_OK = 0,
+  ESP_ERR_INVALID_ARG = 1,     /* bad pointer, size, tolerance or option     */
+  ESP_ERR_CUTOFF_TOO_LARGE = 2,/* r_c >= L/2 (minimum image would fail)       */
+  ESP_ERR_NOT_NEUTRAL = 3,     /* sum q != 0 and allow_background == 0        */
+  ESP_ERR_NONFINITE = 4,       /* a position or charge is NaN or infinite     */
+  ESP_ERR_OOM = 5,             /* device allocation failed                    */
+  ESP_ERR_CUDA = 6,            /* CUDA runtime error                          */
+  ESP_ERR_CUFFT = 7,           /* cuFFT error                                 */
+  ESP_ERR_TIMEOUT = 8,         /* a device wait exceeded the plan deadline    */
+  ESP_ERR_BUSY = 9,            /* admission refused (memory budget)           */
+  ESP_ERR_UNSUPPORTED = 10,    /* a size beyond a compiled limit (e.g. P>16) */
+  ESP_ERR_INTERNAL = 11,       /* a kernel bounds check failed                */
+  ESP_ERR_NOT_READY = 12       /* positions or charges not set yet           */
+} esp_status;
+
+enum { ESP_KERNEL_PSWF = 0, ESP_KERNEL_GAUSS = 1 };
+enum { ESP_FP32 = 0, ESP_FP64 = 1 };
+enum { ESP_HOST = 0, ESP_DEVICE = 1 };
+
+/* Cubic box: L[0] = L[1] = L[2] > 0 (non-cubic boxes are rejected). */
+typedef struct { double L[3]; } esp_box;
+
+/* Options. Zero-initialise (or call esp_plan_opts_init) and set what you
+ * need; a zero field means "the planner chooses". */
+typedef struct {
+  double r_c;          /* cutoff of the local part; 0 = cost model           */
+  int P;               /* stencil points per axis; 0 = Table 2 (P_esp)       */
+  int n_f;             /* grid points per axis; 0 = Eq. pswfparameters rule
+                          raised until the aliasing estimate is <= eps/2     */
+  double c;            /* PSWF split shape; 0 = solve psi_0^c(1) = tolerance */
+  double c1;           /* PSWF SI-kernel shape; 0 = minimise the aliasing
+                          estimate over c1/c in [1.1, 1.4]                   */
+  double alpha;        /* Gaussian split shape (kernel = GAUSS); 0 = ln(1/eps) */
+  int kernel;          /* ESP_KERNEL_PSWF (default) or ESP_KERNEL_GAUSS      */
+  int precision;       /* ESP_FP32 (production) or ESP_FP64 (plain mode)     */
+  double prefactor;    /* scales u, E, F; 0 = 1                              */
+  int device;          /* CUDA device ordinal                                */
+  void* stream;        /* cudaStream_t to run on; NULL = plan-owned stream   */
+  int allow_background;/* 1 = neutralising background for sum q != 0        */
+  int brick_cells;     /* tuning: cells per spread/gather brick edge; 0 auto */
+  double timeout_ms;   /* deadline of host waits; 0 = 60000                  */
+  int reserved[8];
+} esp_plan_opts;
+
+/* Parameters a plan chose (esp_plan_info). */
+typedef struct {
+  double L, r_c, h, c, c1, alpha, prefactor;
+  double alias_estimate;   /* relative E_A of Eq. errorformula at (c1, n_f)  */
+  double si_fit_error;     /* max |SI-kernel polynomial - psi| (FP64)        */
+  double near_fit_error;   /* max error of the local-part polynomials        */
+  int64_t N;
+  int P, n_f, kernel, precision;
+  int n_cells;             /* cell-list cells per axis (edge >= r_c/2)       */
+  int brick_cells;         /* cells per brick edge                           */
+  int tile;                /* shared-memory tile edge in grid points         */
+  int si_degree, near_degree;
+  size_t device_bytes;     /* device memory held by the plan                 */
+} esp_plan_params;
+
+/* Fill opts with defaults (all planner choices, FP32, PSWF, device 0). */
+void esp_plan_opts_init(esp_plan_opts* opts);
+
+/* Create a plan for N charges in `box` at relative RMS force tolerance
+ * `tolerance` (Eq. Deltadef; 1e-15 < tolerance < 0.1). Allocates all device
+ * memory and cuFFT plans. opts may be NULL. On success *out owns everything. */
+esp_status esp_plan(const esp_box* box, int64_t N, double tolerance,
+                    const esp_plan_opts* opts, esp_plan_t* out);
+
+esp_status esp_plan_info(esp_plan_t plan, esp_plan_params* out);
+
+/* Run the planner only (host FP64, no device allocation, no GPU needed) and
+ * report the parameters esp_plan would choose; device_bytes is an estimate
+ * that excludes the cuFFT work areas. */
+esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance,
+                          const esp_plan_opts* opts, esp_plan_params* out);
+
+/* Charges q[N] (double or float). Must be called before the first compute
+ * and whenever charges change. */
+esp_status esp_set_charges(esp_plan_t plan, const double* q, int where);
+esp_status esp_set_charges_f32(esp_plan_t plan, const float* q, int where);
+
+/* Positions xyz[N*3]: ingest (wrap, fixed-point conversion, finite check)
+ * and bin sort (counting sort by cell) -- steps A0-A1 of the pipeline. */
+esp_status esp_set_positions(esp_plan_t plan, const double* xyz, int where);
+esp_status esp_set_positions_f32(esp_plan_t plan, const float* xyz, int where);
+
+/* Spread, R2C FFT, fused influence scale + spectral energy, C2R FFT, gather,
+ * local part, corrections and compensated FP64 energy. Any of energy,
+ * forces, potential may be NULL. */
+esp_status esp_compute(esp_plan_t plan, double* energy, double* forces,
+                       double* potential, int where);
+esp_status esp_compute_f32(esp_plan_t plan, double* energy, float* forces,
+                           float* potential, int where);
+
+/* Wait (bounded by the plan deadline) for the plan's queued work; reports a
+ * device-side error flag raised since the last call. */
+esp_status esp_synchronize(esp_plan_t plan);
+
+/* Per-phase device times (ms) of the last compute when timing is enabled:
+ * [0] ingest+sort, [1] spread, [2] r2c, [3] scale, [4] c2r, [5] gather,
+ * [6] near, [7] finalize, [8] whole compute. Returns ESP_ERR_NOT_READY when
+ * timing is off. */
+esp_status esp_set_timing(esp_plan_t plan, int enable);
+esp_status esp_phase_times(esp_plan_t plan, float* ms, int n);
+
+/* Spectral energy 1/2 sum_k p_k |bh_k|^2 of the last compute (host double). */
+esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* e_gather);
+
+esp_status esp_destroy(esp_plan_t plan);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* esp_last_error(void);
+
+/* Library build identification (compile-time arch list and version). */
+const char* esp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESP_GB300_H */

@@ -1,0 +1,132 @@
+// Device code of the ESP solve (sm_103a). Every kernel works on a pool of one
+// or more independent systems described by SysDesc records, so the same code
+// serves a single system and a batch of systems.
+//
+// Pipeline (paper, Methods; one pass per esp_compute):
+//   ingest   wrap positions into the box, fixed-point (FP32 mode) or wrapped
+//            FP64 coordinates, cell key and rank within the cell
+//   scan     exclusive scan of the per-cell counts (cell list offsets)
+//   scatter  counting-sort scatter: sorted atoms (coords + charge), permutation
+//   spread   Eq. spread: b_l = sum_j q_j phi~(r_j - h l), one CTA per brick of
+//            cells accumulating into a shared-memory tile with a P-1 halo,
+//            flushed to the periodic grid with global atomics
+//   R2C FFT  cuFFT (library)
+//   scale    Eq. pk: ch_k = p_k bh_k, p_k = G[|k|^2] w[kx] w[ky] w[kz], fused
+//            with the spectral energy 1/2 sum_k p_k |bh_k|^2
+//   C2R FFT  cuFFT (library)
+//   gather   Eq. interp: u~_i and grad u~_i (analytic derivatives of the
+//            piecewise polynomials), same tile structure, read-only
+//   near     Eq. localpart: cell-list pair sum within r_c, L(r) and -L'(r)
+//            from polynomials in x = r / r_c
+//   finalize self term, background, per-atom totals in the caller's order,
+//            energy partials
+//   reduce   compensated FP64 energy per system
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace espk {
+
+constexpr int kMaxP = 16;
+constexpr int kMinP = 4;
+constexpr int kChunk = 256;   // atoms per chunk = threads of a per-atom block
+
+// Polynomial degrees (coefficient counts) per precision.
+template <typename real> struct Deg;
+template <> struct Deg<float> { static constexpr int si = 10; static constexpr int nr = 16; };
+template <> struct Deg<double> { static constexpr int si = 18; static constexpr int nr = 28; };
+
+// SI kernel: P pieces, piece a gives the weight of grid point l0 + a as a
+// polynomial in y = 2 delta - 1, delta = t - l0 - (P/2 - 1) in (0, 1].
+template <typename real> struct SICoef { real c[kMaxP][Deg<real>::si]; };
+// Local part: 1 - g(x) and chi(x) as polynomials in y = 2x - 1, x = r / r_c.
+template <typename real> struct NearCoef { real e[Deg<real>::nr]; real chi[Deg<real>::nr]; };
+
+// Per-system geometry and constants (same record on host and device).
+struct SysDesc {
+  int n_f;        // grid points per axis
+  int n_c;        // cell-list cells per axis (cell edge >= r_c / 2)
+  int bc;         // cells per brick edge (n_c % bc == 0)
+  int nb;         // bricks per axis (n_c / bc)
+  int T;          // shared tile edge in grid points
+  int n_atoms;
+  int gsize;      // entries of the radial table G (3 (n_f/2)^2 + 1)
+  int pad0;
+  long long atom0;   // first atom of the system in the pooled atom arrays
+  long long cell0;   // first entry of the system in the pooled count/start arrays
+  long long grid0;   // first element of the system's real grid
+  long long spec0;   // first element of the system's half spectrum
+  long long tab0;    // first element of the system's G table (w follows G)
+  double L, inv_L, h, inv_h;
+  double r_c, rc2, inv_rc;
+  double fix_scale;  // L / 2^32
+  double self_coef;  // chi(0) / (4 pi r_c)
+  double bg_shift;   // -(Q/V) (r_c^2/2) int_0^1 x^2 chi
+  double prefactor;
+};
+
+// ------------------------------------------------------------ coordinates
+// FP32 mode stores coordinates as 32-bit fixed-point fractions of L: the grid
+// index of the stencil origin is then exact integer arithmetic and pair
+// differences are exact integer differences (minimum image = int32 wrap).
+__host__ __device__ inline void stencil_fixed(uint32_t u, int n_f, int P, int& l0, int64_t& r) {
+  // t = u n_f / 2^32 (32.32 fixed point); l0 = ceil(t - P/2);
+  // r = (t - l0 - P/2 + 1) * 2^32 in (0, 2^32]
+  int64_t v = (int64_t)((uint64_t)u * (uint64_t)n_f) - ((int64_t)P << 31);
+  int64_t l = (v + 0xFFFFFFFFLL) >> 32;   // arithmetic shift: ceil(v / 2^32)
+  l0 = (int)l;
+  r = v - (l << 32) + (1LL << 32);
+}
+
+__host__ __device__ inline uint32_t cell_min_fixed(int c, int n_c) {
+  // smallest u with (u n_c) >> 32 == c
+  return (uint32_t)((((uint64_t)c << 32) + (uint64_t)n_c - 1) / (uint64_t)n_c);
+}
+
+__host__ __device__ inline int tile_origin_fixed(int cb, int n_c, int n_f, int P) {
+  int l0; int64_t r;
+  stencil_fixed(cell_min_fixed(cb, n_c), n_f, P, l0, r);
+  return l0;
+}
+
+__host__ __device__ inline int tile_last_fixed(int cb_end, int n_c, int n_f, int P) {
+  // l0 of the largest u below cell cb_end
+  uint64_t umax = (cb_end >= n_c) ? 0xFFFFFFFFull : (uint64_t)cell_min_fixed(cb_end, n_c) - 1;
+  int l0; int64_t r;
+  stencil_fixed((uint32_t)umax, n_f, P, l0, r);
+  return l0;
+}
+
+// FP64 mode keeps wrapped FP64 coordinates.
+__host__ __device__ inline int stencil_origin_f64(double x, double inv_h, int P, double& delta) {
+  double t = x * inv_h;
+  double l0 = ceil(t - 0.5 * P);
+  delta = t - l0 - 0.5 * P + 1.0;
+  return (int)l0;
+}
+
+__host__ __device__ inline int wrap_index(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// --------------------------------------------------------------- reductions
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ inline double block_sum(double v, double* smem32) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) smem32[wid] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? smem32[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+
+}  // namespace espk

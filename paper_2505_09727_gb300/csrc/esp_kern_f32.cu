@@ -1,0 +1,29 @@
+// FP32 production instantiations of the ESP kernels (P = 4 ... 12), plus the
+// precision-independent scan and energy launchers.
+#define ESP_REAL float
+#define ESP_P_MIN 4
+#define ESP_P_MAX 12
+#define ESP_P_CASES(FN, ...)                                              \
+  ESP_P_CASE(4, FN, __VA_ARGS__) ESP_P_CASE(5, FN, __VA_ARGS__)           \
+  ESP_P_CASE(6, FN, __VA_ARGS__) ESP_P_CASE(7, FN, __VA_ARGS__)           \
+  ESP_P_CASE(8, FN, __VA_ARGS__) ESP_P_CASE(9, FN, __VA_ARGS__)           \
+  ESP_P_CASE(10, FN, __VA_ARGS__) ESP_P_CASE(11, FN, __VA_ARGS__)         \
+  ESP_P_CASE(12, FN, __VA_ARGS__)
+#include "esp_kern_impl.cuh"
+
+namespace espk {
+
+cudaError_t launch_scan(const uint32_t* count, uint32_t* start, long long n, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(count, start, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const SysDesc* sys, int nsys, const double* fourier, int n_fourier_blocks,
+                          const double* partials, int n_chunks, const int* chunk_first,
+                          const double* consts, double* out, double* user_energy, cudaStream_t st) {
+  k_energy<<<nsys, 256, 0, st>>>(sys, fourier, n_fourier_blocks, partials, n_chunks, chunk_first,
+                                 consts, out, user_energy);
+  return cudaGetLastError();
+}
+
+}  // namespace espk

@@ -1,0 +1,13 @@
+// FP64 plain-mode instantiations of the ESP kernels (P = 4 ... 16).
+#define ESP_REAL double
+#define ESP_P_MIN 4
+#define ESP_P_MAX 16
+#define ESP_P_CASES(FN, ...)                                              \
+  ESP_P_CASE(4, FN, __VA_ARGS__) ESP_P_CASE(5, FN, __VA_ARGS__)           \
+  ESP_P_CASE(6, FN, __VA_ARGS__) ESP_P_CASE(7, FN, __VA_ARGS__)           \
+  ESP_P_CASE(8, FN, __VA_ARGS__) ESP_P_CASE(9, FN, __VA_ARGS__)           \
+  ESP_P_CASE(10, FN, __VA_ARGS__) ESP_P_CASE(11, FN, __VA_ARGS__)         \
+  ESP_P_CASE(12, FN, __VA_ARGS__) ESP_P_CASE(13, FN, __VA_ARGS__)         \
+  ESP_P_CASE(14, FN, __VA_ARGS__) ESP_P_CASE(15, FN, __VA_ARGS__)         \
+  ESP_P_CASE(16, FN, __VA_ARGS__)
+#include "esp_kern_impl.cuh"

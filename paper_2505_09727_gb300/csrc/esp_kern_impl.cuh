@@ -1,0 +1,165 @@
+// Launcher bodies shared by the FP32 and FP64 instantiation units. Each unit
+// defines ESP_REAL and the P range it compiles, then includes this file.
+#pragma once
+#include "esp_kernels.cuh"
+#include "esp_launch.h"
+
+namespace espk {
+
+namespace detail {
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename real, typename In>
+__global__ void __launch_bounds__(256) k_convert(const In* __restrict__ src, real* __restrict__ dst,
+                                                 long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (real)src[i];
+}
+
+}  // namespace detail
+
+template <>
+cudaError_t Launch<ESP_REAL>::ingest(const SysDesc* sys, const int2* chunks, int n_chunks,
+                                     const void* xyz, bool xyz_is_double, void* coord,
+                                     uint32_t* key, uint32_t* rank, uint32_t* count, int* err,
+                                     cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  if (n_chunks == 0) return cudaSuccess;
+  if (xyz_is_double)
+    k_ingest<ESP_REAL, double><<<n_chunks, kChunk, 0, st>>>(
+        sys, chunks, (const double*)xyz, (A*)coord, key, rank, count, err);
+  else
+    k_ingest<ESP_REAL, float><<<n_chunks, kChunk, 0, st>>>(
+        sys, chunks, (const float*)xyz, (A*)coord, key, rank, count, err);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t Launch<ESP_REAL>::scatter(const SysDesc* sys, const int2* chunks, int n_chunks,
+                                      const void* coord, const uint32_t* key, const uint32_t* rank,
+                                      const uint32_t* start, const ESP_REAL* q, void* atoms,
+                                      uint32_t* perm, cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  if (n_chunks == 0) return cudaSuccess;
+  k_scatter<ESP_REAL, ESP_REAL><<<n_chunks, kChunk, 0, st>>>(sys, chunks, (const A*)coord, key, rank,
+                                                             start, q, (A*)atoms, perm);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t spread_p(const SysDesc* sys, const int2* work, int n_work, size_t smem,
+                            const void* atoms, const uint32_t* start, ESP_REAL* grids,
+                            const SICoef<ESP_REAL>& si, int* err, cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  auto kern = k_spread<ESP_REAL, P>;
+  cudaError_t e = detail::allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_work, 256, smem, st>>>(sys, work, (const A*)atoms, start, grids, si, err);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t gather_p(const SysDesc* sys, const int2* work, int n_work, size_t smem,
+                            const void* atoms, const uint32_t* start, const ESP_REAL* grids,
+                            void* far, const SICoef<ESP_REAL>& si, int* err, cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  using R = typename Types<ESP_REAL>::res;
+  auto kern = k_gather<ESP_REAL, P>;
+  cudaError_t e = detail::allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_work, 256, smem, st>>>(sys, work, (const A*)atoms, start, grids, (R*)far, si, err);
+  return cudaGetLastError();
+}
+
+#define ESP_P_CASE(PP, FN, ...) \
+  case PP: return FN<PP>(__VA_ARGS__);
+
+template <>
+cudaError_t Launch<ESP_REAL>::spread(int P, const SysDesc* sys, const int2* work, int n_work,
+                                     size_t smem, const void* atoms, const uint32_t* start,
+                                     ESP_REAL* grids, const SICoef<ESP_REAL>& si, int* err,
+                                     cudaStream_t st) {
+  if (n_work == 0) return cudaSuccess;
+  switch (P) {
+    ESP_P_CASES(spread_p, sys, work, n_work, smem, atoms, start, grids, si, err, st)
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t Launch<ESP_REAL>::gather(int P, const SysDesc* sys, const int2* work, int n_work,
+                                     size_t smem, const void* atoms, const uint32_t* start,
+                                     const ESP_REAL* grids, void* far, const SICoef<ESP_REAL>& si,
+                                     int* err, cudaStream_t st) {
+  if (n_work == 0) return cudaSuccess;
+  switch (P) {
+    ESP_P_CASES(gather_p, sys, work, n_work, smem, atoms, start, grids, far, si, err, st)
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+bool Launch<ESP_REAL>::supports_P(int P) { return P >= ESP_P_MIN && P <= ESP_P_MAX; }
+
+template <>
+cudaError_t Launch<ESP_REAL>::scale(const SysDesc* sys, int nsys, int nblk, void* spec,
+                                    const ESP_REAL* tabs, double* partials, cudaStream_t st) {
+  using C = typename Types<ESP_REAL>::cplx;
+  dim3 grid(nblk, nsys);
+  k_scale<ESP_REAL><<<grid, 256, 0, st>>>(sys, (C*)spec, tabs, partials);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n_chunks,
+                                   const void* atoms, const uint32_t* start, void* nearres,
+                                   const NearCoef<ESP_REAL>& nc, cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  using R = typename Types<ESP_REAL>::res;
+  if (n_chunks == 0) return cudaSuccess;
+  k_near<ESP_REAL><<<n_chunks, kChunk, 0, st>>>(sys, chunks, (const A*)atoms, start, (R*)nearres, nc);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t Launch<ESP_REAL>::finalize(const SysDesc* sys, const int2* chunks, int n_chunks,
+                                       const void* atoms, const uint32_t* perm, const void* far,
+                                       const void* nearres, void* forces, void* pot,
+                                       bool out_double, double* partials, cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  using R = typename Types<ESP_REAL>::res;
+  if (n_chunks == 0) return cudaSuccess;
+  if (out_double)
+    k_finalize<ESP_REAL, double><<<n_chunks, kChunk, 0, st>>>(
+        sys, chunks, (const A*)atoms, perm, (const R*)far, (const R*)nearres, (double*)forces,
+        (double*)pot, partials, n_chunks);
+  else
+    k_finalize<ESP_REAL, float><<<n_chunks, kChunk, 0, st>>>(
+        sys, chunks, (const A*)atoms, perm, (const R*)far, (const R*)nearres, (float*)forces,
+        (float*)pot, partials, n_chunks);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t Launch<ESP_REAL>::convert_charges(const void* src, bool src_double, ESP_REAL* dst,
+                                              long long n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (src_double)
+    detail::k_convert<ESP_REAL, double><<<blocks, 256, 0, st>>>((const double*)src, dst, n);
+  else
+    detail::k_convert<ESP_REAL, float><<<blocks, 256, 0, st>>>((const float*)src, dst, n);
+  return cudaGetLastError();
+}
+
+template <>
+size_t Launch<ESP_REAL>::atom_bytes() { return sizeof(typename Types<ESP_REAL>::atom); }
+template <>
+size_t Launch<ESP_REAL>::res_bytes() { return sizeof(typename Types<ESP_REAL>::res); }
+
+}  // namespace espk

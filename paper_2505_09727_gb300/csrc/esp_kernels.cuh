@@ -1,0 +1,562 @@
+// Kernel templates of the ESP pipeline (see esp_device.cuh for the overview).
+// Instantiated for FP32 (production) in esp_kern_f32.cu and FP64 (plain mode)
+// in esp_kern_f64.cu.
+#pragma once
+#include "esp_device.cuh"
+
+namespace espk {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+// 32-byte aligned FP64 quadruple (one 256-bit access per atom / result).
+struct __align__(32) dquad { double x, y, z, w; };
+__host__ __device__ inline dquad make_dquad(double x, double y, double z, double w) {
+  dquad d; d.x = x; d.y = y; d.z = z; d.w = w; return d;
+}
+
+template <typename real> struct Types;
+template <> struct Types<float> {
+  using atom = uint4;      // (ux, uy, uz) fixed point, w = charge bits
+  using res = float4;      // (u, a, b, c)
+  using cplx = float2;
+};
+template <> struct Types<double> {
+  using atom = dquad;      // (x, y, z) wrapped, w = charge
+  using res = dquad;
+  using cplx = double2;
+};
+
+__device__ inline float atom_q(const uint4& a) { return __uint_as_float(a.w); }
+__device__ inline double atom_q(const dquad& a) { return a.w; }
+
+// ------------------------------------------------------------ cell geometry
+__device__ inline int cell_key(const SysDesc& S, int cx, int cy, int cz) {
+  const int bc = S.bc, nb = S.nb;
+  const int bx = cx / bc, by = cy / bc, bz = cz / bc;
+  const int lx = cx - bx * bc, ly = cy - by * bc, lz = cz - bz * bc;
+  return ((bz * nb + by) * nb + bx) * (bc * bc * bc) + (lz * bc + ly) * bc + lx;
+}
+
+__device__ inline void atom_cell(const SysDesc& S, const uint4& a, int& cx, int& cy, int& cz) {
+  cx = (int)(((uint64_t)a.x * (uint64_t)S.n_c) >> 32);
+  cy = (int)(((uint64_t)a.y * (uint64_t)S.n_c) >> 32);
+  cz = (int)(((uint64_t)a.z * (uint64_t)S.n_c) >> 32);
+}
+
+__device__ inline int cell_f64(double x, const SysDesc& S) {
+  int c = (int)(x * S.inv_L * S.n_c);
+  return c < 0 ? 0 : (c >= S.n_c ? S.n_c - 1 : c);
+}
+
+__device__ inline void atom_cell(const SysDesc& S, const dquad& a, int& cx, int& cy, int& cz) {
+  cx = cell_f64(a.x, S);
+  cy = cell_f64(a.y, S);
+  cz = cell_f64(a.z, S);
+}
+
+// Tile origin of brick coordinate cb (cells cb*bc ...) along one axis.
+__device__ inline int tile_origin(const SysDesc& S, int cbrick, int P, float) {
+  return tile_origin_fixed(cbrick * S.bc, S.n_c, S.n_f, P);
+}
+__device__ inline int tile_origin(const SysDesc& S, int cbrick, int P, double) {
+  double d;
+  double x = (double)(cbrick * S.bc) * S.L / S.n_c;
+  return stencil_origin_f64(x, S.inv_h, P, d) - 1;   // one-point margin for FP64 rounding
+}
+
+// Stencil of one coordinate: origin l0 and y = 2 delta - 1.
+__device__ inline int stencil(const SysDesc& S, uint32_t u, int P, float& y) {
+  int l0; int64_t r;
+  stencil_fixed(u, S.n_f, P, l0, r);
+  y = (float)(r - (1LL << 31)) * 4.656612873077392578125e-10f;   // 2^-31
+  return l0;
+}
+__device__ inline int stencil(const SysDesc& S, double x, int P, double& y) {
+  double delta;
+  int l0 = stencil_origin_f64(x, S.inv_h, P, delta);
+  y = 2.0 * delta - 1.0;
+  return l0;
+}
+
+// P SI weights (and optionally derivatives d phi / dt) at y.
+template <typename real, int P, bool DERIV>
+__device__ __forceinline__ void si_weights(const SICoef<real>& si, real y, real* w, real* dw) {
+  constexpr int NC = Deg<real>::si;
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    real v = si.c[a][NC - 1];
+    real d = real(0);
+#pragma unroll
+    for (int k = NC - 2; k >= 0; --k) {
+      if (DERIV) d = d * y + v;
+      v = v * y + si.c[a][k];
+    }
+    w[a] = v;
+    if (DERIV) dw[a] = real(2) * d;    // d/dt = d/d delta = 2 d/dy
+  }
+}
+
+// Weight (and derivative) of one stencil point a (runtime, block-uniform).
+template <typename real, bool DERIV>
+__device__ __forceinline__ void si_weight_one(const SICoef<real>& si, int a, real y, real& w, real& dw) {
+  constexpr int NC = Deg<real>::si;
+  real v = si.c[a][NC - 1];
+  real d = real(0);
+#pragma unroll
+  for (int k = NC - 2; k >= 0; --k) {
+    if (DERIV) d = d * y + v;
+    v = v * y + si.c[a][k];
+  }
+  w = v;
+  if (DERIV) dw = real(2) * d;
+}
+
+// Wide stencils keep the outer (z) loop rolled to bound code size.
+template <int P> struct Unroll { static constexpr int outer = P <= 8 ? P : 1; };
+
+// ================================================================ kernels
+// A0: wrap, convert, key, rank. One thread per atom of a chunk.
+template <typename real, typename In>
+__global__ void __launch_bounds__(kChunk) k_ingest(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ chunks, const In* __restrict__ xyz,
+    typename Types<real>::atom* __restrict__ coord, uint32_t* __restrict__ key,
+    uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ err) {
+  const int2 ch = chunks[blockIdx.x];
+  const SysDesc& S = sys[ch.x];
+  const int local = ch.y + threadIdx.x;
+  if (local >= S.n_atoms) return;
+  const long long i = S.atom0 + local;
+  double p[3];
+  bool finite = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    p[a] = (double)xyz[3 * i + a];
+    finite &= isfinite(p[a]);
+  }
+  if (!finite) {
+    atomicOr(err, 1);
+    p[0] = p[1] = p[2] = 0.0;
+  }
+  int c[3];
+  typename Types<real>::atom out;
+  if constexpr (sizeof(real) == 4) {
+    uint32_t u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double f = p[a] * S.inv_L;
+      f -= floor(f);
+      if (!(f < 1.0) || f < 0.0) f = 0.0;
+      u[a] = (uint32_t)(f * 4294967296.0);
+      c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
+    }
+    out = make_uint4(u[0], u[1], u[2], 0u);
+  } else {
+    double w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double x = p[a] - S.L * floor(p[a] * S.inv_L);
+      if (!(x < S.L) || x < 0.0) x = 0.0;
+      w[a] = x;
+      c[a] = cell_f64(x, S);
+    }
+    out = make_dquad(w[0], w[1], w[2], 0.0);
+  }
+  const uint32_t k = (uint32_t)cell_key(S, c[0], c[1], c[2]);
+  coord[i] = out;
+  key[i] = k;
+  rank[i] = atomicAdd(&count[S.cell0 + k], 1u);
+}
+
+// A1a: exclusive scan of the pooled cell counts (one block of 1024 threads).
+static __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ count,
+                                               uint32_t* __restrict__ start, long long n) {
+  __shared__ uint32_t wsum[32];
+  const long long per = (n + blockDim.x - 1) / blockDim.x;
+  const long long b = per * threadIdx.x;
+  const long long e = b + per < n ? b + per : n;
+  uint32_t s = 0;
+  for (long long j = b; j < e; ++j) s += count[j];
+  // block exclusive scan of s
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t v = wsum[lane];
+    uint32_t vi = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += t;
+    }
+    wsum[lane] = vi - v;
+  }
+  __syncthreads();
+  uint32_t run = wsum[wid] + incl - s;
+  for (long long j = b; j < e; ++j) {
+    start[j] = run;
+    run += count[j];
+  }
+  if (threadIdx.x == blockDim.x - 1) start[n] = run;
+}
+
+// A1b: counting-sort scatter. perm[sorted] = pooled caller index.
+template <typename real, typename Q>
+__global__ void __launch_bounds__(kChunk) k_scatter(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
+    const typename Types<real>::atom* __restrict__ coord, const uint32_t* __restrict__ key,
+    const uint32_t* __restrict__ rank, const uint32_t* __restrict__ start, const Q* __restrict__ q,
+    typename Types<real>::atom* __restrict__ atoms, uint32_t* __restrict__ perm) {
+  const int2 ch = chunks[blockIdx.x];
+  const SysDesc& S = sys[ch.x];
+  const int local = ch.y + threadIdx.x;
+  if (local >= S.n_atoms) return;
+  const long long i = S.atom0 + local;
+  const uint32_t dst = start[S.cell0 + key[i]] + rank[i];
+  typename Types<real>::atom a = coord[i];
+  if constexpr (sizeof(real) == 4) a.w = __float_as_uint((float)q[i]);
+  else a.w = (double)q[i];
+  atoms[dst] = a;
+  perm[dst] = (uint32_t)i;
+}
+
+// A2: spread (Eq. spread). One CTA per (system, brick).
+template <typename real, int P>
+__global__ void __launch_bounds__(256) k_spread(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ work,
+    const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ start,
+    real* __restrict__ grids, const SICoef<real> si, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* tile = reinterpret_cast<real*>(smem_raw);
+  const int2 wk = work[blockIdx.x];
+  const SysDesc& S = sys[wk.x];
+  const int nb = S.nb, T = S.T, n_f = S.n_f, bc = S.bc;
+  const int b = wk.y;
+  const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+  const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
+            oz = tile_origin(S, bz, P, real());
+  const int T3 = T * T * T;
+  for (int j = threadIdx.x; j < T3; j += blockDim.x) tile[j] = real(0);
+  __syncthreads();
+  const long long k0 = S.cell0 + (long long)b * bc * bc * bc;
+  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc];
+  for (uint32_t i = a_begin + threadIdx.x; i < a_end; i += blockDim.x) {
+    const typename Types<real>::atom at = atoms[i];
+    real yx, yy, yz;
+    const int lx = stencil(S, at.x, P, yx) - ox;
+    const int ly = stencil(S, at.y, P, yy) - oy;
+    const int lz = stencil(S, at.z, P, yz) - oz;
+    if (lx < 0 || ly < 0 || lz < 0 || lx > T - P || ly > T - P || lz > T - P) {
+      atomicOr(err, 2);
+      continue;
+    }
+    real wx[P], wy[P];
+    si_weights<real, P, false>(si, yx, wx, nullptr);
+    si_weights<real, P, false>(si, yy, wy, nullptr);
+    const real q = (real)atom_q(at);
+#pragma unroll (Unroll<P>::outer)
+    for (int c = 0; c < P; ++c) {
+      real wzc, unused;
+      si_weight_one<real, false>(si, c, yz, wzc, unused);
+      const real qz = q * wzc;
+#pragma unroll
+      for (int bb = 0; bb < P; ++bb) {
+        const real qzy = qz * wy[bb];
+        real* row = tile + ((lz + c) * T + (ly + bb)) * T + lx;
+#pragma unroll
+        for (int a = 0; a < P; ++a) atomicAdd(row + a, qzy * wx[a]);
+      }
+    }
+  }
+  __syncthreads();
+  real* grid = grids + S.grid0;
+  for (int j = threadIdx.x; j < T3; j += blockDim.x) {
+    const real v = tile[j];
+    if (v != real(0)) {
+      const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
+      const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f),
+                gz = wrap_index(oz + jz, n_f);
+      atomicAdd(grid + ((long long)gz * n_f + gy) * n_f + gx, v);
+    }
+  }
+}
+
+// A4: influence scale fused with the spectral energy (Eq. pk). Grid-stride
+// over the half spectrum [kz][ky][kx], kx in [0, n_f/2]; blockIdx.y = system.
+template <typename real>
+__global__ void __launch_bounds__(256) k_scale(
+    const SysDesc* __restrict__ sys, typename Types<real>::cplx* __restrict__ spec,
+    const real* __restrict__ tabs, double* __restrict__ partials) {
+  __shared__ double red[32];
+  const SysDesc& S = sys[blockIdx.y];
+  const int n = S.n_f, nh = n / 2 + 1, half = n / 2;
+  const long long total = (long long)n * n * nh;
+  typename Types<real>::cplx* sp = spec + S.spec0;
+  const real* G = tabs + S.tab0;
+  const real* W = G + S.gsize;
+  double e = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(idx % nh);
+    const long long r = idx / nh;
+    const int kyi = (int)(r % n), kzi = (int)(r / n);
+    const int ky = kyi < half ? kyi : kyi - n;
+    const int kz = kzi < half ? kzi : kzi - n;
+    const int m = kx * kx + ky * ky + kz * kz;
+    const real p = __ldg(G + m) * __ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz));
+    typename Types<real>::cplx v = sp[idx];
+    const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
+    e += wgt * (double)p * ((double)v.x * v.x + (double)v.y * v.y);
+    v.x *= p;
+    v.y *= p;
+    sp[idx] = v;
+  }
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * e;
+}
+
+// A6: gather (Eq. interp) with analytic-derivative forces.
+template <typename real, int P>
+__global__ void __launch_bounds__(256) k_gather(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ work,
+    const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ start,
+    const real* __restrict__ grids, typename Types<real>::res* __restrict__ far,
+    const SICoef<real> si, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* tile = reinterpret_cast<real*>(smem_raw);
+  const int2 wk = work[blockIdx.x];
+  const SysDesc& S = sys[wk.x];
+  const int nb = S.nb, T = S.T, n_f = S.n_f, bc = S.bc;
+  const int b = wk.y;
+  const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+  const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
+            oz = tile_origin(S, bz, P, real());
+  const int T3 = T * T * T;
+  const real* grid = grids + S.grid0;
+  for (int j = threadIdx.x; j < T3; j += blockDim.x) {
+    const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
+    const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f),
+              gz = wrap_index(oz + jz, n_f);
+    tile[j] = __ldg(grid + ((long long)gz * n_f + gy) * n_f + gx);
+  }
+  __syncthreads();
+  const long long k0 = S.cell0 + (long long)b * bc * bc * bc;
+  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc];
+  const real inv_h = (real)S.inv_h;
+  for (uint32_t i = a_begin + threadIdx.x; i < a_end; i += blockDim.x) {
+    const typename Types<real>::atom at = atoms[i];
+    real yx, yy, yz;
+    const int lx = stencil(S, at.x, P, yx) - ox;
+    const int ly = stencil(S, at.y, P, yy) - oy;
+    const int lz = stencil(S, at.z, P, yz) - oz;
+    typename Types<real>::res out;
+    if (lx < 0 || ly < 0 || lz < 0 || lx > T - P || ly > T - P || lz > T - P) {
+      atomicOr(err, 2);
+      out.x = out.y = out.z = out.w = real(0);
+      far[i] = out;
+      continue;
+    }
+    real wx[P], wy[P], dx[P], dy[P];
+    si_weights<real, P, true>(si, yx, wx, dx);
+    si_weights<real, P, true>(si, yy, wy, dy);
+    real u = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll (Unroll<P>::outer)
+    for (int c = 0; c < P; ++c) {
+      real wzc, dzc;
+      si_weight_one<real, true>(si, c, yz, wzc, dzc);
+      real uc = 0, gxc = 0, gyc = 0;
+#pragma unroll
+      for (int bb = 0; bb < P; ++bb) {
+        const real* row = tile + ((lz + c) * T + (ly + bb)) * T + lx;
+        real s0 = 0, s1 = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          const real v = row[a];
+          s0 += wx[a] * v;
+          s1 += dx[a] * v;
+        }
+        uc += wy[bb] * s0;
+        gyc += dy[bb] * s0;
+        gxc += wy[bb] * s1;
+      }
+      u += wzc * uc;
+      gz += dzc * uc;
+      gx += wzc * gxc;
+      gy += wzc * gyc;
+    }
+    out.x = u;
+    out.y = gx * inv_h;
+    out.z = gy * inv_h;
+    out.w = gz * inv_h;
+    far[i] = out;
+  }
+}
+
+// A7: local part (Eq. localpart). One thread per sorted atom; the 5^3 cells
+// around its cell (edge >= r_c/2) cover every neighbour within r_c.
+template <typename real>
+__device__ __forceinline__ real horner(const real* c, real y) {
+  constexpr int NC = Deg<real>::nr;
+  real v = c[NC - 1];
+#pragma unroll
+  for (int k = NC - 2; k >= 0; --k) v = v * y + c[k];
+  return v;
+}
+
+__device__ inline void pair_delta(const SysDesc& S, const uint4& a, const uint4& b, float scale,
+                                  float& dx, float& dy, float& dz) {
+  dx = (float)(int)(a.x - b.x) * scale;    // int32 wrap = minimum image
+  dy = (float)(int)(a.y - b.y) * scale;
+  dz = (float)(int)(a.z - b.z) * scale;
+}
+__device__ inline void pair_delta(const SysDesc& S, const dquad& a, const dquad& b, double,
+                                  double& dx, double& dy, double& dz) {
+  dx = a.x - b.x; dx -= S.L * rint(dx * S.inv_L);
+  dy = a.y - b.y; dy -= S.L * rint(dy * S.inv_L);
+  dz = a.z - b.z; dz -= S.L * rint(dz * S.inv_L);
+}
+
+__device__ inline float rsqrt_real(float x) { return rsqrtf(x); }
+__device__ inline double rsqrt_real(double x) { return 1.0 / sqrt(x); }
+
+template <typename real>
+__global__ void __launch_bounds__(kChunk) k_near(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
+    const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ start,
+    typename Types<real>::res* __restrict__ nearres, const NearCoef<real> nc) {
+  const int2 ch = chunks[blockIdx.x];
+  const SysDesc& S = sys[ch.x];
+  const int local = ch.y + threadIdx.x;
+  if (local >= S.n_atoms) return;
+  const long long i = S.atom0 + local;
+  const typename Types<real>::atom ai = atoms[i];
+  int cx, cy, cz;
+  atom_cell(S, ai, cx, cy, cz);
+  const int n_c = S.n_c;
+  const int span = n_c < 5 ? n_c : 5;
+  const real scale = (real)S.fix_scale;
+  const real rc2 = (real)S.rc2, inv_rc = (real)S.inv_rc;
+  real pot = 0, fx = 0, fy = 0, fz = 0;
+  for (int dz = 0; dz < span; ++dz) {
+    const int zz = wrap_index(cz - 2 + dz, n_c);
+    for (int dy = 0; dy < span; ++dy) {
+      const int yy = wrap_index(cy - 2 + dy, n_c);
+      for (int dxc = 0; dxc < span; ++dxc) {
+        const int xx = wrap_index(cx - 2 + dxc, n_c);
+        const long long kk = S.cell0 + cell_key(S, xx, yy, zz);
+        const uint32_t jb = start[kk], je = start[kk + 1];
+        for (uint32_t j = jb; j < je; ++j) {
+          const typename Types<real>::atom aj = atoms[j];
+          real ddx, ddy, ddz;
+          pair_delta(S, ai, aj, scale, ddx, ddy, ddz);
+          const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2 < rc2 && (long long)j != i) {
+            const real rinv = rsqrt_real(r2);
+            const real y = real(2) * (r2 * rinv * inv_rc) - real(1);
+            const real e = horner<real>(nc.e, y);
+            const real chi = horner<real>(nc.chi, y);
+            const real qj = (real)atom_q(aj);
+            const real qe = qj * e * rinv;
+            pot += qe;
+            const real s = (qe + qj * chi * inv_rc) * rinv * rinv;
+            fx += s * ddx;
+            fy += s * ddy;
+            fz += s * ddz;
+          }
+        }
+      }
+    }
+  }
+  const real qi = (real)atom_q(ai);
+  const real k4 = real(1.0 / kFourPi);
+  typename Types<real>::res out;
+  out.x = pot * k4;
+  out.y = qi * fx * k4;
+  out.z = qi * fy * k4;
+  out.w = qi * fz * k4;
+  nearres[i] = out;
+}
+
+// A8: per-atom totals in the caller's order and energy partials.
+// partials layout: [near chunk partials][gather chunk partials].
+template <typename real, typename Out>
+__global__ void __launch_bounds__(kChunk) k_finalize(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
+    const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ perm,
+    const typename Types<real>::res* __restrict__ far, const typename Types<real>::res* __restrict__ nearres,
+    Out* __restrict__ forces, Out* __restrict__ pot, double* __restrict__ partials, int n_chunks) {
+  __shared__ double red[32];
+  const int2 ch = chunks[blockIdx.x];
+  const SysDesc& S = sys[ch.x];
+  const int local = ch.y + threadIdx.x;
+  double en = 0.0, eg = 0.0;
+  if (local < S.n_atoms) {
+    const long long i = S.atom0 + local;
+    const typename Types<real>::atom at = atoms[i];
+    const double q = (double)atom_q(at);
+    const typename Types<real>::res f = far[i];
+    const typename Types<real>::res nr = nearres[i];
+    const uint32_t o = perm[i];
+    const double u = (double)f.x + (double)nr.x - q * S.self_coef + S.bg_shift;
+    const double pre = S.prefactor;
+    if (forces) {
+      forces[3ll * o + 0] = (Out)(pre * (-q * (double)f.y + (double)nr.y));
+      forces[3ll * o + 1] = (Out)(pre * (-q * (double)f.z + (double)nr.z));
+      forces[3ll * o + 2] = (Out)(pre * (-q * (double)f.w + (double)nr.w));
+    }
+    if (pot) pot[o] = (Out)(pre * u);
+    en = 0.5 * q * (double)nr.x;
+    eg = 0.5 * q * (double)f.x;
+  }
+  en = block_sum(en, red);
+  eg = block_sum(eg, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = en;
+    partials[n_chunks + blockIdx.x] = eg;
+  }
+}
+
+// Compensated (Neumaier) sum of a strided range, then a pairwise block tree.
+__device__ inline void neumaier_add(double& s, double& c, double v) {
+  double t = s + v;
+  if (fabs(s) >= fabs(v)) c += (s - t) + v; else c += (v - t) + s;
+  s = t;
+}
+
+// Per-system energy: E = prefactor (E_fourier + E_near + E_self + E_bg).
+// One block per system. out[3 s + 0] = E, [1] = E_fourier, [2] = E_gather.
+static __global__ void __launch_bounds__(256) k_energy(
+    const SysDesc* __restrict__ sys, const double* __restrict__ fourier, int n_fourier_blocks,
+    const double* __restrict__ partials, int n_chunks, const int* __restrict__ chunk_first,
+    const double* __restrict__ consts, double* __restrict__ out, double* __restrict__ user_energy) {
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  double vs[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+  for (int j = threadIdx.x; j < n_fourier_blocks; j += blockDim.x)
+    neumaier_add(vs[0], vc[0], fourier[(long long)s * n_fourier_blocks + j]);
+  for (int j = chunk_first[s] + threadIdx.x; j < chunk_first[s + 1]; j += blockDim.x) {
+    neumaier_add(vs[1], vc[1], partials[j]);
+    neumaier_add(vs[2], vc[2], partials[n_chunks + j]);
+  }
+  double tot[3];
+  for (int a = 0; a < 3; ++a) tot[a] = block_sum(vs[a] + vc[a], red);
+  if (threadIdx.x == 0) {
+    const double pre = sys[s].prefactor;
+    // consts[2 s] = E_self, consts[2 s + 1] = E_bg (host FP64)
+    double acc = 0.0, cc = 0.0;
+    neumaier_add(acc, cc, tot[0]);
+    neumaier_add(acc, cc, tot[1]);
+    neumaier_add(acc, cc, consts[2 * s]);
+    neumaier_add(acc, cc, consts[2 * s + 1]);
+    const double e = pre * (acc + cc);
+    out[3 * s + 0] = e;
+    out[3 * s + 1] = pre * tot[0];
+    out[3 * s + 2] = pre * tot[2];
+    if (user_energy) user_energy[s] = e;
+  }
+}
+
+}  // namespace espk

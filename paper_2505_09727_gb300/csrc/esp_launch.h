@@ -1,0 +1,45 @@
+// Host-callable launchers for the ESP kernels, one set per precision.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "esp_device.cuh"
+
+namespace espk {
+
+template <typename real>
+struct Launch {
+  static cudaError_t ingest(const SysDesc* sys, const int2* chunks, int n_chunks, const void* xyz,
+                            bool xyz_is_double, void* coord, uint32_t* key, uint32_t* rank,
+                            uint32_t* count, int* err, cudaStream_t st);
+  static cudaError_t scatter(const SysDesc* sys, const int2* chunks, int n_chunks, const void* coord,
+                             const uint32_t* key, const uint32_t* rank, const uint32_t* start,
+                             const real* q, void* atoms, uint32_t* perm, cudaStream_t st);
+  static cudaError_t spread(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem,
+                            const void* atoms, const uint32_t* start, real* grids,
+                            const SICoef<real>& si, int* err, cudaStream_t st);
+  static cudaError_t scale(const SysDesc* sys, int nsys, int nblk, void* spec, const real* tabs,
+                           double* partials, cudaStream_t st);
+  static cudaError_t gather(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem,
+                            const void* atoms, const uint32_t* start, const real* grids, void* far,
+                            const SICoef<real>& si, int* err, cudaStream_t st);
+  static cudaError_t near(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
+                          const uint32_t* start, void* nearres, const NearCoef<real>& nc,
+                          cudaStream_t st);
+  static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
+                              const uint32_t* perm, const void* far, const void* nearres,
+                              void* forces, void* pot, bool out_double, double* partials,
+                              cudaStream_t st);
+  static cudaError_t convert_charges(const void* src, bool src_double, real* dst, long long n,
+                                     cudaStream_t st);
+  static bool supports_P(int P);
+  static size_t atom_bytes();
+  static size_t res_bytes();
+};
+
+cudaError_t launch_scan(const uint32_t* count, uint32_t* start, long long n, cudaStream_t st);
+cudaError_t launch_energy(const SysDesc* sys, int nsys, const double* fourier, int n_fourier_blocks,
+                          const double* partials, int n_chunks, const int* chunk_first,
+                          const double* consts, double* out, double* user_energy, cudaStream_t st);
+
+}  // namespace espk

@@ -1,0 +1,293 @@
+// Host planning of one system (see esp_plan.h).
+//
+// Parameter rules (paper, Methods):
+//  * c from psi_0^c(1) = eps (Eq. pswfparameters), P from Table 2;
+//  * n_f starts at ceil(c L / (pi r_c)) (PSWF, Eq. pswfparameters) or
+//    2 ceil(ln(1/eps) L / (pi r_c)) (Gaussian, Eq. cemparameters), rounded to
+//    an even FFT-friendly size;
+//  * the SI-kernel shape c1 is the one of c1/c in {1.10, 1.15, ..., 1.40} that
+//    minimises the relative aliasing estimate (Eq. errorformula), and n_f is
+//    raised until that minimum is at most eps/2 ("n_f possibly increased,
+//    until [E_A] is of order eps");
+//  * r_c, when not given, minimises a GPU cost model of the local and
+//    spectral parts ("r_c may be adjusted to balance the computational costs").
+#include "esp_plan.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace espe {
+
+static const double kPi = 3.14159265358979323846;
+
+// Sum over ky, kz of |chihat(2 pi r_c |k| / L)| / |k|^2 for each kx in I.
+static std::vector<double> alias_rows(const espm::Split& s, int n_f, double L, double r_c) {
+  const int h = n_f / 2;
+  const int mmax = 3 * h * h;
+  std::vector<double> base(mmax + 1, 0.0);
+  for (int m = 1; m <= mmax; ++m)
+    base[m] = std::fabs(s.chihat(2.0 * kPi * r_c * std::sqrt((double)m) / L)) / m;
+  // S2[q] = sum_{ky,kz} base[q + ky^2 + kz^2]
+  std::vector<double> rows(n_f, 0.0);
+  for (int kx = -h; kx < h; ++kx) {
+    double r = 0.0;
+    for (int ky = -h; ky < h; ++ky)
+      for (int kz = -h; kz < h; ++kz) r += base[kx * kx + ky * ky + kz * kz];
+    rows[kx + h] = r;
+  }
+  return rows;
+}
+
+static double alias_from_rows(const std::vector<double>& rows, const espm::Window& w, int n_f) {
+  const int h = n_f / 2;
+  double num = 0.0, den = 0.0;
+  for (int kx = -h; kx < h; ++kx) {
+    const double th = 2.0 * kPi * kx / n_f;
+    const double ratio = std::fabs(w.Phi(th + 2.0 * kPi) / w.Phi(th));
+    num += ratio * rows[kx + h];
+    den += rows[kx + h];
+  }
+  return 6.0 * num / den;
+}
+
+// GPU cost model (seconds) used only to pick r_c when the caller does not.
+static double model_cost(double L, long long N, int P, double c, double r_c, int kernel, double tol) {
+  const double rho = (double)N / (L * L * L);
+  const double nmin = kernel == ESP_KERNEL_PSWF ? c * L / (kPi * r_c)
+                                                : 2.0 * std::ceil(std::log(1.0 / tol) * L / (kPi * r_c));
+  const int n_f = espm::round_grid(nmin);
+  if (n_f > 1024) return 1e30;
+  const int n_c = std::max(1, (int)std::floor(2.0 * L / r_c));
+  const double cell = L / n_c;
+  const double cand = n_c >= 5 ? 125.0 * cell * cell * cell * rho : (double)N;
+  const double nf3 = (double)n_f * n_f * n_f;
+  const double t_near = 2.5e-13 * (double)N * cand;
+  const double t_sg = 1.5e-13 * (double)N * P * P * P;
+  const double t_fft = 2.0 * 1.0e-12 * nf3 * std::log2(std::max(8.0, nf3)) + 2.0e-5;
+  return t_near + t_sg + t_fft;
+}
+
+// Chebyshev interpolation of f on y in [-1,1] at degree `deg`, converted to
+// monomial coefficients in y (out[k] multiplies y^k); returns the max error of
+// the monomial form on a fine sample.
+template <class F>
+static double fit(F f, int deg, std::vector<double>& out) {
+  const int n = deg + 1;
+  const double pi = kPi;
+  std::vector<double> fv(n), cheb(n, 0.0);
+  for (int j = 0; j < n; ++j) fv[j] = f(std::cos(pi * (j + 0.5) / n));
+  for (int k = 0; k < n; ++k) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += fv[j] * std::cos(pi * k * (j + 0.5) / n);
+    cheb[k] = (k == 0 ? 1.0 : 2.0) * s / n;
+  }
+  out.assign(n, 0.0);
+  std::vector<double> tprev(n, 0.0), tcur(n, 0.0), tnext(n, 0.0);
+  tprev[0] = 1.0;
+  if (n > 1) tcur[1] = 1.0;
+  out[0] += cheb[0];
+  if (n > 1) out[1] += cheb[1];
+  for (int k = 2; k < n; ++k) {
+    std::fill(tnext.begin(), tnext.end(), 0.0);
+    for (int i = 0; i + 1 < n; ++i) tnext[i + 1] += 2.0 * tcur[i];
+    for (int i = 0; i < n; ++i) tnext[i] -= tprev[i];
+    for (int i = 0; i < n; ++i) out[i] += cheb[k] * tnext[i];
+    tprev.swap(tcur);
+    tcur.swap(tnext);
+  }
+  double err = 0.0;
+  for (int i = 0; i <= 1000; ++i) {
+    const double y = -1.0 + 2.0 * i / 1000.0;
+    double v = 0.0;
+    for (int k = n - 1; k >= 0; --k) v = v * y + out[k];
+    err = std::max(err, std::fabs(v - f(y)));
+  }
+  return err;
+}
+
+static int tile_edge(const espk::SysDesc& d, int P, int precision) {
+  int T = 0;
+  for (int cb = 0; cb < d.nb; ++cb) {
+    int t;
+    if (precision == ESP_FP32) {
+      t = espk::tile_last_fixed((cb + 1) * d.bc, d.n_c, d.n_f, P) -
+          espk::tile_origin_fixed(cb * d.bc, d.n_c, d.n_f, P) + P;
+    } else {
+      double dl;
+      const int lo = espk::stencil_origin_f64((double)(cb * d.bc) * d.L / d.n_c, d.inv_h, P, dl);
+      const int hi = espk::stencil_origin_f64((double)((cb + 1) * d.bc) * d.L / d.n_c, d.inv_h, P, dl);
+      t = hi - lo + P + 2;
+    }
+    T = std::max(T, t);
+  }
+  return T;
+}
+
+esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts& o, HostPlan& hp,
+                          std::string& msg) {
+  if (!(L > 0.0) || !std::isfinite(L)) { msg = "box edge must be positive and finite"; return ESP_ERR_INVALID_ARG; }
+  if (N < 0 || N >= (1LL << 31)) { msg = "N must be in [0, 2^31)"; return ESP_ERR_INVALID_ARG; }
+  if (!(tol > 1e-15 && tol < 0.1)) { msg = "tolerance must be in (1e-15, 0.1)"; return ESP_ERR_INVALID_ARG; }
+  const int prec = o.precision;
+  const int kernel = o.kernel;
+  if (prec != ESP_FP32 && prec != ESP_FP64) { msg = "precision must be ESP_FP32 or ESP_FP64"; return ESP_ERR_INVALID_ARG; }
+  if (kernel != ESP_KERNEL_PSWF && kernel != ESP_KERNEL_GAUSS) { msg = "unknown kernel"; return ESP_ERR_INVALID_ARG; }
+  const int pmax = prec == ESP_FP32 ? 12 : 16;
+
+  const double c = o.c > 0 ? o.c : espm::c_from_tolerance(tol);
+  const int P = o.P > 0 ? o.P : espm::stencil_width(tol);
+  if (P < espk::kMinP || P > pmax) {
+    msg = "stencil width P=" + std::to_string(P) + " outside the compiled range [4, " + std::to_string(pmax) + "]";
+    return ESP_ERR_UNSUPPORTED;
+  }
+  const double alpha = kernel == ESP_KERNEL_GAUSS ? (o.alpha > 0 ? o.alpha : std::log(1.0 / tol)) : 0.0;
+  espm::Split split = kernel == ESP_KERNEL_PSWF ? espm::make_pswf_split(c) : espm::make_gauss_split(alpha);
+
+  double r_c = o.r_c;
+  if (!(r_c > 0)) {
+    double best = 1e300;
+    r_c = 0.45 * L;
+    for (int i = 0; i < 60; ++i) {
+      const double r = L * (0.02 + (0.48 - 0.02) * i / 59.0);
+      const double t = model_cost(L, std::max<long long>(N, 1), P, c, r, kernel, tol);
+      if (t < best) { best = t; r_c = r; }
+    }
+  }
+  if (!(r_c < 0.5 * L)) { msg = "cutoff r_c must be smaller than L/2"; return ESP_ERR_CUTOFF_TOO_LARGE; }
+
+  // grid size and SI-kernel shape
+  std::vector<double> ratios;
+  if (o.c1 > 0) ratios.push_back(o.c1 / c);
+  else for (int i = 0; i < 7; ++i) ratios.push_back(1.10 + 0.05 * i);
+  int n_f;
+  if (o.n_f > 0) {
+    if (o.n_f % 2 || o.n_f < 4) { msg = "n_f must be even and >= 4"; return ESP_ERR_INVALID_ARG; }
+    n_f = o.n_f;
+  } else {
+    const double nmin = kernel == ESP_KERNEL_PSWF ? c * L / (kPi * r_c)
+                                                  : 2.0 * std::ceil(std::log(1.0 / tol) * L / (kPi * r_c));
+    n_f = espm::round_grid(std::max(4.0, nmin));
+  }
+  if (n_f > 1024) { msg = "grid too large (n_f > 1024): raise r_c or the tolerance"; return ESP_ERR_UNSUPPORTED; }
+  double best_c1 = ratios[0] * c, best_alias = 1e300;
+  std::vector<espm::Window> windows;
+  for (double r : ratios) windows.push_back(espm::make_window(r * c, P));
+  for (int step = 0; step < 8; ++step) {
+    const std::vector<double> rows = alias_rows(split, n_f, L, r_c);
+    best_alias = 1e300;
+    for (size_t i = 0; i < ratios.size(); ++i) {
+      const double a = alias_from_rows(rows, windows[i], n_f);
+      if (a < best_alias) { best_alias = a; best_c1 = ratios[i] * c; }
+    }
+    if (o.n_f > 0 || best_alias <= 0.5 * tol || n_f >= 1024) break;
+    n_f = espm::round_grid(n_f + 1);
+  }
+  const espm::Window win = espm::make_window(best_c1, P);
+
+  // cell list and bricks
+  const int nc_max = std::max(1, (int)std::floor(2.0 * L / r_c * (1.0 - 1e-12)));
+  const int cand[7] = {4, 3, 5, 2, 6, 8, 1};
+  const double h = L / n_f;
+  int n_c = 0, bc = 0, T = 0;
+  const size_t rb = prec == ESP_FP32 ? 4 : 8;
+  for (int i = 0; i < 7; ++i) {
+    const int b = cand[i];
+    if (o.brick_cells > 0 && b != o.brick_cells) continue;
+    const int nc = (nc_max / b) * b;
+    if (nc < b || nc == 0) continue;
+    espk::SysDesc d{};
+    d.n_f = n_f; d.n_c = nc; d.bc = b; d.nb = nc / b;
+    d.L = L; d.inv_h = n_f / L;
+    const int t = tile_edge(d, P, prec);
+    if ((size_t)t * t * t * rb > 200 * 1024) continue;
+    if (nc > n_c) { n_c = nc; bc = b; T = t; }
+  }
+  if (o.brick_cells > 0 && n_c == 0) {
+    // requested brick does not divide any usable cell count: use single-cell bricks
+    msg = "brick_cells incompatible with the cell grid";
+    return ESP_ERR_INVALID_ARG;
+  }
+  if (n_c == 0) { msg = "no brick/tile shape fits in shared memory"; return ESP_ERR_UNSUPPORTED; }
+
+  // descriptor
+  espk::SysDesc& d = hp.desc;
+  d = espk::SysDesc{};
+  d.n_f = n_f; d.n_c = n_c; d.bc = bc; d.nb = n_c / bc; d.T = T;
+  d.n_atoms = (int)N;
+  d.gsize = 3 * (n_f / 2) * (n_f / 2) + 1;
+  d.L = L; d.inv_L = 1.0 / L; d.h = h; d.inv_h = n_f / L;
+  d.r_c = r_c; d.rc2 = r_c * r_c; d.inv_rc = 1.0 / r_c;
+  d.fix_scale = L / 4294967296.0;
+  hp.self_unit = split.chi0() / (4.0 * kPi * r_c);
+  hp.m2 = split.second_moment();
+  d.self_coef = hp.self_unit;
+  d.bg_shift = 0.0;
+  d.prefactor = o.prefactor > 0 ? o.prefactor : 1.0;
+
+  // polynomial tables
+  double si_err = 0.0, near_err = 0.0;
+  std::vector<double> co;
+  for (int a = 0; a < P; ++a) {
+    auto fa = [&](double y) { return win.phi(0.5 * (y + 1.0) + 0.5 * P - 1.0 - a); };
+    si_err = std::max(si_err, fit(fa, espk::Deg<float>::si - 1, co) * (prec == ESP_FP32 ? 1.0 : 0.0));
+    for (int k = 0; k < espk::Deg<float>::si; ++k) hp.si32.c[a][k] = (float)co[k];
+    const double e64 = fit(fa, espk::Deg<double>::si - 1, co);
+    if (prec == ESP_FP64) si_err = std::max(si_err, e64);
+    for (int k = 0; k < espk::Deg<double>::si; ++k) hp.si64.c[a][k] = co[k];
+  }
+  auto fe = [&](double y) { return split.one_minus_g(0.5 * (y + 1.0)); };
+  auto fc = [&](double y) { return split.chi(0.5 * (y + 1.0)); };
+  {
+    double e1 = fit(fe, espk::Deg<float>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.e[k] = (float)co[k];
+    double e2 = fit(fc, espk::Deg<float>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.chi[k] = (float)co[k];
+    double e3 = fit(fe, espk::Deg<double>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.e[k] = co[k];
+    double e4 = fit(fc, espk::Deg<double>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.chi[k] = co[k];
+    near_err = prec == ESP_FP32 ? std::max(e1, e2) : std::max(e3, e4);
+  }
+
+  // influence tables (Eq. pk, Phi in grid units)
+  hp.G.assign(d.gsize, 0.0);
+  for (int m = 1; m < d.gsize; ++m) {
+    const double xi = 2.0 * kPi * std::sqrt((double)m) / L;
+    hp.G[m] = split.chihat(r_c * xi) / (xi * xi) / (L * L * L);
+  }
+  hp.W.assign(n_f / 2 + 1, 0.0);
+  for (int k = 0; k <= n_f / 2; ++k) {
+    const double ph = win.Phi(2.0 * kPi * k / n_f);
+    hp.W[k] = 1.0 / (ph * ph);
+  }
+
+  hp.tol = tol;
+  hp.n_cells3 = (long long)n_c * n_c * n_c;
+  hp.grid_elems = (long long)n_f * n_f * n_f;
+  hp.spec_elems = (long long)n_f * n_f * (n_f / 2 + 1);
+  hp.n_bricks = d.nb * d.nb * d.nb;
+
+  esp_plan_params& info = hp.info;
+  info = esp_plan_params{};
+  info.L = L; info.r_c = r_c; info.h = h; info.c = c; info.c1 = best_c1; info.alpha = alpha;
+  info.prefactor = d.prefactor;
+  info.alias_estimate = best_alias;
+  info.si_fit_error = si_err;
+  info.near_fit_error = near_err;
+  info.N = N; info.P = P; info.n_f = n_f; info.kernel = kernel; info.precision = prec;
+  info.n_cells = n_c; info.brick_cells = bc; info.tile = T;
+  info.si_degree = (prec == ESP_FP32 ? espk::Deg<float>::si : espk::Deg<double>::si) - 1;
+  info.near_degree = (prec == ESP_FP32 ? espk::Deg<float>::nr : espk::Deg<double>::nr) - 1;
+  return ESP_OK;
+}
+
+void charge_constants(const HostPlan& hp, double Q, double Q2, double* e_self, double* e_bg,
+                      double* bg_shift) {
+  const double L = hp.desc.L, V = L * L * L, r_c = hp.desc.r_c;
+  const double shift = -(Q / V) * 0.5 * r_c * r_c * hp.m2;
+  *bg_shift = shift;
+  *e_self = -0.5 * Q2 * hp.self_unit;
+  *e_bg = 0.5 * Q * shift;
+}
+
+}  // namespace espe

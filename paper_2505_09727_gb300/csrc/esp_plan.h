@@ -1,0 +1,39 @@
+// Host planning of one system: parameter choice (paper's rules), polynomial
+// tables and influence tables. Shared by the single-system and batch paths.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/esp.h"
+#include "esp_device.cuh"
+#include "esp_math.h"
+
+namespace espe {
+
+struct HostPlan {
+  esp_plan_params info{};
+  double tol = 0;
+  double self_unit = 0;        // chi(0) / (4 pi r_c)
+  double m2 = 0;               // int_0^1 x^2 chi
+  espk::SysDesc desc{};        // atom0/cell0/grid0/spec0/tab0 are zero here
+  espk::SICoef<float> si32{};
+  espk::SICoef<double> si64{};
+  espk::NearCoef<float> nc32{};
+  espk::NearCoef<double> nc64{};
+  std::vector<double> G, W;    // influence tables: G[|k|^2], W[|k_a|]
+  long long n_cells3 = 0;      // n_c^3
+  long long grid_elems = 0;    // n_f^3
+  long long spec_elems = 0;    // n_f^2 (n_f/2 + 1)
+  int n_bricks = 0;            // nb^3
+};
+
+// Fill `hp` for a cubic box of edge L with N atoms. Returns ESP_OK or an
+// error with a message in `msg`.
+esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts& opts, HostPlan& hp,
+                          std::string& msg);
+
+// Constants that depend on the charges (self energy, background).
+void charge_constants(const HostPlan& hp, double Q, double Q2, double* e_self, double* e_bg,
+                      double* bg_shift);
+
+}  // namespace espe

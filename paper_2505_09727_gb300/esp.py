@@ -1,0 +1,286 @@
+"""Python binding of the C-ABI in include/esp.h (argument marshalling only).
+
+Every function has the name of its C entry point. Arrays may be NumPy arrays
+(host memory, ``where=ESP_HOST``) or torch tensors (``where`` follows the
+tensor's device). All computation runs in libesp_gb300.so; this module never
+computes anything itself and raises if the library is not built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+ESP_OK = 0
+ESP_KERNEL_PSWF, ESP_KERNEL_GAUSS = 0, 1
+ESP_FP32, ESP_FP64 = 0, 1
+ESP_HOST, ESP_DEVICE = 0, 1
+
+STATUS = {
+    0: "ESP_OK", 1: "ESP_ERR_INVALID_ARG", 2: "ESP_ERR_CUTOFF_TOO_LARGE", 3: "ESP_ERR_NOT_NEUTRAL",
+    4: "ESP_ERR_NONFINITE", 5: "ESP_ERR_OOM", 6: "ESP_ERR_CUDA", 7: "ESP_ERR_CUFFT",
+    8: "ESP_ERR_TIMEOUT", 9: "ESP_ERR_BUSY", 10: "ESP_ERR_UNSUPPORTED", 11: "ESP_ERR_INTERNAL",
+    12: "ESP_ERR_NOT_READY",
+}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libesp_gb300.so")
+
+
+class EspError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class esp_box(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3)]
+
+
+class esp_plan_opts(ctypes.Structure):
+    _fields_ = [
+        ("r_c", ctypes.c_double), ("P", ctypes.c_int), ("n_f", ctypes.c_int),
+        ("c", ctypes.c_double), ("c1", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("prefactor", ctypes.c_double),
+        ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("allow_background", ctypes.c_int),
+        ("brick_cells", ctypes.c_int), ("timeout_ms", ctypes.c_double),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+
+class esp_plan_params(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_double), ("r_c", ctypes.c_double), ("h", ctypes.c_double),
+        ("c", ctypes.c_double), ("c1", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("prefactor", ctypes.c_double), ("alias_estimate", ctypes.c_double),
+        ("si_fit_error", ctypes.c_double), ("near_fit_error", ctypes.c_double),
+        ("N", ctypes.c_int64), ("P", ctypes.c_int), ("n_f", ctypes.c_int),
+        ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("n_cells", ctypes.c_int),
+        ("brick_cells", ctypes.c_int), ("tile", ctypes.c_int), ("si_degree", ctypes.c_int),
+        ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "esp_plan_opts_init": (None, [ctypes.POINTER(esp_plan_opts)]),
+    "esp_plan": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
+                                ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
+    "esp_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(esp_plan_params)]),
+    "esp_plan_query": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
+                                      ctypes.POINTER(esp_plan_opts), ctypes.POINTER(esp_plan_params)]),
+    "esp_set_charges": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "esp_set_charges_f32": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "esp_set_positions": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "esp_set_positions_f32": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "esp_compute": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "esp_compute_f32": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "esp_synchronize": (ctypes.c_int, [_P]),
+    "esp_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "esp_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "esp_last_spectral_energy": (ctypes.c_int, [_P, _D, _D]),
+    "esp_destroy": (ctypes.c_int, [_P]),
+    "esp_last_error": (ctypes.c_char_p, []),
+    "esp_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libesp_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != ESP_OK:
+        msg = load_library().esp_last_error()
+        raise EspError(status, msg.decode() if msg else "")
+
+
+def _ptr(x, dtype=None):
+    """(pointer, where) of a NumPy array or a torch tensor (None -> NULL)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {x.dtype}")
+        return ctypes.c_void_p(x.ctypes.data), ESP_HOST
+    # torch tensor (duck-typed to keep torch optional here)
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), (ESP_DEVICE if x.is_cuda else ESP_HOST)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x), None
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def esp_plan_opts_init() -> esp_plan_opts:
+    o = esp_plan_opts()
+    load_library().esp_plan_opts_init(ctypes.byref(o))
+    return o
+
+
+def make_opts(**kw) -> esp_plan_opts:
+    o = esp_plan_opts_init()
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(getattr(v, "cuda_stream", v))
+        setattr(o, k, v)
+    return o
+
+
+def esp_plan(L: float, N: int, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> int:
+    if opts is None:
+        opts = make_opts(**kw)
+    box = esp_box((ctypes.c_double * 3)(L, L, L))
+    out = _P()
+    _check(load_library().esp_plan(ctypes.byref(box), int(N), float(tolerance), ctypes.byref(opts),
+                                   ctypes.byref(out)))
+    return out.value
+
+
+def esp_plan_query(L: float, N: int, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> dict:
+    """Planner only (no GPU needed): the parameters esp_plan would choose."""
+    if opts is None:
+        opts = make_opts(**kw)
+    box = esp_box((ctypes.c_double * 3)(L, L, L))
+    p = esp_plan_params()
+    _check(load_library().esp_plan_query(ctypes.byref(box), int(N), float(tolerance), ctypes.byref(opts),
+                                         ctypes.byref(p)))
+    return p.as_dict()
+
+
+def esp_plan_info(plan: int) -> dict:
+    p = esp_plan_params()
+    _check(load_library().esp_plan_info(_P(plan), ctypes.byref(p)))
+    return p.as_dict()
+
+
+def esp_set_charges(plan: int, q, where: int | None = None):
+    ptr, w = _ptr(q)
+    f32 = str(getattr(q, "dtype", "")).endswith("float32")
+    fn = load_library().esp_set_charges_f32 if f32 else load_library().esp_set_charges
+    _check(fn(_P(plan), ptr, where if where is not None else w))
+
+
+def esp_set_positions(plan: int, xyz, where: int | None = None):
+    ptr, w = _ptr(xyz)
+    f32 = str(getattr(xyz, "dtype", "")).endswith("float32")
+    fn = load_library().esp_set_positions_f32 if f32 else load_library().esp_set_positions
+    _check(fn(_P(plan), ptr, where if where is not None else w))
+
+
+def esp_compute(plan: int, energy=None, forces=None, potential=None, where: int | None = None):
+    """Fill the given output buffers (NumPy float64 arrays, or torch tensors).
+
+    With NumPy outputs, ``energy`` may be a length-1 float64 array. Returns the
+    energy as a float when it was computed on the host.
+    """
+    ws = {w for _, w in (_ptr(energy), _ptr(forces), _ptr(potential)) if w is not None}
+    if where is None:
+        where = ws.pop() if len(ws) == 1 else ESP_HOST
+    f32 = any(str(getattr(a, "dtype", "")).endswith("float32") for a in (forces, potential) if a is not None)
+    e_ptr = _ptr(energy)[0]
+    fn = load_library().esp_compute_f32 if f32 else load_library().esp_compute
+    _check(fn(_P(plan), e_ptr, _ptr(forces)[0], _ptr(potential)[0], where))
+    if isinstance(energy, np.ndarray):
+        return float(energy[0])
+    return None
+
+
+def esp_synchronize(plan: int):
+    _check(load_library().esp_synchronize(_P(plan)))
+
+
+def esp_set_timing(plan: int, enable: bool = True):
+    _check(load_library().esp_set_timing(_P(plan), int(enable)))
+
+
+PHASES = ("ingest_sort", "spread", "fft_r2c", "scale", "fft_c2r", "gather", "near", "finalize", "total")
+
+
+def esp_phase_times(plan: int) -> dict:
+    buf = (ctypes.c_float * len(PHASES))()
+    _check(load_library().esp_phase_times(_P(plan), buf, len(PHASES)))
+    return dict(zip(PHASES, list(buf)))
+
+
+def esp_last_spectral_energy(plan: int) -> tuple[float, float]:
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().esp_last_spectral_energy(_P(plan), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def esp_destroy(plan: int):
+    _check(load_library().esp_destroy(_P(plan)))
+
+
+def esp_last_error() -> str:
+    msg = load_library().esp_last_error()
+    return msg.decode() if msg else ""
+
+
+def esp_version() -> str:
+    return load_library().esp_version().decode()
+
+
+class Plan:
+    """Owning handle: plan + host-side convenience (host arrays in, host arrays out)."""
+
+    def __init__(self, L: float, N: int, tolerance: float, **opts):
+        self.handle = esp_plan(L, N, tolerance, **opts)
+        self.N = int(N)
+
+    @property
+    def info(self) -> dict:
+        return esp_plan_info(self.handle)
+
+    def set_charges(self, q, where=None):
+        esp_set_charges(self.handle, q, where)
+
+    def set_positions(self, xyz, where=None):
+        esp_set_positions(self.handle, xyz, where)
+
+    def compute(self):
+        """Host arrays: returns (energy, forces (N,3), potential (N,))."""
+        e = np.zeros(1)
+        f = np.zeros((self.N, 3))
+        u = np.zeros(self.N)
+        esp_compute(self.handle, e, f, u, ESP_HOST)
+        return float(e[0]), f, u
+
+    def close(self):
+        if self.handle:
+            esp_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,111 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every entry point
+declared in include/*.h, validates its arguments, and its host planner makes
+the same parameter choices as the oracle's reading of the paper's rules."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+from oracle import params as oparams
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_09727_gb300 import _build, esp
+    _build.build()
+    return esp
+
+
+def declared_symbols():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(esp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert "esp_plan" in names and "esp_compute" in names and len(names) >= 15
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_version_and_opts(lib):
+    assert "sm_103a" in lib.esp_version()
+    o = lib.esp_plan_opts_init()
+    assert o.precision == lib.ESP_FP32 and o.kernel == lib.ESP_KERNEL_PSWF and o.prefactor == 1.0
+
+
+@pytest.mark.parametrize("L,N,eps,r_c", [
+    (14.413, 300_000, 1e-4, 1.0),       # water 1e5 molecules
+    (31.05, 3_000_000, 1e-5, 1.0),      # water 1e6 molecules
+    (20.0, 1000, 1e-4, 5.0),            # uniform +-1 charges
+    (8.0, 4096, 1e-4, 2.0),             # NaCl 8^3 cells
+    (3.912, 6000, 1e-3, 1.0),
+    (5.0, 300, 1e-5, 1.2),
+])
+def test_planner_matches_oracle_reading(lib, L, N, eps, r_c):
+    got = lib.esp_plan_query(L, N, eps, r_c=r_c)
+    want = oparams.plan(eps, L, r_c)
+    assert abs(got["c"] - want["c"]) < 1e-9 * want["c"]
+    assert got["P"] == want["P"]
+    assert got["n_f"] == want["n_f"]
+    assert abs(got["c1"] - want["c1"]) < 1e-9 * want["c1"]
+    assert abs(got["alias_estimate"] - want["alias"]) < 1e-6 * want["alias"]
+    assert got["h"] == pytest.approx(L / want["n_f"])
+    # cell list: edge >= r_c / 2, bricks divide the cell grid
+    assert L / got["n_cells"] >= r_c / 2
+    assert got["n_cells"] % got["brick_cells"] == 0
+    assert got["si_fit_error"] < 1e-8 and got["near_fit_error"] < 1e-7
+
+
+def test_planner_gaussian_split(lib):
+    got = lib.esp_plan_query(14.413, 300_000, 1e-4, r_c=1.0, kernel=lib.ESP_KERNEL_GAUSS)
+    want = oparams.plan(1e-4, 14.413, 1.0, kind="gauss")
+    assert got["n_f"] == want["n_f"] and abs(got["alpha"] - math.log(1e4)) < 1e-12
+
+
+def test_planner_fp64_fits_to_rounding(lib):
+    got = lib.esp_plan_query(20.0, 1000, 1e-10, r_c=5.0, precision=lib.ESP_FP64)
+    assert got["si_fit_error"] < 1e-13 and got["near_fit_error"] < 1e-13
+    assert got["P"] == oparams.stencil_width(1e-10)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(L=10.0, N=100, tol=1e-4, r_c=5.0), 2),       # r_c >= L/2
+    (dict(L=10.0, N=100, tol=0.5, r_c=1.0), 1),        # tolerance out of range
+    (dict(L=-1.0, N=100, tol=1e-4, r_c=1.0), 1),       # bad box
+    (dict(L=10.0, N=-5, tol=1e-4, r_c=1.0), 1),        # bad N
+    (dict(L=10.0, N=100, tol=1e-4, r_c=1.0, P=20), 10),  # P beyond compiled range
+    (dict(L=10.0, N=100, tol=1e-4, r_c=1.0, n_f=31), 1),  # odd grid
+])
+def test_invalid_arguments_rejected(lib, kw, status):
+    L, N, tol = kw.pop("L"), kw.pop("N"), kw.pop("tol")
+    with pytest.raises(lib.EspError) as exc:
+        lib.esp_plan_query(L, N, tol, **kw)
+    assert exc.value.status == status
+    assert lib.esp_last_error()
+
+
+def test_non_cubic_box_rejected(lib):
+    box = lib.esp_box((ctypes.c_double * 3)(10.0, 10.0, 11.0))
+    p = lib.esp_plan_params()
+    o = lib.esp_plan_opts_init()
+    st = lib.load_library().esp_plan_query(ctypes.byref(box), 10, 1e-4, ctypes.byref(o), ctypes.byref(p))
+    assert st == 1 and "cubic" in lib.esp_last_error()
+
+
+def test_null_arguments(lib):
+    so = lib.load_library()
+    assert so.esp_plan_query(None, 10, 1e-4, None, None) == 1
+    assert so.esp_destroy(None) == 0
+    assert so.esp_plan_info(None, None) == 1
