@@ -73,11 +73,13 @@ def default_params(eps: float, L: float, r_c: float, kind: str = "pswf",
 def stencil(pos, L, n_f, window):
     """Per-axis stencil of every particle: grid indices, weights, d(weight)/dx.
 
-    Grid coordinate t = x/h; the P points l0 .. l0+P-1 with l0 = ceil(t - P/2)
-    carry weights phi(t - l); derivatives are phi'(t - l)/h.
+    Grid coordinate t = x/h, evaluated as (x/L) n_f; the P points
+    l0 .. l0+P-1 with l0 = ceil(t - P/2) carry weights phi(t - l); derivatives
+    are phi'(t - l)/h. (At the measure-zero tie t - P/2 in Z the end point is
+    left out; evaluating t as (x/L) n_f fixes how rounding decides that tie.)
     """
     h = L / n_f
-    t = np.mod(np.asarray(pos, dtype=np.float64), L) / h
+    t = (np.mod(np.asarray(pos, dtype=np.float64), L) / L) * n_f
     P = window.P
     l0 = np.ceil(t - 0.5 * P).astype(np.int64)
     l = l0[:, :, None] + np.arange(P)[None, None, :]          # (N,3,P)

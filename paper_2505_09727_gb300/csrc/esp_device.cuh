@@ -97,9 +97,11 @@ __host__ __device__ inline int tile_last_fixed(int cb_end, int n_c, int n_f, int
   return l0;
 }
 
-// FP64 mode keeps wrapped FP64 coordinates.
-__host__ __device__ inline int stencil_origin_f64(double x, double inv_h, int P, double& delta) {
-  double t = x * inv_h;
+// FP64 mode keeps wrapped FP64 coordinates; the grid coordinate is computed as
+// t = (x / L) n_f (IEEE division, then product) so that the measure-zero tie
+// t - P/2 in Z is decided by the same rounding as in the FP64 reference.
+__host__ __device__ inline int stencil_origin_f64(double x, double L, int n_f, int P, double& delta) {
+  double t = (x / L) * (double)n_f;
   double l0 = ceil(t - 0.5 * P);
   delta = t - l0 - 0.5 * P + 1.0;
   return (int)l0;

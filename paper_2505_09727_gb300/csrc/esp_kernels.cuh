@@ -61,7 +61,7 @@ __device__ inline int tile_origin(const SysDesc& S, int cbrick, int P, float) {
 __device__ inline int tile_origin(const SysDesc& S, int cbrick, int P, double) {
   double d;
   double x = (double)(cbrick * S.bc) * S.L / S.n_c;
-  return stencil_origin_f64(x, S.inv_h, P, d) - 1;   // one-point margin for FP64 rounding
+  return stencil_origin_f64(x, S.L, S.n_f, P, d) - 1;   // one-point margin for FP64 rounding
 }
 
 // Stencil of one coordinate: origin l0 and y = 2 delta - 1.
@@ -73,7 +73,7 @@ __device__ inline int stencil(const SysDesc& S, uint32_t u, int P, float& y) {
 }
 __device__ inline int stencil(const SysDesc& S, double x, int P, double& y) {
   double delta;
-  int l0 = stencil_origin_f64(x, S.inv_h, P, delta);
+  int l0 = stencil_origin_f64(x, S.L, S.n_f, P, delta);
   y = 2.0 * delta - 1.0;
   return l0;
 }
@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
     uint32_t u[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double f = p[a] * S.inv_L;
-      f -= floor(f);
-      if (!(f < 1.0) || f < 0.0) f = 0.0;
+      double f = p[a] / S.L;
+      if (!(f >= 0.0 && f < 1.0)) {
+        f -= floor(f);
+        if (!(f < 1.0) || f < 0.0) f = 0.0;
+      }
       u[a] = (uint32_t)(f * 4294967296.0);
       c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
     }
@@ -154,8 +156,11 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
     double w[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double x = p[a] - S.L * floor(p[a] * S.inv_L);
-      if (!(x < S.L) || x < 0.0) x = 0.0;
+      double x = p[a];
+      if (!(x >= 0.0 && x < S.L)) {
+        x = x - S.L * floor(x / S.L);
+        if (!(x < S.L) || x < 0.0) x = 0.0;
+      }
       w[a] = x;
       c[a] = cell_f64(x, S);
     }

@@ -114,8 +114,8 @@ static int tile_edge(const espk::SysDesc& d, int P, int precision) {
           espk::tile_origin_fixed(cb * d.bc, d.n_c, d.n_f, P) + P;
     } else {
       double dl;
-      const int lo = espk::stencil_origin_f64((double)(cb * d.bc) * d.L / d.n_c, d.inv_h, P, dl);
-      const int hi = espk::stencil_origin_f64((double)((cb + 1) * d.bc) * d.L / d.n_c, d.inv_h, P, dl);
+      const int lo = espk::stencil_origin_f64((double)(cb * d.bc) * d.L / d.n_c, d.L, d.n_f, P, dl);
+      const int hi = espk::stencil_origin_f64((double)((cb + 1) * d.bc) * d.L / d.n_c, d.L, d.n_f, P, dl);
       t = hi - lo + P + 2;
     }
     T = std::max(T, t);

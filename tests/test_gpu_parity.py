@@ -64,13 +64,22 @@ CASES = {
 }
 
 
+def force_error(s, f, f_ref):
+    """Relative RMS force error; for lattices whose forces vanish by symmetry
+    the denominator is the nearest-neighbour pair force 1/(4 pi d^2) instead."""
+    if s.name.startswith("nacl"):
+        scale = 1.0 / (4 * np.pi * 0.25)
+        return float(np.sqrt(np.mean(np.sum((f - f_ref) ** 2, axis=1)))) / scale
+    return metrics.relative_rms_force_error(f, f_ref)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_matches_oracle(esp, name):
     make, eps, r_c = CASES[name]
     s = make()
     g = gpu_solve(esp, s, eps, r_c=r_c, precision=esp.ESP_FP64)
     ref = oracle_same(s, eps, g["info"])
-    assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= 1e-9
+    assert force_error(s, g["forces"], ref["forces"]) <= 1e-9
     assert abs(g["energy"] - ref["energy"]) <= 1e-10 * abs(ref["energy"])
     assert rel_rms(g["potential"], ref["potential"]) <= 1e-9
     # discrete energy identity 1/2 sum q u~ = 1/2 sum p |bh|^2
@@ -84,7 +93,7 @@ def test_fp32_matches_oracle(esp, name):
     s = make()
     g = gpu_solve(esp, s, eps, r_c=r_c, precision=esp.ESP_FP32)
     ref = oracle_same(s, eps, g["info"])
-    assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= FP32_PARITY
+    assert force_error(s, g["forces"], ref["forces"]) <= FP32_PARITY
     assert abs(g["energy"] - ref["energy"]) <= FP32_PARITY * abs(ref["energy"])
     assert rel_rms(g["potential"], ref["potential"]) <= FP32_PARITY
 
@@ -195,8 +204,10 @@ def test_device_pointer_path_matches_host_path(esp):
     finally:
         esp.esp_destroy(h)
     torch.cuda.synchronize()
-    assert np.array_equal(f.cpu().numpy(), host["forces"])
-    assert float(e.cpu()[0]) == host["energy"]
+    # same arithmetic; only the order of floating-point atomics differs
+    assert metrics.relative_rms_force_error(f.cpu().numpy(), host["forces"]) <= 1e-6
+    assert abs(float(e.cpu()[0]) - host["energy"]) <= 1e-6 * abs(host["energy"])
+    assert rel_rms(u.cpu().numpy(), host["potential"]) <= 1e-6
     # float32 inputs and outputs
     h = esp.esp_plan(s.L, s.n, 1e-4, r_c=1.0, stream=stream.cuda_stream)
     try:
