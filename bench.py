@@ -170,7 +170,11 @@ def run_gpu(args, world, rank, local):
     dev = torch.device("cuda", local)
     s = inputs.spce_water(args.molecules, seed=WORKLOAD["seed"])
     N, L = s.n, s.L
-    stream = torch.cuda.current_stream(dev)
+    # one explicit stream for the plan, the tensors and the timing events
+    # (torch's default stream is the legacy NULL stream, which the plan does
+    # not adopt)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     h = esp.esp_plan(L, N, WORKLOAD["tolerance"], r_c=WORKLOAD["r_c_nm"], device=local,
                      stream=stream.cuda_stream)
     info = esp.esp_plan_info(h)

@@ -189,7 +189,8 @@ def test_device_pointer_path_matches_host_path(esp):
     s = inputs.spce_water(2000, seed=8)
     host = gpu_solve(esp, s, 1e-4, r_c=1.0)
     dev = torch.device("cuda:0")
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     q = torch.tensor(s.q, device=dev)
     x = torch.tensor(s.pos, device=dev)
     e = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -219,6 +220,8 @@ def test_device_pointer_path_matches_host_path(esp):
         esp.esp_synchronize(h)
     finally:
         esp.esp_destroy(h)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(torch.cuda.default_stream(dev))
     assert metrics.relative_rms_force_error(f32.double().cpu().numpy(), host["forces"]) <= 1e-5
 
 
