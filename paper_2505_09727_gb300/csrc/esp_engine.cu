@@ -67,6 +67,7 @@ struct esp_plan_s {
   double Q = 0, Q2 = 0;
   bool have_q = false, have_pos = false;
   bool timing = false;
+  int timing_mode = 0;          // 1: events, 2: events with serialised phases
   bool own_stream = false;
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -350,9 +351,14 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
   // A1b: scatter into cell order
   ESP_CU(L::scatter(p->d_desc, p->d_chunks, p->n_chunks, p->d_coord, p->d_key, p->d_rank, p->d_start,
                     (const real*)p->d_q, p->d_atoms, p->d_perm, st));
-  // fork: local part on the second stream
-  ESP_CU(cudaEventRecord(p->ev_fork, st));
-  ESP_CU(cudaStreamWaitEvent(st2, p->ev_fork, 0));
+  // fork: local part on the second stream (on the main stream when timing
+  // mode 2 serialises the phases so each kernel is timed alone)
+  const bool serial = p->timing_mode == 2;
+  if (serial) st2 = st;
+  else {
+    ESP_CU(cudaEventRecord(p->ev_fork, st));
+    ESP_CU(cudaStreamWaitEvent(st2, p->ev_fork, 0));
+  }
   rec(p, 9, st2);
   const espk::NearCoef<real>& nc = *reinterpret_cast<const espk::NearCoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.nc32 : (const void*)&hp.nc64);
@@ -360,7 +366,7 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
       sizeof(real) == 4 ? (const void*)&hp.si32 : (const void*)&hp.si64);
   ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_start, p->d_near, nc, st2));
   rec(p, 10, st2);
-  ESP_CU(cudaEventRecord(p->ev_join, st2));
+  if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
 
   // spectral part
   rec(p, 3, st);
@@ -384,7 +390,7 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
                    (const real*)p->d_grid, p->d_far, si, p->d_err, st));
   rec(p, 8, st);
   // join and finish
-  ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
+  if (!serial) ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
   ESP_CU(L::finalize(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_perm, p->d_far, p->d_near,
                      outF, outU, out_double, p->d_partials, st));
   ESP_CU(espk::launch_energy(p->d_desc, 1, p->d_fourier, p->n_fourier_blocks, p->d_partials,
@@ -567,6 +573,7 @@ esp_status esp_synchronize(esp_plan_t p) {
 esp_status esp_set_timing(esp_plan_t p, int enable) {
   if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL plan");
   p->timing = enable != 0;
+  p->timing_mode = enable;
   return ESP_OK;
 }
 

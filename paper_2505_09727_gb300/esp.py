@@ -211,7 +211,8 @@ def esp_synchronize(plan: int):
     _check(load_library().esp_synchronize(_P(plan)))
 
 
-def esp_set_timing(plan: int, enable: bool = True):
+def esp_set_timing(plan: int, enable: int = 1):
+    """0 off, 1 events around the phases, 2 events with the phases serialised."""
     _check(load_library().esp_set_timing(_P(plan), int(enable)))
 
 
