@@ -170,6 +170,40 @@ esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* 
 
 esp_status esp_destroy(esp_plan_t plan);
 
+/* Local part without device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (code running
+ * while a framework's caching allocator owns the device heap, inside regions
+ * where an allocation would synchronise the device, or under a fixed device
+ * memory budget).
+ *
+ * For N charges q[N] at xyz[N*3] (both FP64, in device memory of
+ * opts->device) it computes what esp_compute returns minus the spectral part:
+ * the local part of Eq. localpart within r_c, the self term and, when
+ * sum q != 0 and allow_background is set, the neutralising background:
+ *   potential[i] = u^l_i - q_i chi(0)/(4 pi r_c) + background,
+ *   forces[i]    = F^l_i,
+ *   *energy      = 1/2 sum q_i u^l_i + E_self + E_bg,
+ * all FP64 in device memory (any of them may be NULL). opts selects the
+ * split, precision, cutoff r_c (required here: 0 picks the planner's cost
+ * model) and stream (NULL = the legacy default stream); the grid options are
+ * ignored.
+ *
+ * Working memory comes from one 6 MiB array in the library's device image,
+ * which every GPU that loads the library holds until the process exits:
+ * about 65k atoms in FP32 mode and 32k in FP64 mode fit; larger systems are
+ * rejected with ESP_ERR_UNSUPPORTED before any device work. The first call
+ * on a device looks up the array's address with that device current; make
+ * that first call before any stream capture. The call reads the charges back
+ * to the host (a synchronising copy) and then enqueues its kernels on the
+ * stream without waiting for them. Every call shares the array, and each
+ * call clears what it reads before writing it; calls whose device work
+ * overlaps (on different streams or host threads) race on the array and
+ * must be serialised by the caller. */
+esp_status esp_local_part_static(const esp_box* box, int64_t N, double tolerance,
+                                 const esp_plan_opts* opts, const double* xyz,
+                                 const double* q, double* energy, double* forces,
+                                 double* potential);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* esp_last_error(void);
 

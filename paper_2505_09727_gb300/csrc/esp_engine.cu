@@ -54,6 +54,10 @@ constexpr int kPhases = 9;
 
 }  // namespace
 
+namespace espe {
+void set_last_error(const std::string& msg) { g_error = msg; }
+}  // namespace espe
+
 struct esp_plan_s {
   espe::HostPlan hp;
   int prec = ESP_FP32;

@@ -32,6 +32,9 @@ struct HostPlan {
 esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts& opts, HostPlan& hp,
                           std::string& msg);
 
+// Message reported by esp_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
+
 // Constants that depend on the charges (self energy, background).
 void charge_constants(const HostPlan& hp, double Q, double Q2, double* e_self, double* e_bg,
                       double* bg_shift);

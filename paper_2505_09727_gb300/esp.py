@@ -84,6 +84,8 @@ _SIGNATURES = {
     "esp_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "esp_last_spectral_energy": (ctypes.c_int, [_P, _D, _D]),
     "esp_destroy": (ctypes.c_int, [_P]),
+    "esp_local_part_static": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
+                                             ctypes.POINTER(esp_plan_opts), _P, _P, _P, _P, _P]),
     "esp_last_error": (ctypes.c_char_p, []),
     "esp_version": (ctypes.c_char_p, []),
 }
@@ -233,6 +235,21 @@ def esp_last_spectral_energy(plan: int) -> tuple[float, float]:
 
 def esp_destroy(plan: int):
     _check(load_library().esp_destroy(_P(plan)))
+
+
+def esp_local_part_static(L: float, N: int, tolerance: float, xyz, q, energy=None, forces=None,
+                          potential=None, opts: esp_plan_opts | None = None, **kw):
+    """Local part, self term and background without device allocation.
+
+    xyz, q and the outputs are FP64 device buffers (torch CUDA tensors or raw
+    device pointers); the work is enqueued on opts.stream.
+    """
+    if opts is None:
+        opts = make_opts(**kw)
+    box = esp_box((ctypes.c_double * 3)(L, L, L))
+    _check(load_library().esp_local_part_static(
+        ctypes.byref(box), int(N), float(tolerance), ctypes.byref(opts), _ptr(xyz)[0], _ptr(q)[0],
+        _ptr(energy)[0], _ptr(forces)[0], _ptr(potential)[0]))
 
 
 def esp_last_error() -> str:
