@@ -33,14 +33,23 @@ constexpr int kChunk = 256;   // atoms per chunk = threads of a per-atom block
 
 // Polynomial degrees (coefficient counts) per precision.
 template <typename real> struct Deg;
-template <> struct Deg<float> { static constexpr int si = 10; static constexpr int nr = 16; };
-template <> struct Deg<double> { static constexpr int si = 18; static constexpr int nr = 28; };
+template <> struct Deg<float> { static constexpr int si = 10; static constexpr int nr = 12; };
+template <> struct Deg<double> { static constexpr int si = 18; static constexpr int nr = 24; };
+
+// Each cell-list cell is split into kSub slabs along z; atoms are sorted by
+// (cell, slab), so the local part reads only the slabs a cutoff sphere meets.
+constexpr int kSub = 4;
 
 // SI kernel: P pieces, piece a gives the weight of grid point l0 + a as a
 // polynomial in y = 2 delta - 1, delta = t - l0 - (P/2 - 1) in (0, 1].
 template <typename real> struct SICoef { real c[kMaxP][Deg<real>::si]; };
-// Local part: 1 - g(x) and chi(x) as polynomials in y = 2x - 1, x = r / r_c.
-template <typename real> struct NearCoef { real e[Deg<real>::nr]; real chi[Deg<real>::nr]; };
+// Local part L(r) = (1 - g(r/r_c)) / (4 pi r) written as bare Coulomb minus a
+// smooth correction. With x = r/r_c and s = x^2 (g is odd and chi even, so
+// both corrections are even in x, i.e. polynomials in s):
+//   4 pi L(r)          = 1/r - H(s)/r_c,          H(s) = g(x)/x,
+//   -4 pi L'(r) / r    = 1/r^3 + K(s)/r_c^3,      K(s) = (x chi(x) - g(x))/x^3,
+// both as polynomials in y = 2 s - 1.
+template <typename real> struct NearCoef { real h[Deg<real>::nr]; real k[Deg<real>::nr]; };
 
 // Per-system geometry and constants (same record on host and device).
 struct SysDesc {
@@ -54,11 +63,13 @@ struct SysDesc {
   int pad0;
   long long atom0;   // first atom of the system in the pooled atom arrays
   long long cell0;   // first entry of the system in the pooled count/start arrays
+                     // (arrays indexed by cell key * kSub + slab)
   long long grid0;   // first element of the system's real grid
   long long spec0;   // first element of the system's half spectrum
   long long tab0;    // first element of the system's G table (w follows G)
   double L, inv_L, h, inv_h;
-  double r_c, rc2, inv_rc;
+  double r_c, rc2, inv_rc, inv_rc2, inv_rc3;
+  double w;          // cell edge L / n_c
   double fix_scale;  // L / 2^32
   double self_coef;  // chi(0) / (4 pi r_c)
   double bg_shift;   // -(Q/V) (r_c^2/2) int_0^1 x^2 chi

@@ -87,7 +87,9 @@ struct esp_plan_s {
   uint32_t* d_rank = nullptr;
   uint32_t* d_count = nullptr;
   uint32_t* d_start = nullptr;
+  uint32_t* d_tiles = nullptr;   // scan tile totals
   void* d_atoms = nullptr;
+  void* d_rel = nullptr;         // cell-relative coordinates + charge (local part)
   uint32_t* d_perm = nullptr;
   void* d_q = nullptr;
   void* d_qstage = nullptr;    // staging for host charges (FP64)
@@ -215,8 +217,10 @@ esp_status build_buffers(esp_plan_s* p) {
   ESP_TRY(dev_alloc(p, &p->d_coord, (size_t)N * L::atom_bytes()));
   ESP_TRY(dev_alloc_t(p, &p->d_key, N));
   ESP_TRY(dev_alloc_t(p, &p->d_rank, N));
-  ESP_TRY(dev_alloc_t(p, &p->d_count, hp.n_cells3));
-  ESP_TRY(dev_alloc_t(p, &p->d_start, hp.n_cells3 + 1));
+  ESP_TRY(dev_alloc_t(p, &p->d_count, hp.n_keys));
+  ESP_TRY(dev_alloc_t(p, &p->d_start, hp.n_keys + 1));
+  ESP_TRY(dev_alloc_t(p, &p->d_tiles, espk::scan_tiles(hp.n_keys)));
+  ESP_TRY(dev_alloc(p, &p->d_rel, (size_t)N * L::res_bytes()));
   ESP_TRY(dev_alloc(p, &p->d_atoms, (size_t)N * L::atom_bytes()));
   ESP_TRY(dev_alloc_t(p, &p->d_perm, N));
   ESP_TRY(dev_alloc(p, &p->d_q, (size_t)N * rb));
@@ -321,10 +325,10 @@ esp_status do_set_positions(esp_plan_s* p, const void* xyz, bool is_double, int 
                            cudaMemcpyHostToDevice, p->st));
     src = p->d_pos;
   }
-  ESP_CU(cudaMemsetAsync(p->d_count, 0, p->hp.n_cells3 * sizeof(uint32_t), p->st));
+  ESP_CU(cudaMemsetAsync(p->d_count, 0, p->hp.n_keys * sizeof(uint32_t), p->st));
   ESP_CU(L::ingest(p->d_desc, p->d_chunks, p->n_chunks, src, src_double, p->d_coord, p->d_key,
                    p->d_rank, p->d_count, p->d_err, p->st));
-  ESP_CU(espk::launch_scan(p->d_count, p->d_start, p->hp.n_cells3, p->st));
+  ESP_CU(espk::launch_scan(p->d_count, p->d_start, p->d_tiles, p->hp.n_keys, p->st));
   rec(p, 1, p->st);
   p->have_pos = true;
   if (where == ESP_HOST) return wait_stream(p, p->st);
@@ -354,7 +358,7 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
   rec(p, 2, st);
   // A1b: scatter into cell order
   ESP_CU(L::scatter(p->d_desc, p->d_chunks, p->n_chunks, p->d_coord, p->d_key, p->d_rank, p->d_start,
-                    (const real*)p->d_q, p->d_atoms, p->d_perm, st));
+                    (const real*)p->d_q, p->d_atoms, p->d_rel, p->d_perm, st));
   // fork: local part on the second stream (on the main stream when timing
   // mode 2 serialises the phases so each kernel is timed alone)
   const bool serial = p->timing_mode == 2;
@@ -368,7 +372,8 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
       sizeof(real) == 4 ? (const void*)&hp.nc32 : (const void*)&hp.nc64);
   const espk::SICoef<real>& si = *reinterpret_cast<const espk::SICoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.si32 : (const void*)&hp.si64);
-  ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_start, p->d_near, nc, st2));
+  ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
+                 st2));
   rec(p, 10, st2);
   if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
 
@@ -507,7 +512,7 @@ esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const
   const size_t rb = o.precision == ESP_FP32 ? 4 : 8;
   const size_t ab = o.precision == ESP_FP32 ? 16 : 32;
   size_t bytes = (size_t)N * (24 + 2 * ab + 4 * 3 + rb + 8 + 2 * ab + 32) +
-                 (size_t)hp.n_cells3 * 8 + (size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb +
+                 (size_t)hp.n_keys * 8 + (size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb +
                  (hp.G.size() + hp.W.size()) * rb;
   hp.info.device_bytes = bytes;
   *out = hp.info;

@@ -43,11 +43,12 @@ template <>
 cudaError_t Launch<ESP_REAL>::scatter(const SysDesc* sys, const int2* chunks, int n_chunks,
                                       const void* coord, const uint32_t* key, const uint32_t* rank,
                                       const uint32_t* start, const ESP_REAL* q, void* atoms,
-                                      uint32_t* perm, cudaStream_t st) {
+                                      void* rel, uint32_t* perm, cudaStream_t st) {
   using A = typename Types<ESP_REAL>::atom;
+  using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
   k_scatter<ESP_REAL, ESP_REAL><<<n_chunks, kChunk, 0, st>>>(sys, chunks, (const A*)coord, key, rank,
-                                                             start, q, (A*)atoms, perm);
+                                                             start, q, (A*)atoms, (R*)rel, perm);
   return cudaGetLastError();
 }
 
@@ -117,12 +118,13 @@ cudaError_t Launch<ESP_REAL>::scale(const SysDesc* sys, int nsys, int nblk, void
 
 template <>
 cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n_chunks,
-                                   const void* atoms, const uint32_t* start, void* nearres,
-                                   const NearCoef<ESP_REAL>& nc, cudaStream_t st) {
+                                   const void* atoms, const void* rel, const uint32_t* start,
+                                   void* nearres, const NearCoef<ESP_REAL>& nc, cudaStream_t st) {
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
-  k_near<ESP_REAL><<<n_chunks, kChunk, 0, st>>>(sys, chunks, (const A*)atoms, start, (R*)nearres, nc);
+  k_near<ESP_REAL><<<n_chunks, kChunk, 0, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start,
+                                                (R*)nearres, nc);
   return cudaGetLastError();
 }
 

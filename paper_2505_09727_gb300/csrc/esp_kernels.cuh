@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
     p[0] = p[1] = p[2] = 0.0;
   }
   int c[3];
+  int slab;
   typename Types<real>::atom out;
   if constexpr (sizeof(real) == 4) {
     uint32_t u[3];
@@ -151,6 +152,9 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
       u[a] = (uint32_t)(f * 4294967296.0);
       c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
     }
+    // slab: fractional position inside the z cell, in kSub parts
+    const uint32_t zfrac = (uint32_t)((uint64_t)u[2] * (uint64_t)S.n_c);
+    slab = (int)(((uint64_t)zfrac * kSub) >> 32);
     out = make_uint4(u[0], u[1], u[2], 0u);
   } else {
     double w[3];
@@ -164,57 +168,115 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
       w[a] = x;
       c[a] = cell_f64(x, S);
     }
+    slab = (int)((w[2] - c[2] * S.w) / S.w * kSub);
+    slab = slab < 0 ? 0 : (slab >= kSub ? kSub - 1 : slab);
     out = make_dquad(w[0], w[1], w[2], 0.0);
   }
-  const uint32_t k = (uint32_t)cell_key(S, c[0], c[1], c[2]);
+  const uint32_t k = (uint32_t)(cell_key(S, c[0], c[1], c[2]) * kSub + slab);
   coord[i] = out;
   key[i] = k;
   rank[i] = atomicAdd(&count[S.cell0 + k], 1u);
 }
 
-// A1a: exclusive scan of the pooled cell counts (one block of 1024 threads).
-static __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ count,
-                                               uint32_t* __restrict__ start, long long n) {
-  __shared__ uint32_t wsum[32];
-  const long long per = (n + blockDim.x - 1) / blockDim.x;
-  const long long b = per * threadIdx.x;
-  const long long e = b + per < n ? b + per : n;
-  uint32_t s = 0;
-  for (long long j = b; j < e; ++j) s += count[j];
-  // block exclusive scan of s
+// A1a: exclusive scan of the pooled cell-list counts in three passes: each
+// block scans kScanTile entries and records its total; one block scans the
+// totals; every block adds its offset. start[n] receives the grand total.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t* wsum, uint32_t* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t incl = s;
+  uint32_t incl = v;
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
   if (lane == 31) wsum[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    uint32_t v = wsum[lane];
-    uint32_t vi = v;
+    const uint32_t x = wsum[lane];
+    uint32_t xi = x;
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(0xffffffffu, vi, o);
-      if (lane >= o) vi += t;
+      const uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
     }
-    wsum[lane] = vi - v;
+    wsum[lane] = xi - x;
+    if (lane == 31) wsum[32] = xi;
   }
   __syncthreads();
-  uint32_t run = wsum[wid] + incl - s;
-  for (long long j = b; j < e; ++j) {
-    start[j] = run;
-    run += count[j];
+  const uint32_t r = wsum[wid] + incl - v;
+  if (total) *total = wsum[32];
+  __syncthreads();
+  return r;
+}
+
+static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
+    const uint32_t* __restrict__ count, uint32_t* __restrict__ start, uint32_t* __restrict__ tile_sum,
+    long long n) {
+  __shared__ uint32_t wsum[33];
+  const long long b = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+  uint32_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = (b + k < n) ? count[b + k] : 0u;
+    s += v[k];
   }
-  if (threadIdx.x == blockDim.x - 1) start[n] = run;
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, wsum, &total);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (b + k < n) start[b + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+static __global__ void __launch_bounds__(kScanThreads) k_scan_totals(
+    uint32_t* __restrict__ tile_sum, int n_tiles, uint32_t* __restrict__ start, long long n) {
+  __shared__ uint32_t wsum[33];
+  const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
+  const int b = per * threadIdx.x;
+  const int e = b + per < n_tiles ? b + per : n_tiles;
+  uint32_t s = 0;
+  for (int j = b; j < e; ++j) s += tile_sum[j];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, wsum, &total);
+  for (int j = b; j < e; ++j) {
+    const uint32_t t = tile_sum[j];
+    tile_sum[j] = run;
+    run += t;
+  }
+  if (threadIdx.x == 0) start[n] = total;
+}
+
+static __global__ void __launch_bounds__(kScanThreads) k_scan_add(
+    uint32_t* __restrict__ start, const uint32_t* __restrict__ tile_sum, long long n) {
+  const uint32_t off = tile_sum[blockIdx.x];
+  const long long b = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k)
+    if (b + k < n) start[b + k] += off;
 }
 
 // A1b: counting-sort scatter. perm[sorted] = pooled caller index.
+// Position of a coordinate relative to the lower face of its cell.
+__device__ inline float cell_relative(const SysDesc& S, uint32_t u) {
+  const uint32_t frac = (uint32_t)((uint64_t)u * (uint64_t)S.n_c);   // fraction of the cell
+  return (float)((double)frac * 2.3283064365386962890625e-10 * S.w);
+}
+__device__ inline double cell_relative(const SysDesc& S, double x) {
+  const int c = cell_f64(x, S);
+  return x - c * S.w;
+}
+
 template <typename real, typename Q>
 __global__ void __launch_bounds__(kChunk) k_scatter(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
     const typename Types<real>::atom* __restrict__ coord, const uint32_t* __restrict__ key,
     const uint32_t* __restrict__ rank, const uint32_t* __restrict__ start, const Q* __restrict__ q,
-    typename Types<real>::atom* __restrict__ atoms, uint32_t* __restrict__ perm) {
+    typename Types<real>::atom* __restrict__ atoms, typename Types<real>::res* __restrict__ rel,
+    uint32_t* __restrict__ perm) {
   const int2 ch = chunks[blockIdx.x];
   const SysDesc& S = sys[ch.x];
   const int local = ch.y + threadIdx.x;
@@ -222,9 +284,15 @@ __global__ void __launch_bounds__(kChunk) k_scatter(
   const long long i = S.atom0 + local;
   const uint32_t dst = start[S.cell0 + key[i]] + rank[i];
   typename Types<real>::atom a = coord[i];
+  typename Types<real>::res r;
+  r.x = cell_relative(S, a.x);
+  r.y = cell_relative(S, a.y);
+  r.z = cell_relative(S, a.z);
+  r.w = (real)q[i];
   if constexpr (sizeof(real) == 4) a.w = __float_as_uint((float)q[i]);
   else a.w = (double)q[i];
   atoms[dst] = a;
+  rel[dst] = r;
   perm[dst] = (uint32_t)i;
 }
 
@@ -246,8 +314,8 @@ __global__ void __launch_bounds__(256) k_spread(
   const int T3 = T * T * T;
   for (int j = threadIdx.x; j < T3; j += blockDim.x) tile[j] = real(0);
   __syncthreads();
-  const long long k0 = S.cell0 + (long long)b * bc * bc * bc;
-  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc];
+  const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
+  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
   for (uint32_t i = a_begin + threadIdx.x; i < a_end; i += blockDim.x) {
     const typename Types<real>::atom at = atoms[i];
     real yx, yy, yz;
@@ -348,8 +416,8 @@ __global__ void __launch_bounds__(256) k_gather(
     tile[j] = __ldg(grid + ((long long)gz * n_f + gy) * n_f + gx);
   }
   __syncthreads();
-  const long long k0 = S.cell0 + (long long)b * bc * bc * bc;
-  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc];
+  const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
+  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
   const real inv_h = (real)S.inv_h;
   for (uint32_t i = a_begin + threadIdx.x; i < a_end; i += blockDim.x) {
     const typename Types<real>::atom at = atoms[i];
@@ -400,8 +468,13 @@ __global__ void __launch_bounds__(256) k_gather(
   }
 }
 
-// A7: local part (Eq. localpart). One thread per sorted atom; the 5^3 cells
-// around its cell (edge >= r_c/2) cover every neighbour within r_c.
+// A7: local part (Eq. localpart). One thread per sorted atom i. The atoms
+// within r_c of i lie in the 5^3 cells around its cell (edge w >= r_c/2). For
+// every neighbouring column the lane computes the xy gap to it; a column no
+// closer than r_c is skipped, otherwise only the z slabs that the cutoff
+// sphere can reach in that column are read. Coordinates are relative to each
+// atom's cell, so a neighbour cell at offset o sits at o*w in i's frame (this
+// also covers periodic images when n_c < 5).
 template <typename real>
 __device__ __forceinline__ real horner(const real* c, real y) {
   constexpr int NC = Deg<real>::nr;
@@ -411,71 +484,100 @@ __device__ __forceinline__ real horner(const real* c, real y) {
   return v;
 }
 
-__device__ inline void pair_delta(const SysDesc& S, const uint4& a, const uint4& b, float scale,
-                                  float& dx, float& dy, float& dz) {
-  dx = (float)(int)(a.x - b.x) * scale;    // int32 wrap = minimum image
-  dy = (float)(int)(a.y - b.y) * scale;
-  dz = (float)(int)(a.z - b.z) * scale;
-}
-__device__ inline void pair_delta(const SysDesc& S, const dquad& a, const dquad& b, double,
-                                  double& dx, double& dy, double& dz) {
-  dx = a.x - b.x; dx -= S.L * rint(dx * S.inv_L);
-  dy = a.y - b.y; dy -= S.L * rint(dy * S.inv_L);
-  dz = a.z - b.z; dz -= S.L * rint(dz * S.inv_L);
-}
-
 __device__ inline float rsqrt_real(float x) { return rsqrtf(x); }
 __device__ inline double rsqrt_real(double x) { return 1.0 / sqrt(x); }
+__device__ inline float sqrt_real(float x) { return sqrtf(x); }
+__device__ inline double sqrt_real(double x) { return sqrt(x); }
+
+// c + o wrapped into [0, n) for |o| <= 2 and any n >= 1.
+__device__ inline int wrap2(int v, int n) {
+  v += v < 0 ? n : 0;
+  v += v < 0 ? n : 0;
+  v -= v >= n ? n : 0;
+  v -= v >= n ? n : 0;
+  return v;
+}
+
+constexpr int kMaxCellsAxis = 2048;
 
 template <typename real>
 __global__ void __launch_bounds__(kChunk) k_near(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
-    const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ start,
+    const typename Types<real>::atom* __restrict__ atoms,
+    const typename Types<real>::res* __restrict__ rel, const uint32_t* __restrict__ start,
     typename Types<real>::res* __restrict__ nearres, const NearCoef<real> nc) {
+  // per-axis parts of the brick-major cell key: key = kx[cx] + ky[cy] + kz[cz]
+  __shared__ int ktab[3][kMaxCellsAxis];
   const int2 ch = chunks[blockIdx.x];
   const SysDesc& S = sys[ch.x];
+  const int n_c = S.n_c, bc = S.bc, nb = S.nb;
+  const bool tab = n_c <= kMaxCellsAxis;
+  if (tab) {
+    for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
+      const int bq = c / bc, l = c - bq * bc;
+      ktab[0][c] = bq * bc * bc * bc + l;
+      ktab[1][c] = bq * nb * bc * bc * bc + l * bc;
+      ktab[2][c] = bq * nb * nb * bc * bc * bc + l * bc * bc;
+    }
+  }
+  __syncthreads();
   const int local = ch.y + threadIdx.x;
   if (local >= S.n_atoms) return;
   const long long i = S.atom0 + local;
-  const typename Types<real>::atom ai = atoms[i];
   int cx, cy, cz;
-  atom_cell(S, ai, cx, cy, cz);
-  const int n_c = S.n_c;
-  const int span = n_c < 5 ? n_c : 5;
-  const real scale = (real)S.fix_scale;
+  atom_cell(S, atoms[i], cx, cy, cz);
+  const typename Types<real>::res ri = rel[i];
+  const real w = (real)S.w;
   const real rc2 = (real)S.rc2, inv_rc = (real)S.inv_rc;
+  const real inv_rc2x2 = real(2) * (real)S.inv_rc2, inv_rc3 = (real)S.inv_rc3;
+  const real slab_per_len = real(kSub) / w;
+  const real margin = real(1e-4) * w;          // guards the slab and column tests against rounding
+  const real cull2 = rc2 + real(2) * margin * (real)S.r_c;
+  const uint32_t* st = start + S.cell0;
   real pot = 0, fx = 0, fy = 0, fz = 0;
-  for (int dz = 0; dz < span; ++dz) {
-    const int zz = wrap_index(cz - 2 + dz, n_c);
-    for (int dy = 0; dy < span; ++dy) {
-      const int yy = wrap_index(cy - 2 + dy, n_c);
-      for (int dxc = 0; dxc < span; ++dxc) {
-        const int xx = wrap_index(cx - 2 + dxc, n_c);
-        const long long kk = S.cell0 + cell_key(S, xx, yy, zz);
-        const uint32_t jb = start[kk], je = start[kk + 1];
+  for (int oy = -2; oy <= 2; ++oy) {
+    const int yy = wrap2(cy + oy, n_c);
+    const real gy = oy > 0 ? oy * w - ri.y : (oy < 0 ? ri.y - (oy + 1) * w : real(0));
+    const real sy = ri.y - oy * w;
+    for (int ox = -2; ox <= 2; ++ox) {
+      const real gx = ox > 0 ? ox * w - ri.x : (ox < 0 ? ri.x - (ox + 1) * w : real(0));
+      const real d2 = gx * gx + gy * gy;
+      if (d2 >= cull2) continue;                  // column beyond the cutoff
+      const real hz = sqrt_real(rc2 - (d2 < rc2 ? d2 : rc2)) + margin;
+      const int xx = wrap2(cx + ox, n_c);
+      const real sx = ri.x - ox * w;
+      for (int oz = -2; oz <= 2; ++oz) {
+        const real sz = ri.z - oz * w;            // i's z in the neighbour cell's frame
+        const real zlo = sz - hz, zhi = sz + hz;
+        if (zhi < real(0) || zlo >= w) continue;
+        const int slo = zlo <= real(0) ? 0 : (int)(zlo * slab_per_len);
+        int shi = (int)(zhi * slab_per_len);
+        shi = shi > kSub - 1 ? kSub - 1 : shi;
+        const int zz = wrap2(cz + oz, n_c);
+        const long long key = tab ? (long long)(ktab[0][xx] + ktab[1][yy] + ktab[2][zz])
+                                  : (long long)cell_key(S, xx, yy, zz);
+        const uint32_t jb = st[key * kSub + slo], je = st[key * kSub + shi + 1];
         for (uint32_t j = jb; j < je; ++j) {
-          const typename Types<real>::atom aj = atoms[j];
-          real ddx, ddy, ddz;
-          pair_delta(S, ai, aj, scale, ddx, ddy, ddz);
-          const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 < rc2 && (long long)j != i) {
+          const typename Types<real>::res rj = rel[j];
+          const real dx = sx - rj.x, dy = sy - rj.y, dz = sz - rj.z;
+          const real r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < rc2 && r2 > real(0)) {
             const real rinv = rsqrt_real(r2);
-            const real y = real(2) * (r2 * rinv * inv_rc) - real(1);
-            const real e = horner<real>(nc.e, y);
-            const real chi = horner<real>(nc.chi, y);
-            const real qj = (real)atom_q(aj);
-            const real qe = qj * e * rinv;
-            pot += qe;
-            const real s = (qe + qj * chi * inv_rc) * rinv * rinv;
-            fx += s * ddx;
-            fy += s * ddy;
-            fz += s * ddz;
+            const real y = r2 * inv_rc2x2 - real(1);
+            const real h = horner<real>(nc.h, y);
+            const real k = horner<real>(nc.k, y);
+            const real qj = rj.w;
+            pot += qj * (rinv - h * inv_rc);
+            const real fs = qj * (rinv * rinv * rinv + k * inv_rc3);
+            fx += fs * dx;
+            fy += fs * dy;
+            fz += fs * dz;
           }
         }
       }
     }
   }
-  const real qi = (real)atom_q(ai);
+  const real qi = ri.w;
   const real k4 = real(1.0 / kFourPi);
   typename Types<real>::res out;
   out.x = pot * k4;

@@ -14,7 +14,7 @@ struct Launch {
                             uint32_t* count, int* err, cudaStream_t st);
   static cudaError_t scatter(const SysDesc* sys, const int2* chunks, int n_chunks, const void* coord,
                              const uint32_t* key, const uint32_t* rank, const uint32_t* start,
-                             const real* q, void* atoms, uint32_t* perm, cudaStream_t st);
+                             const real* q, void* atoms, void* rel, uint32_t* perm, cudaStream_t st);
   static cudaError_t spread(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem,
                             const void* atoms, const uint32_t* start, real* grids,
                             const SICoef<real>& si, int* err, cudaStream_t st);
@@ -24,8 +24,8 @@ struct Launch {
                             const void* atoms, const uint32_t* start, const real* grids, void* far,
                             const SICoef<real>& si, int* err, cudaStream_t st);
   static cudaError_t near(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
-                          const uint32_t* start, void* nearres, const NearCoef<real>& nc,
-                          cudaStream_t st);
+                          const void* rel, const uint32_t* start, void* nearres,
+                          const NearCoef<real>& nc, cudaStream_t st);
   static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                               const uint32_t* perm, const void* far, const void* nearres,
                               void* forces, void* pot, bool out_double, double* partials,
@@ -37,7 +37,11 @@ struct Launch {
   static size_t res_bytes();
 };
 
-cudaError_t launch_scan(const uint32_t* count, uint32_t* start, long long n, cudaStream_t st);
+// Exclusive scan of n counts into start[0..n] (start[n] = total); tile_sum
+// needs scan_tiles(n) entries.
+long long scan_tiles(long long n);
+cudaError_t launch_scan(const uint32_t* count, uint32_t* start, uint32_t* tile_sum, long long n,
+                        cudaStream_t st);
 cudaError_t launch_energy(const SysDesc* sys, int nsys, const double* fourier, int n_fourier_blocks,
                           const double* partials, int n_chunks, const int* chunk_first,
                           const double* consts, double* out, double* user_energy, cudaStream_t st);

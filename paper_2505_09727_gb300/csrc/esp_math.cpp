@@ -238,6 +238,11 @@ double Split::chi(double x) const {
   return psi.value(x) / C0;
 }
 
+double Split::dchi(double x) const {
+  if (kind == 1) return -2.0 * alpha * x * chi(x);
+  return psi.deriv(x) / C0;
+}
+
 double Split::one_minus_g(double x) const {
   if (kind == 1) return std::erfc(std::sqrt(alpha) * x);
   if (x >= 1.0) return 0.0;

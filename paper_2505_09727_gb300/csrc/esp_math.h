@@ -37,6 +37,7 @@ struct Split {
   std::vector<double> gx, gw, chi_at;   // 0..1 Gauss-Legendre rule and chi there
   double chi(double x) const;
   double one_minus_g(double x) const;   // int_x^1 chi (PSWF) or erfc(sqrt(a) x)
+  double dchi(double x) const;          // chi'(x) for 0 <= x <= 1
   double chihat(double kappa) const;    // int_0^inf chi(x) cos(kappa x) dx
   double chi0() const { return chi(0.0); }
   double second_moment() const;         // int_0^inf x^2 chi

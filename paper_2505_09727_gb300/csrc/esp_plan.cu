@@ -217,6 +217,8 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.gsize = 3 * (n_f / 2) * (n_f / 2) + 1;
   d.L = L; d.inv_L = 1.0 / L; d.h = h; d.inv_h = n_f / L;
   d.r_c = r_c; d.rc2 = r_c * r_c; d.inv_rc = 1.0 / r_c;
+  d.inv_rc2 = d.inv_rc * d.inv_rc; d.inv_rc3 = d.inv_rc2 * d.inv_rc;
+  d.w = L / n_c;
   d.fix_scale = L / 4294967296.0;
   hp.self_unit = split.chi0() / (4.0 * kPi * r_c);
   hp.m2 = split.second_moment();
@@ -235,17 +237,33 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     if (prec == ESP_FP64) si_err = std::max(si_err, e64);
     for (int k = 0; k < espk::Deg<double>::si; ++k) hp.si64.c[a][k] = co[k];
   }
-  auto fe = [&](double y) { return split.one_minus_g(0.5 * (y + 1.0)); };
-  auto fc = [&](double y) { return split.chi(0.5 * (y + 1.0)); };
+  // local part: H(s) = g(x)/x and K(s) = (x chi(x) - g(x))/x^3, s = x^2 = (y+1)/2;
+  // K by the cancellation-free form K = (1/x) int_0^1 u chi'(x u) du
+  std::vector<double> gq_x, gq_w;
+  espm::gauss_legendre(48, gq_x, gq_w);
+  for (size_t i = 0; i < gq_x.size(); ++i) { gq_x[i] = 0.5 * (gq_x[i] + 1.0); gq_w[i] *= 0.5; }
+  auto g_of = [&](double x) {
+    return split.kind == 1 ? std::erf(std::sqrt(split.alpha) * x) : split.psi.integral0(x) / split.C0;
+  };
+  auto fh = [&](double y) {
+    const double x = std::sqrt(std::max(0.0, 0.5 * (y + 1.0)));
+    return x > 1e-12 ? g_of(x) / x : split.chi0();
+  };
+  auto fk = [&](double y) {
+    const double x = std::max(1e-9, std::sqrt(std::max(0.0, 0.5 * (y + 1.0))));
+    double acc = 0.0;
+    for (size_t i = 0; i < gq_x.size(); ++i) acc += gq_w[i] * gq_x[i] * split.dchi(x * gq_x[i]);
+    return acc / x;
+  };
   {
-    double e1 = fit(fe, espk::Deg<float>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.e[k] = (float)co[k];
-    double e2 = fit(fc, espk::Deg<float>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.chi[k] = (float)co[k];
-    double e3 = fit(fe, espk::Deg<double>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.e[k] = co[k];
-    double e4 = fit(fc, espk::Deg<double>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.chi[k] = co[k];
+    double e1 = fit(fh, espk::Deg<float>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.h[k] = (float)co[k];
+    double e2 = fit(fk, espk::Deg<float>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.k[k] = (float)co[k];
+    double e3 = fit(fh, espk::Deg<double>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.h[k] = co[k];
+    double e4 = fit(fk, espk::Deg<double>::nr - 1, co);
+    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.k[k] = co[k];
     near_err = prec == ESP_FP32 ? std::max(e1, e2) : std::max(e3, e4);
   }
 
@@ -262,7 +280,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
 
   hp.tol = tol;
-  hp.n_cells3 = (long long)n_c * n_c * n_c;
+  hp.n_keys = (long long)n_c * n_c * n_c * espk::kSub;
   hp.grid_elems = (long long)n_f * n_f * n_f;
   hp.spec_elems = (long long)n_f * n_f * (n_f / 2 + 1);
   hp.n_bricks = d.nb * d.nb * d.nb;

@@ -21,7 +21,7 @@ struct HostPlan {
   espk::NearCoef<float> nc32{};
   espk::NearCoef<double> nc64{};
   std::vector<double> G, W;    // influence tables: G[|k|^2], W[|k_a|]
-  long long n_cells3 = 0;      // n_c^3
+  long long n_keys = 0;        // n_c^3 * kSub: length of the cell-list count array
   long long grid_elems = 0;    // n_f^3
   long long spec_elems = 0;    // n_f^2 (n_f/2 + 1)
   int n_bricks = 0;            // nb^3

@@ -81,8 +81,10 @@ esp_status run_local(const espe::HostPlan& hp, unsigned char* scratch, const dou
   auto* d_coord = c.take<unsigned char>(N * L::atom_bytes());
   auto* d_key = c.take<uint32_t>(N);
   auto* d_rank = c.take<uint32_t>(N);
-  auto* d_count = c.take<uint32_t>(hp.n_cells3);
-  auto* d_start = c.take<uint32_t>(hp.n_cells3 + 1);
+  auto* d_count = c.take<uint32_t>(hp.n_keys);
+  auto* d_start = c.take<uint32_t>(hp.n_keys + 1);
+  auto* d_tiles = c.take<uint32_t>(espk::scan_tiles(hp.n_keys));
+  auto* d_rel = c.take<unsigned char>(N * L::res_bytes());
   auto* d_atoms = c.take<unsigned char>(N * L::atom_bytes());
   auto* d_perm = c.take<uint32_t>(N);
   auto* d_q = c.take<real>(N);
@@ -114,7 +116,7 @@ esp_status run_local(const espe::HostPlan& hp, unsigned char* scratch, const dou
     SCU(cudaMemcpyAsync(d_chunks, chunks.data(), n_chunks * sizeof(int2), cudaMemcpyHostToDevice, st));
   SCU(cudaMemcpyAsync(d_chunk_first, chunk_first, sizeof(chunk_first), cudaMemcpyHostToDevice, st));
   SCU(cudaMemcpyAsync(d_consts, consts, sizeof(consts), cudaMemcpyHostToDevice, st));
-  SCU(cudaMemsetAsync(d_count, 0, hp.n_cells3 * sizeof(uint32_t), st));
+  SCU(cudaMemsetAsync(d_count, 0, hp.n_keys * sizeof(uint32_t), st));
   SCU(cudaMemsetAsync(d_far, 0, N * L::res_bytes(), st));
   SCU(cudaMemsetAsync(d_fourier, 0, sizeof(double), st));
   SCU(cudaMemsetAsync(d_err, 0, sizeof(int), st));
@@ -123,9 +125,10 @@ esp_status run_local(const espe::HostPlan& hp, unsigned char* scratch, const dou
       sizeof(real) == 4 ? (const void*)&hp.nc32 : (const void*)&hp.nc64);
   SCU(L::convert_charges(q, true, d_q, N, st));
   SCU(L::ingest(d_desc, d_chunks, n_chunks, xyz, true, d_coord, d_key, d_rank, d_count, d_err, st));
-  SCU(espk::launch_scan(d_count, d_start, hp.n_cells3, st));
-  SCU(L::scatter(d_desc, d_chunks, n_chunks, d_coord, d_key, d_rank, d_start, d_q, d_atoms, d_perm, st));
-  SCU(L::near(d_desc, d_chunks, n_chunks, d_atoms, d_start, d_near, nc, st));
+  SCU(espk::launch_scan(d_count, d_start, d_tiles, hp.n_keys, st));
+  SCU(L::scatter(d_desc, d_chunks, n_chunks, d_coord, d_key, d_rank, d_start, d_q, d_atoms, d_rel, d_perm,
+                 st));
+  SCU(L::near(d_desc, d_chunks, n_chunks, d_atoms, d_rel, d_start, d_near, nc, st));
   SCU(L::finalize(d_desc, d_chunks, n_chunks, d_atoms, d_perm, d_far, d_near, forces, potential, true,
                   d_partials, st));
   SCU(espk::launch_energy(d_desc, 1, d_fourier, 1, d_partials, n_chunks, d_chunk_first, d_consts,
@@ -144,7 +147,8 @@ size_t needed_bytes(const espe::HostPlan& hp, int precision) {
   b += align256(sizeof(espk::SysDesc) + 1) + align256(std::max<long long>(1, n_chunks) * 8 + 1) +
        align256(9);
   b += align256(N * ab + 1) * 2 + align256(N * 4 + 1) * 3;
-  b += align256(hp.n_cells3 * 4 + 1) + align256((hp.n_cells3 + 1) * 4 + 1);
+  b += align256(hp.n_keys * 4 + 1) + align256((hp.n_keys + 1) * 4 + 1) +
+       align256(espk::scan_tiles(hp.n_keys) * 4 + 1) + align256(N * ab + 1);
   b += align256(N * rb + 1) + align256(N * ab + 1) * 2;
   b += align256(2 * std::max<long long>(1, n_chunks) * 8 + 1) + 4 * 256;
   return b;

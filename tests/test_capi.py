@@ -76,7 +76,8 @@ def test_planner_gaussian_split(lib):
 
 def test_planner_fp64_fits_to_rounding(lib):
     got = lib.esp_plan_query(20.0, 1000, 1e-10, r_c=5.0, precision=lib.ESP_FP64)
-    assert got["si_fit_error"] < 1e-13 and got["near_fit_error"] < 1e-13
+    # (the near-field correction K reaches ~35 at this shape: 1e-12 is ~3e-14 relative)
+    assert got["si_fit_error"] < 1e-13 and got["near_fit_error"] < 1e-12
     assert got["P"] == oparams.stencil_width(1e-10)
 
 
