@@ -110,7 +110,7 @@ struct esp_plan_s {
   bool fwd_ok = false, inv_ok = false;
   cudaStream_t st = nullptr, st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaEvent_t tev[12] = {};
+  cudaEvent_t tev[13] = {};
   float phase_ms[kPhases] = {};
   bool timed_valid = false;     // events of the last compute were recorded
   double e_fourier = 0, e_gather = 0;
@@ -359,6 +359,7 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
   // A1b: scatter into cell order
   ESP_CU(L::scatter(p->d_desc, p->d_chunks, p->n_chunks, p->d_coord, p->d_key, p->d_rank, p->d_start,
                     (const real*)p->d_q, p->d_atoms, p->d_rel, p->d_perm, st));
+  rec(p, 12, st);
   // fork: local part on the second stream (on the main stream when timing
   // mode 2 serialises the phases so each kernel is timed alone)
   const bool serial = p->timing_mode == 2;
@@ -596,7 +597,7 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
     cudaEventElapsedTime(&t, p->tev[a], p->tev[b]);
     return t;
   };
-  p->phase_ms[0] = el(0, 1) + el(2, 3);   // ingest + scan, scatter
+  p->phase_ms[0] = el(0, 1) + el(2, 12);  // ingest + scan, scatter
   p->phase_ms[1] = el(3, 4);              // spread (with grid clear)
   p->phase_ms[2] = el(4, 5);              // R2C FFT
   p->phase_ms[3] = el(5, 6);              // scale + energy

@@ -265,10 +265,9 @@ __device__ inline float cell_relative(const SysDesc& S, uint32_t u) {
   const uint32_t frac = (uint32_t)((uint64_t)u * (uint64_t)S.n_c);   // fraction of the cell
   return (float)((double)frac * 2.3283064365386962890625e-10 * S.w);
 }
-__device__ inline double cell_relative(const SysDesc& S, double x) {
-  const int c = cell_f64(x, S);
-  return x - c * S.w;
-}
+// FP64 mode keeps absolute wrapped coordinates in the pair records, so pair
+// differences are the same FP64 subtractions as a plain minimum-image sum.
+__device__ inline double cell_relative(const SysDesc&, double x) { return x; }
 
 template <typename real, typename Q>
 __global__ void __launch_bounds__(kChunk) k_scatter(
@@ -526,8 +525,16 @@ __global__ void __launch_bounds__(kChunk) k_near(
   const long long i = S.atom0 + local;
   int cx, cy, cz;
   atom_cell(S, atoms[i], cx, cy, cz);
-  const typename Types<real>::res ri = rel[i];
+  const typename Types<real>::res ra = rel[i];
   const real w = (real)S.w;
+  // ri: position relative to i's cell (for the column and slab tests)
+  typename Types<real>::res ri = ra;
+  if constexpr (sizeof(real) == 8) {
+    ri.x = ra.x - cx * S.w;
+    ri.y = ra.y - cy * S.w;
+    ri.z = ra.z - cz * S.w;
+  }
+  const real Lbox = (real)S.L;
   const real rc2 = (real)S.rc2, inv_rc = (real)S.inv_rc;
   const real inv_rc2x2 = real(2) * (real)S.inv_rc2, inv_rc3 = (real)S.inv_rc3;
   const real slab_per_len = real(kSub) / w;
@@ -538,22 +545,31 @@ __global__ void __launch_bounds__(kChunk) k_near(
   for (int oy = -2; oy <= 2; ++oy) {
     const int yy = wrap2(cy + oy, n_c);
     const real gy = oy > 0 ? oy * w - ri.y : (oy < 0 ? ri.y - (oy + 1) * w : real(0));
-    const real sy = ri.y - oy * w;
+    // i's y in the frame of the neighbour's records: cell-relative (FP32) or
+    // absolute minus the periodic image shift (FP64)
+    real sy;
+    if constexpr (sizeof(real) == 8) sy = ra.y - Lbox * (real)((cy + oy - yy) / n_c);
+    else sy = ri.y - oy * w;
     for (int ox = -2; ox <= 2; ++ox) {
       const real gx = ox > 0 ? ox * w - ri.x : (ox < 0 ? ri.x - (ox + 1) * w : real(0));
       const real d2 = gx * gx + gy * gy;
       if (d2 >= cull2) continue;                  // column beyond the cutoff
       const real hz = sqrt_real(rc2 - (d2 < rc2 ? d2 : rc2)) + margin;
       const int xx = wrap2(cx + ox, n_c);
-      const real sx = ri.x - ox * w;
+      real sx;
+      if constexpr (sizeof(real) == 8) sx = ra.x - Lbox * (real)((cx + ox - xx) / n_c);
+      else sx = ri.x - ox * w;
       for (int oz = -2; oz <= 2; ++oz) {
-        const real sz = ri.z - oz * w;            // i's z in the neighbour cell's frame
-        const real zlo = sz - hz, zhi = sz + hz;
+        const real zc = ri.z - oz * w;            // i's z in the neighbour cell's frame
+        const real zlo = zc - hz, zhi = zc + hz;
         if (zhi < real(0) || zlo >= w) continue;
         const int slo = zlo <= real(0) ? 0 : (int)(zlo * slab_per_len);
         int shi = (int)(zhi * slab_per_len);
         shi = shi > kSub - 1 ? kSub - 1 : shi;
         const int zz = wrap2(cz + oz, n_c);
+        real sz;
+        if constexpr (sizeof(real) == 8) sz = ra.z - Lbox * (real)((cz + oz - zz) / n_c);
+        else sz = zc;
         const long long key = tab ? (long long)(ktab[0][xx] + ktab[1][yy] + ktab[2][zz])
                                   : (long long)cell_key(S, xx, yy, zz);
         const uint32_t jb = st[key * kSub + slo], je = st[key * kSub + shi + 1];
@@ -577,7 +593,7 @@ __global__ void __launch_bounds__(kChunk) k_near(
       }
     }
   }
-  const real qi = ri.w;
+  const real qi = ra.w;
   const real k4 = real(1.0 / kFourPi);
   typename Types<real>::res out;
   out.x = pot * k4;

@@ -92,6 +92,12 @@ def test_fp64_matches_oracle(esp, name):
 def test_fp32_matches_oracle(esp, name):
     make, eps, r_c = CASES[name]
     s = make()
+    if name == "nacl8":
+        # r_c = 2.0 is a lattice shell: pairs at exactly r = r_c, where the
+        # truncated local force jumps by O(eps). FP64 decides r < r_c exactly
+        # like the oracle; FP32 coordinates cannot, so the FP32 case uses a
+        # cutoff between shells.
+        r_c = 1.9
     g = gpu_solve(esp, s, eps, r_c=r_c, precision=esp.ESP_FP32)
     ref = oracle_same(s, eps, g["info"])
     assert force_error(s, g["forces"], ref["forces"]) <= FP32_PARITY
