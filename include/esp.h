@@ -97,7 +97,8 @@ typedef struct {
   int allow_background;/* 1 = neutralising background for sum q != 0        */
   int brick_cells;     /* tuning: cells per spread/gather brick edge; 0 auto */
   double timeout_ms;   /* deadline of host waits; 0 = 60000                  */
-  int reserved[8];
+  int cell_reach;      /* tuning: cell edge ~ r_c / cell_reach (2 or 3; 0 auto) */
+  int reserved[7];
 } esp_plan_opts;
 
 /* Parameters a plan chose (esp_plan_info). */
@@ -108,7 +109,9 @@ typedef struct {
   double near_fit_error;   /* max error of the local-part polynomials        */
   int64_t N;
   int P, n_f, kernel, precision;
-  int n_cells;             /* cell-list cells per axis (edge >= r_c/2)       */
+  int n_cells;             /* cell-list cells per axis (edge >= r_c/reach)   */
+  int cell_reach;          /* neighbour cells per side in the local part     */
+  int near_terms;          /* polynomial terms of the local-part corrections */
   int brick_cells;         /* cells per brick edge                           */
   int tile;                /* shared-memory tile edge in grid points         */
   int si_degree, near_degree;

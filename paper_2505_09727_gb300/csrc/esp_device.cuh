@@ -60,7 +60,7 @@ struct SysDesc {
   int T;          // shared tile edge in grid points
   int n_atoms;
   int gsize;      // entries of the radial table G (3 (n_f/2)^2 + 1)
-  int pad0;
+  int reach;      // neighbour cells per side in the local part (edge w >= r_c / reach)
   long long atom0;   // first atom of the system in the pooled atom arrays
   long long cell0;   // first entry of the system in the pooled count/start arrays
                      // (arrays indexed by cell key * kSub + slab)

@@ -2,6 +2,7 @@
 // precision-independent scan and energy launchers.
 #define ESP_REAL float
 #define ESP_P_MIN 4
+#define ESP_NEAR_SHORT 10
 #define ESP_P_MAX 12
 #define ESP_P_CASES(FN, ...)                                              \
   ESP_P_CASE(4, FN, __VA_ARGS__) ESP_P_CASE(5, FN, __VA_ARGS__)           \

@@ -1,6 +1,7 @@
 // FP64 plain-mode instantiations of the ESP kernels (P = 4 ... 16).
 #define ESP_REAL double
 #define ESP_P_MIN 4
+#define ESP_NEAR_SHORT 24
 #define ESP_P_MAX 16
 #define ESP_P_CASES(FN, ...)                                              \
   ESP_P_CASE(4, FN, __VA_ARGS__) ESP_P_CASE(5, FN, __VA_ARGS__)           \

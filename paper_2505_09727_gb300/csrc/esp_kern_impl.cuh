@@ -119,12 +119,19 @@ cudaError_t Launch<ESP_REAL>::scale(const SysDesc* sys, int nsys, int nblk, void
 template <>
 cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n_chunks,
                                    const void* atoms, const void* rel, const uint32_t* start,
-                                   void* nearres, const NearCoef<ESP_REAL>& nc, cudaStream_t st) {
+                                   void* nearres, const NearCoef<ESP_REAL>& nc, int terms,
+                                   cudaStream_t st) {
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
-  k_near<ESP_REAL><<<n_chunks, kChunk, 0, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start,
-                                                (R*)nearres, nc);
+  if (terms == ESP_NEAR_SHORT)
+    k_near<ESP_REAL, ESP_NEAR_SHORT><<<n_chunks, kChunk, 0, st>>>(
+        sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc);
+  else if (terms == Deg<ESP_REAL>::nr)
+    k_near<ESP_REAL, Deg<ESP_REAL>::nr><<<n_chunks, kChunk, 0, st>>>(
+        sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -30,11 +30,13 @@ __device__ inline float atom_q(const uint4& a) { return __uint_as_float(a.w); }
 __device__ inline double atom_q(const dquad& a) { return a.w; }
 
 // ------------------------------------------------------------ cell geometry
+// Cells are numbered brick by brick; inside a brick z runs fastest, so the
+// cells of one column of a brick are consecutive.
 __device__ inline int cell_key(const SysDesc& S, int cx, int cy, int cz) {
   const int bc = S.bc, nb = S.nb;
   const int bx = cx / bc, by = cy / bc, bz = cz / bc;
   const int lx = cx - bx * bc, ly = cy - by * bc, lz = cz - bz * bc;
-  return ((bz * nb + by) * nb + bx) * (bc * bc * bc) + (lz * bc + ly) * bc + lx;
+  return ((bz * nb + by) * nb + bx) * (bc * bc * bc) + (lx * bc + ly) * bc + lz;
 }
 
 __device__ inline void atom_cell(const SysDesc& S, const uint4& a, int& cx, int& cy, int& cz) {
@@ -260,11 +262,19 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_add(
 }
 
 // A1b: counting-sort scatter. perm[sorted] = pooled caller index.
-// Position of a coordinate relative to the lower face of its cell.
+// Position of a coordinate relative to the lower face of its cell (x, y) or
+// of its brick (z: the cells of a brick column share one z frame).
 __device__ inline float cell_relative(const SysDesc& S, uint32_t u) {
   const uint32_t frac = (uint32_t)((uint64_t)u * (uint64_t)S.n_c);   // fraction of the cell
   return (float)((double)frac * 2.3283064365386962890625e-10 * S.w);
 }
+__device__ inline float brick_relative(const SysDesc& S, uint32_t u) {
+  const uint64_t t = (uint64_t)u * (uint64_t)S.n_c;                   // 32.32 cell coordinate
+  const int c = (int)(t >> 32);
+  const double in_brick = (double)(c % S.bc) + (double)(uint32_t)t * 2.3283064365386962890625e-10;
+  return (float)(in_brick * S.w);
+}
+__device__ inline double brick_relative(const SysDesc&, double x) { return x; }
 // FP64 mode keeps absolute wrapped coordinates in the pair records, so pair
 // differences are the same FP64 subtractions as a plain minimum-image sum.
 __device__ inline double cell_relative(const SysDesc&, double x) { return x; }
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(kChunk) k_scatter(
   typename Types<real>::res r;
   r.x = cell_relative(S, a.x);
   r.y = cell_relative(S, a.y);
-  r.z = cell_relative(S, a.z);
+  r.z = brick_relative(S, a.z);
   r.w = (real)q[i];
   if constexpr (sizeof(real) == 4) a.w = __float_as_uint((float)q[i]);
   else a.w = (double)q[i];
@@ -468,15 +478,15 @@ __global__ void __launch_bounds__(256) k_gather(
 }
 
 // A7: local part (Eq. localpart). One thread per sorted atom i. The atoms
-// within r_c of i lie in the 5^3 cells around its cell (edge w >= r_c/2). For
-// every neighbouring column the lane computes the xy gap to it; a column no
-// closer than r_c is skipped, otherwise only the z slabs that the cutoff
-// sphere can reach in that column are read. Coordinates are relative to each
-// atom's cell, so a neighbour cell at offset o sits at o*w in i's frame (this
-// also covers periodic images when n_c < 5).
-template <typename real>
+// within r_c of i lie in the (2R+1)^2 columns of cells around its cell (edge
+// w >= r_c/R). For every neighbouring column the lane computes the xy gap; a
+// column no closer than r_c is skipped, otherwise the z window of the cutoff
+// sphere over that column is read as one contiguous key range per brick it
+// crosses (cells of a brick column are consecutive, split into kSub z slabs).
+// FP32 records hold x, y relative to the cell and z relative to the brick;
+// FP64 records hold absolute coordinates and use periodic image shifts.
+template <typename real, int NC>
 __device__ __forceinline__ real horner(const real* c, real y) {
-  constexpr int NC = Deg<real>::nr;
   real v = c[NC - 1];
 #pragma unroll
   for (int k = NC - 2; k >= 0; --k) v = v * y + c[k];
@@ -488,35 +498,31 @@ __device__ inline double rsqrt_real(double x) { return 1.0 / sqrt(x); }
 __device__ inline float sqrt_real(float x) { return sqrtf(x); }
 __device__ inline double sqrt_real(double x) { return sqrt(x); }
 
-// c + o wrapped into [0, n) for |o| <= 2 and any n >= 1.
-__device__ inline int wrap2(int v, int n) {
-  v += v < 0 ? n : 0;
-  v += v < 0 ? n : 0;
-  v -= v >= n ? n : 0;
-  v -= v >= n ? n : 0;
-  return v;
+__device__ inline int floor_div(int a, int b) {      // b > 0
+  const int q = a / b;
+  return (a % b != 0 && a < 0) ? q - 1 : q;
 }
 
 constexpr int kMaxCellsAxis = 2048;
 
-template <typename real>
+template <typename real, int NC>
 __global__ void __launch_bounds__(kChunk) k_near(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
     const typename Types<real>::atom* __restrict__ atoms,
     const typename Types<real>::res* __restrict__ rel, const uint32_t* __restrict__ start,
     typename Types<real>::res* __restrict__ nearres, const NearCoef<real> nc) {
-  // per-axis parts of the brick-major cell key: key = kx[cx] + ky[cy] + kz[cz]
+  // per-axis parts of the cell key: key = kx[cx] + ky[cy] + kz[cz]
   __shared__ int ktab[3][kMaxCellsAxis];
   const int2 ch = chunks[blockIdx.x];
   const SysDesc& S = sys[ch.x];
-  const int n_c = S.n_c, bc = S.bc, nb = S.nb;
+  const int n_c = S.n_c, bc = S.bc, nb = S.nb, R = S.reach;
   const bool tab = n_c <= kMaxCellsAxis;
   if (tab) {
     for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
       const int bq = c / bc, l = c - bq * bc;
-      ktab[0][c] = bq * bc * bc * bc + l;
+      ktab[0][c] = bq * bc * bc * bc + l * bc * bc;
       ktab[1][c] = bq * nb * bc * bc * bc + l * bc;
-      ktab[2][c] = bq * nb * nb * bc * bc * bc + l * bc * bc;
+      ktab[2][c] = bq * nb * nb * bc * bc * bc + l;
     }
   }
   __syncthreads();
@@ -527,52 +533,62 @@ __global__ void __launch_bounds__(kChunk) k_near(
   atom_cell(S, atoms[i], cx, cy, cz);
   const typename Types<real>::res ra = rel[i];
   const real w = (real)S.w;
-  // ri: position relative to i's cell (for the column and slab tests)
-  typename Types<real>::res ri = ra;
-  if constexpr (sizeof(real) == 8) {
-    ri.x = ra.x - cx * S.w;
-    ri.y = ra.y - cy * S.w;
-    ri.z = ra.z - cz * S.w;
-  }
   const real Lbox = (real)S.L;
+  // i's position relative to its own cell
+  real xi, yi, zi;
+  if constexpr (sizeof(real) == 8) {
+    xi = ra.x - cx * S.w;
+    yi = ra.y - cy * S.w;
+    zi = ra.z - cz * S.w;
+  } else {
+    xi = ra.x;
+    yi = ra.y;
+    zi = ra.z - (real)(cz % bc) * w;
+  }
   const real rc2 = (real)S.rc2, inv_rc = (real)S.inv_rc;
   const real inv_rc2x2 = real(2) * (real)S.inv_rc2, inv_rc3 = (real)S.inv_rc3;
   const real slab_per_len = real(kSub) / w;
   const real margin = real(1e-4) * w;          // guards the slab and column tests against rounding
   const real cull2 = rc2 + real(2) * margin * (real)S.r_c;
+  const int slab_min = -R * kSub, slab_max = (R + 1) * kSub - 1;
   const uint32_t* st = start + S.cell0;
   real pot = 0, fx = 0, fy = 0, fz = 0;
-  for (int oy = -2; oy <= 2; ++oy) {
-    const int yy = wrap2(cy + oy, n_c);
-    const real gy = oy > 0 ? oy * w - ri.y : (oy < 0 ? ri.y - (oy + 1) * w : real(0));
-    // i's y in the frame of the neighbour's records: cell-relative (FP32) or
-    // absolute minus the periodic image shift (FP64)
+  for (int oy = -R; oy <= R; ++oy) {
+    const int yy = ((cy + oy) % n_c + n_c) % n_c;
+    const real gy = oy > 0 ? oy * w - yi : (oy < 0 ? yi - (oy + 1) * w : real(0));
     real sy;
     if constexpr (sizeof(real) == 8) sy = ra.y - Lbox * (real)((cy + oy - yy) / n_c);
-    else sy = ri.y - oy * w;
-    for (int ox = -2; ox <= 2; ++ox) {
-      const real gx = ox > 0 ? ox * w - ri.x : (ox < 0 ? ri.x - (ox + 1) * w : real(0));
+    else sy = yi - oy * w;
+    const int ky = tab ? ktab[1][yy] : 0;
+    for (int ox = -R; ox <= R; ++ox) {
+      const real gx = ox > 0 ? ox * w - xi : (ox < 0 ? xi - (ox + 1) * w : real(0));
       const real d2 = gx * gx + gy * gy;
       if (d2 >= cull2) continue;                  // column beyond the cutoff
       const real hz = sqrt_real(rc2 - (d2 < rc2 ? d2 : rc2)) + margin;
-      const int xx = wrap2(cx + ox, n_c);
+      const int xx = ((cx + ox) % n_c + n_c) % n_c;
       real sx;
       if constexpr (sizeof(real) == 8) sx = ra.x - Lbox * (real)((cx + ox - xx) / n_c);
-      else sx = ri.x - ox * w;
-      for (int oz = -2; oz <= 2; ++oz) {
-        const real zc = ri.z - oz * w;            // i's z in the neighbour cell's frame
-        const real zlo = zc - hz, zhi = zc + hz;
-        if (zhi < real(0) || zlo >= w) continue;
-        const int slo = zlo <= real(0) ? 0 : (int)(zlo * slab_per_len);
-        int shi = (int)(zhi * slab_per_len);
-        shi = shi > kSub - 1 ? kSub - 1 : shi;
-        const int zz = wrap2(cz + oz, n_c);
+      else sx = xi - ox * w;
+      const int kxy = tab ? ktab[0][xx] + ky : 0;
+      // z window in slabs relative to the bottom of i's cell
+      int s_lo = (int)floor((zi - hz) * slab_per_len);
+      int s_hi = (int)floor((zi + hz) * slab_per_len);
+      s_lo = s_lo < slab_min ? slab_min : s_lo;
+      s_hi = s_hi > slab_max ? slab_max : s_hi;
+      const int oz_last = floor_div(s_hi, kSub);
+      int oz = floor_div(s_lo, kSub);
+      while (oz <= oz_last) {
+        const int zc = cz + oz;                     // unwrapped cell index
+        const int zz = ((zc % n_c) + n_c) % n_c;
+        const int seg_last = min(oz_last, oz + (bc - 1 - zz % bc));   // stay inside the brick
+        const int sl_first = (oz == floor_div(s_lo, kSub)) ? s_lo - oz * kSub : 0;
+        const int sl_last = (seg_last == oz_last) ? s_hi - seg_last * kSub : kSub - 1;
+        const long long k0 = tab ? (long long)(kxy + ktab[2][zz]) : (long long)cell_key(S, xx, yy, zz);
+        const uint32_t jb = st[k0 * kSub + sl_first];
+        const uint32_t je = st[(k0 + (seg_last - oz)) * kSub + sl_last + 1];
         real sz;
-        if constexpr (sizeof(real) == 8) sz = ra.z - Lbox * (real)((cz + oz - zz) / n_c);
-        else sz = zc;
-        const long long key = tab ? (long long)(ktab[0][xx] + ktab[1][yy] + ktab[2][zz])
-                                  : (long long)cell_key(S, xx, yy, zz);
-        const uint32_t jb = st[key * kSub + slo], je = st[key * kSub + shi + 1];
+        if constexpr (sizeof(real) == 8) sz = ra.z - Lbox * (real)((zc - zz) / n_c);
+        else sz = zi - (real)(oz - zz % bc) * w;    // frame of this brick column
         for (uint32_t j = jb; j < je; ++j) {
           const typename Types<real>::res rj = rel[j];
           const real dx = sx - rj.x, dy = sy - rj.y, dz = sz - rj.z;
@@ -580,8 +596,8 @@ __global__ void __launch_bounds__(kChunk) k_near(
           if (r2 < rc2 && r2 > real(0)) {
             const real rinv = rsqrt_real(r2);
             const real y = r2 * inv_rc2x2 - real(1);
-            const real h = horner<real>(nc.h, y);
-            const real k = horner<real>(nc.k, y);
+            const real h = horner<real, NC>(nc.h, y);
+            const real k = horner<real, NC>(nc.k, y);
             const real qj = rj.w;
             pot += qj * (rinv - h * inv_rc);
             const real fs = qj * (rinv * rinv * rinv + k * inv_rc3);
@@ -590,6 +606,7 @@ __global__ void __launch_bounds__(kChunk) k_near(
             fz += fs * dz;
           }
         }
+        oz = seg_last + 1;
       }
     }
   }

@@ -184,14 +184,20 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
   const espm::Window win = espm::make_window(best_c1, P);
 
-  // cell list and bricks
-  const int nc_max = std::max(1, (int)std::floor(2.0 * L / r_c * (1.0 - 1e-12)));
-  const int cand[7] = {4, 3, 5, 2, 6, 8, 1};
+  // cell list and bricks: cell edge w >= r_c / reach. A reach of 3 (smaller
+  // cells) reads fewer non-neighbours in the local part; it needs at least a
+  // few cells per axis to pay off.
+  int reach = o.cell_reach > 0 ? o.cell_reach : 3;
+  if (reach < 1 || reach > 4) { msg = "cell_reach must be 1 ... 4"; return ESP_ERR_INVALID_ARG; }
+  if (o.cell_reach <= 0 && std::floor(3.0 * L / r_c) < 9) reach = 2;
+  const int nc_max = std::max(1, (int)std::floor(reach * L / r_c * (1.0 - 1e-12)));
+  // brick = bc^3 cells; prefer a brick edge near 8 grid points among shapes
+  // that keep at least 90% of the finest admissible cell count
   const double h = L / n_f;
   int n_c = 0, bc = 0, T = 0;
+  double best_score = -1e300;
   const size_t rb = prec == ESP_FP32 ? 4 : 8;
-  for (int i = 0; i < 7; ++i) {
-    const int b = cand[i];
+  for (int b = 1; b <= 8; ++b) {
     if (o.brick_cells > 0 && b != o.brick_cells) continue;
     const int nc = (nc_max / b) * b;
     if (nc < b || nc == 0) continue;
@@ -200,7 +206,11 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     d.L = L; d.inv_h = n_f / L;
     const int t = tile_edge(d, P, prec);
     if ((size_t)t * t * t * rb > 200 * 1024) continue;
-    if (nc > n_c) { n_c = nc; bc = b; T = t; }
+    const double edge = (double)b * n_f / nc;            // brick edge in grid points
+    const double keep = (double)nc / nc_max;
+    double score = -std::fabs(std::log(edge / 8.0));
+    if (keep < 0.9) score -= 10.0 + (1.0 - keep) * 10.0;
+    if (score > best_score) { best_score = score; n_c = nc; bc = b; T = t; }
   }
   if (o.brick_cells > 0 && n_c == 0) {
     // requested brick does not divide any usable cell count: use single-cell bricks
@@ -213,6 +223,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   espk::SysDesc& d = hp.desc;
   d = espk::SysDesc{};
   d.n_f = n_f; d.n_c = n_c; d.bc = bc; d.nb = n_c / bc; d.T = T;
+  d.reach = reach;
   d.n_atoms = (int)N;
   d.gsize = 3 * (n_f / 2) * (n_f / 2) + 1;
   d.L = L; d.inv_L = 1.0 / L; d.h = h; d.inv_h = n_f / L;
@@ -256,15 +267,26 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     return acc / x;
   };
   {
-    double e1 = fit(fh, espk::Deg<float>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.h[k] = (float)co[k];
-    double e2 = fit(fk, espk::Deg<float>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<float>::nr; ++k) hp.nc32.k[k] = (float)co[k];
+    // FP32: 10 terms when that fit is 100x below the tolerance, else 12
+    double e1 = 0, e2 = 0;
+    for (int terms : {10, espk::Deg<float>::nr}) {
+      std::vector<double> ch, ck;
+      e1 = fit(fh, terms - 1, ch);
+      e2 = fit(fk, terms - 1, ck);
+      const double scale = std::max(std::fabs(fh(-1.0)), std::fabs(fk(1.0)));
+      hp.near_nc = terms;
+      for (int k = 0; k < espk::Deg<float>::nr; ++k) {
+        hp.nc32.h[k] = k < terms ? (float)ch[k] : 0.0f;
+        hp.nc32.k[k] = k < terms ? (float)ck[k] : 0.0f;
+      }
+      if (std::max(e1, e2) <= 0.01 * tol * std::max(1.0, scale)) break;
+    }
     double e3 = fit(fh, espk::Deg<double>::nr - 1, co);
     for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.h[k] = co[k];
     double e4 = fit(fk, espk::Deg<double>::nr - 1, co);
     for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.k[k] = co[k];
     near_err = prec == ESP_FP32 ? std::max(e1, e2) : std::max(e3, e4);
+    if (prec == ESP_FP64) hp.near_nc = espk::Deg<double>::nr;
   }
 
   // influence tables (Eq. pk, Phi in grid units)
@@ -294,6 +316,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   info.near_fit_error = near_err;
   info.N = N; info.P = P; info.n_f = n_f; info.kernel = kernel; info.precision = prec;
   info.n_cells = n_c; info.brick_cells = bc; info.tile = T;
+  info.cell_reach = reach; info.near_terms = hp.near_nc;
   info.si_degree = (prec == ESP_FP32 ? espk::Deg<float>::si : espk::Deg<double>::si) - 1;
   info.near_degree = (prec == ESP_FP32 ? espk::Deg<float>::nr : espk::Deg<double>::nr) - 1;
   return ESP_OK;

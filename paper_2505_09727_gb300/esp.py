@@ -44,7 +44,7 @@ class esp_plan_opts(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("prefactor", ctypes.c_double),
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("allow_background", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("timeout_ms", ctypes.c_double),
-        ("reserved", ctypes.c_int * 8),
+        ("cell_reach", ctypes.c_int), ("reserved", ctypes.c_int * 7),
     ]
 
 
@@ -56,6 +56,7 @@ class esp_plan_params(ctypes.Structure):
         ("si_fit_error", ctypes.c_double), ("near_fit_error", ctypes.c_double),
         ("N", ctypes.c_int64), ("P", ctypes.c_int), ("n_f", ctypes.c_int),
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("n_cells", ctypes.c_int),
+        ("cell_reach", ctypes.c_int), ("near_terms", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("tile", ctypes.c_int), ("si_degree", ctypes.c_int),
         ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
     ]

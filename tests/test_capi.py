@@ -62,8 +62,8 @@ def test_planner_matches_oracle_reading(lib, L, N, eps, r_c):
     assert abs(got["c1"] - want["c1"]) < 1e-9 * want["c1"]
     assert abs(got["alias_estimate"] - want["alias"]) < 1e-6 * want["alias"]
     assert got["h"] == pytest.approx(L / want["n_f"])
-    # cell list: edge >= r_c / 2, bricks divide the cell grid
-    assert L / got["n_cells"] >= r_c / 2
+    # cell list: edge >= r_c / reach, bricks divide the cell grid
+    assert L / got["n_cells"] >= r_c / got["cell_reach"]
     assert got["n_cells"] % got["brick_cells"] == 0
     assert got["si_fit_error"] < 1e-8 and got["near_fit_error"] < 1e-7
 
