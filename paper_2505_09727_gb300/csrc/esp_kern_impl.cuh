@@ -10,7 +10,7 @@ namespace detail {
 
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
+  if (smem <= 32 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -124,14 +124,14 @@ cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
-  if (terms == ESP_NEAR_SHORT)
-    k_near<ESP_REAL, ESP_NEAR_SHORT><<<n_chunks, kChunk, 0, st>>>(
-        sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc);
-  else if (terms == Deg<ESP_REAL>::nr)
-    k_near<ESP_REAL, Deg<ESP_REAL>::nr><<<n_chunks, kChunk, 0, st>>>(
-        sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc);
-  else
-    return cudaErrorInvalidValue;
+  auto kshort = k_near<ESP_REAL, ESP_NEAR_SHORT>;
+  auto klong = k_near<ESP_REAL, Deg<ESP_REAL>::nr>;
+  auto kern = terms == ESP_NEAR_SHORT ? kshort : (terms == Deg<ESP_REAL>::nr ? klong : nullptr);
+  if (!kern) return cudaErrorInvalidValue;
+  cudaError_t e = detail::allow_smem(kern, kNearQueueBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<n_chunks, kChunk, kNearQueueBytes, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start,
+                                                  (R*)nearres, nc);
   return cudaGetLastError();
 }
 

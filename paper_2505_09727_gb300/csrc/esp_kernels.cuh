@@ -477,14 +477,20 @@ __global__ void __launch_bounds__(256) k_gather(
   }
 }
 
-// A7: local part (Eq. localpart). One thread per sorted atom i. The atoms
-// within r_c of i lie in the (2R+1)^2 columns of cells around its cell (edge
-// w >= r_c/R). For every neighbouring column the lane computes the xy gap; a
-// column no closer than r_c is skipped, otherwise the z window of the cutoff
-// sphere over that column is read as one contiguous key range per brick it
-// crosses (cells of a brick column are consecutive, split into kSub z slabs).
-// FP32 records hold x, y relative to the cell and z relative to the brick;
-// FP64 records hold absolute coordinates and use periodic image shifts.
+// A7: local part (Eq. localpart). One thread per sorted atom i, in two
+// phases that alternate at warp-uniform points:
+//  scan   the atoms within r_c of i lie in the (2R+1)^2 columns of cells
+//         around its cell (edge w >= r_c/R). Per neighbouring column the
+//         lane computes the xy gap; a column no closer than r_c is skipped,
+//         otherwise the z window of the cutoff sphere over the column is read
+//         as one contiguous key range per brick it crosses (cells of a brick
+//         column are consecutive, split into kSub z slabs). Each candidate is
+//         tested with cheap cell-relative coordinates (FP32; absolute with
+//         image shifts in FP64) and, if r < r_c, its index is queued.
+//  pairs  when some lane's queue fills, every lane evaluates its queued pairs
+//         with the minimum-image difference of the fixed-point coordinates
+//         (int32 wrap; FP64: r - L rint(r/L)), so the pair work runs only for
+//         pairs inside the cutoff and with most lanes busy.
 template <typename real, int NC>
 __device__ __forceinline__ real horner(const real* c, real y) {
   real v = c[NC - 1];
@@ -498,12 +504,66 @@ __device__ inline double rsqrt_real(double x) { return 1.0 / sqrt(x); }
 __device__ inline float sqrt_real(float x) { return sqrtf(x); }
 __device__ inline double sqrt_real(double x) { return sqrt(x); }
 
-__device__ inline int floor_div(int a, int b) {      // b > 0
-  const int q = a / b;
-  return (a % b != 0 && a < 0) ? q - 1 : q;
+constexpr int kMaxCellsAxis = 512;
+constexpr int kMaxReach = 4;
+constexpr int kTabPad = kMaxReach + 1;            // unwrapped cell indices -kTabPad ... n_c + kTabPad - 1
+constexpr int kNearWarps = kChunk / 32;
+constexpr int kQueueCap = 48;                      // pairs buffered per lane
+constexpr int kQueueFlush = 24;                    // flush when a lane holds this many
+constexpr size_t kNearQueueBytes = (size_t)kNearWarps * kQueueCap * 32 * sizeof(uint32_t);
+
+struct NearTabs {
+  int key[3][kMaxCellsAxis];                       // key parts per axis (brick-major, z fastest in brick)
+  short wrap[kMaxCellsAxis + 2 * kTabPad];         // wrapped index of an unwrapped cell index
+  short image[kMaxCellsAxis + 2 * kTabPad];        // periodic image of an unwrapped cell index
+  short bend[kMaxCellsAxis + 2 * kTabPad];         // last unwrapped index in the same brick (z)
+};
+
+template <typename real>
+__device__ __forceinline__ void pair_geometry(const SysDesc& S, const typename Types<real>::atom& ai,
+                                              const typename Types<real>::atom& aj, real& dx, real& dy,
+                                              real& dz) {
+  if constexpr (sizeof(real) == 4) {
+    const float sc = (float)S.fix_scale;
+    dx = (float)(int)(ai.x - aj.x) * sc;         // int32 wrap = minimum image
+    dy = (float)(int)(ai.y - aj.y) * sc;
+    dz = (float)(int)(ai.z - aj.z) * sc;
+  } else {
+    dx = ai.x - aj.x; dx -= S.L * rint(dx * S.inv_L);
+    dy = ai.y - aj.y; dy -= S.L * rint(dy * S.inv_L);
+    dz = ai.z - aj.z; dz -= S.L * rint(dz * S.inv_L);
+  }
 }
 
-constexpr int kMaxCellsAxis = 2048;
+template <typename real, int NC>
+__device__ __forceinline__ void near_flush(const SysDesc& S, const typename Types<real>::atom& ai,
+                                           const typename Types<real>::atom* __restrict__ atoms,
+                                           const uint32_t* q, int cnt, const NearCoef<real>& nc,
+                                           real rc2, real inv_rc, real inv_rc2x2, real inv_rc3,
+                                           real& pot, real& fx, real& fy, real& fz) {
+  const int m = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+  for (int k = 0; k < m; ++k) {
+    if (k < cnt) {
+      const uint32_t j = q[k * 32];
+      const typename Types<real>::atom aj = atoms[j];
+      real dx, dy, dz;
+      pair_geometry<real>(S, ai, aj, dx, dy, dz);
+      const real r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < rc2 && r2 > real(0)) {
+        const real rinv = rsqrt_real(r2);
+        const real y = r2 * inv_rc2x2 - real(1);
+        const real h = horner<real, NC>(nc.h, y);
+        const real kk = horner<real, NC>(nc.k, y);
+        const real qj = (real)atom_q(aj);
+        pot += qj * (rinv - h * inv_rc);
+        const real fs = qj * (rinv * rinv * rinv + kk * inv_rc3);
+        fx += fs * dx;
+        fy += fs * dy;
+        fz += fs * dz;
+      }
+    }
+  }
+}
 
 template <typename real, int NC>
 __global__ void __launch_bounds__(kChunk) k_near(
@@ -511,31 +571,37 @@ __global__ void __launch_bounds__(kChunk) k_near(
     const typename Types<real>::atom* __restrict__ atoms,
     const typename Types<real>::res* __restrict__ rel, const uint32_t* __restrict__ start,
     typename Types<real>::res* __restrict__ nearres, const NearCoef<real> nc) {
-  // per-axis parts of the cell key: key = kx[cx] + ky[cy] + kz[cz]
-  __shared__ int ktab[3][kMaxCellsAxis];
+  __shared__ NearTabs tabs;
+  extern __shared__ __align__(16) uint32_t queue_mem[];   // [warp][kQueueCap][32]
   const int2 ch = chunks[blockIdx.x];
   const SysDesc& S = sys[ch.x];
   const int n_c = S.n_c, bc = S.bc, nb = S.nb, R = S.reach;
-  const bool tab = n_c <= kMaxCellsAxis;
-  if (tab) {
-    for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
-      const int bq = c / bc, l = c - bq * bc;
-      ktab[0][c] = bq * bc * bc * bc + l * bc * bc;
-      ktab[1][c] = bq * nb * bc * bc * bc + l * bc;
-      ktab[2][c] = bq * nb * nb * bc * bc * bc + l;
-    }
+  for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
+    const int bq = c / bc, l = c - bq * bc;
+    tabs.key[0][c] = bq * bc * bc * bc + l * bc * bc;
+    tabs.key[1][c] = bq * nb * bc * bc * bc + l * bc;
+    tabs.key[2][c] = bq * nb * nb * bc * bc * bc + l;
+  }
+  for (int u = threadIdx.x; u < n_c + 2 * kTabPad; u += blockDim.x) {
+    const int zc = u - kTabPad;
+    const int zz = ((zc % n_c) + n_c) % n_c;
+    tabs.wrap[u] = (short)zz;
+    tabs.image[u] = (short)((zc - zz) / n_c);
+    tabs.bend[u] = (short)(zc + (bc - 1 - zz % bc));
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31;
+  uint32_t* q = queue_mem + (size_t)(threadIdx.x >> 5) * kQueueCap * 32 + lane;
   const int local = ch.y + threadIdx.x;
-  if (local >= S.n_atoms) return;
-  const long long i = S.atom0 + local;
+  const bool valid = local < S.n_atoms;
+  const long long i = S.atom0 + (valid ? local : 0);
+  const typename Types<real>::atom ai = atoms[i];
   int cx, cy, cz;
-  atom_cell(S, atoms[i], cx, cy, cz);
+  atom_cell(S, ai, cx, cy, cz);
   const typename Types<real>::res ra = rel[i];
   const real w = (real)S.w;
   const real Lbox = (real)S.L;
-  // i's position relative to its own cell
-  real xi, yi, zi;
+  real xi, yi, zi;                                  // i relative to its own cell
   if constexpr (sizeof(real) == 8) {
     xi = ra.x - cx * S.w;
     yi = ra.y - cy * S.w;
@@ -553,63 +619,78 @@ __global__ void __launch_bounds__(kChunk) k_near(
   const int slab_min = -R * kSub, slab_max = (R + 1) * kSub - 1;
   const uint32_t* st = start + S.cell0;
   real pot = 0, fx = 0, fy = 0, fz = 0;
+  int cnt = 0;
   for (int oy = -R; oy <= R; ++oy) {
-    const int yy = ((cy + oy) % n_c + n_c) % n_c;
+    const int uy = cy + oy + kTabPad;
+    const int yy = tabs.wrap[uy];
     const real gy = oy > 0 ? oy * w - yi : (oy < 0 ? yi - (oy + 1) * w : real(0));
     real sy;
-    if constexpr (sizeof(real) == 8) sy = ra.y - Lbox * (real)((cy + oy - yy) / n_c);
+    if constexpr (sizeof(real) == 8) sy = ra.y - Lbox * (real)tabs.image[uy];
     else sy = yi - oy * w;
-    const int ky = tab ? ktab[1][yy] : 0;
     for (int ox = -R; ox <= R; ++ox) {
       const real gx = ox > 0 ? ox * w - xi : (ox < 0 ? xi - (ox + 1) * w : real(0));
       const real d2 = gx * gx + gy * gy;
-      if (d2 >= cull2) continue;                  // column beyond the cutoff
-      const real hz = sqrt_real(rc2 - (d2 < rc2 ? d2 : rc2)) + margin;
-      const int xx = ((cx + ox) % n_c + n_c) % n_c;
-      real sx;
-      if constexpr (sizeof(real) == 8) sx = ra.x - Lbox * (real)((cx + ox - xx) / n_c);
-      else sx = xi - ox * w;
-      const int kxy = tab ? ktab[0][xx] + ky : 0;
-      // z window in slabs relative to the bottom of i's cell
-      int s_lo = (int)floor((zi - hz) * slab_per_len);
-      int s_hi = (int)floor((zi + hz) * slab_per_len);
-      s_lo = s_lo < slab_min ? slab_min : s_lo;
-      s_hi = s_hi > slab_max ? slab_max : s_hi;
-      const int oz_last = floor_div(s_hi, kSub);
-      int oz = floor_div(s_lo, kSub);
-      while (oz <= oz_last) {
-        const int zc = cz + oz;                     // unwrapped cell index
-        const int zz = ((zc % n_c) + n_c) % n_c;
-        const int seg_last = min(oz_last, oz + (bc - 1 - zz % bc));   // stay inside the brick
-        const int sl_first = (oz == floor_div(s_lo, kSub)) ? s_lo - oz * kSub : 0;
-        const int sl_last = (seg_last == oz_last) ? s_hi - seg_last * kSub : kSub - 1;
-        const long long k0 = tab ? (long long)(kxy + ktab[2][zz]) : (long long)cell_key(S, xx, yy, zz);
-        const uint32_t jb = st[k0 * kSub + sl_first];
-        const uint32_t je = st[(k0 + (seg_last - oz)) * kSub + sl_last + 1];
-        real sz;
-        if constexpr (sizeof(real) == 8) sz = ra.z - Lbox * (real)((zc - zz) / n_c);
-        else sz = zi - (real)(oz - zz % bc) * w;    // frame of this brick column
-        for (uint32_t j = jb; j < je; ++j) {
-          const typename Types<real>::res rj = rel[j];
-          const real dx = sx - rj.x, dy = sy - rj.y, dz = sz - rj.z;
-          const real r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 < rc2 && r2 > real(0)) {
-            const real rinv = rsqrt_real(r2);
-            const real y = r2 * inv_rc2x2 - real(1);
-            const real h = horner<real, NC>(nc.h, y);
-            const real k = horner<real, NC>(nc.k, y);
-            const real qj = rj.w;
-            pot += qj * (rinv - h * inv_rc);
-            const real fs = qj * (rinv * rinv * rinv + k * inv_rc3);
-            fx += fs * dx;
-            fy += fs * dy;
-            fz += fs * dz;
+      if (valid && d2 < cull2) {
+        const real hz = sqrt_real(rc2 - (d2 < rc2 ? d2 : rc2)) + margin;
+        const int ux = cx + ox + kTabPad;
+        const int xx = tabs.wrap[ux];
+        real sx;
+        if constexpr (sizeof(real) == 8) sx = ra.x - Lbox * (real)tabs.image[ux];
+        else sx = xi - ox * w;
+        const int kxy = tabs.key[0][xx] + tabs.key[1][yy];
+        int s_lo = (int)floor((zi - hz) * slab_per_len);
+        int s_hi = (int)floor((zi + hz) * slab_per_len);
+        s_lo = s_lo < slab_min ? slab_min : s_lo;
+        s_hi = s_hi > slab_max ? slab_max : s_hi;
+        const int oz_first = s_lo >> 2, oz_last = s_hi >> 2;     // kSub = 4
+        for (int oz = oz_first; oz <= oz_last;) {
+          const int uz = cz + oz + kTabPad;
+          const int zz = tabs.wrap[uz];
+          const int seg_last = min(oz_last, (int)tabs.bend[uz] - cz);
+          const int sl_first = oz == oz_first ? s_lo - oz * kSub : 0;
+          const int sl_last = seg_last == oz_last ? s_hi - seg_last * kSub : kSub - 1;
+          const int k0 = kxy + tabs.key[2][zz];
+          const uint32_t jb = st[(long long)k0 * kSub + sl_first];
+          const uint32_t je = st[(long long)(k0 + seg_last - oz) * kSub + sl_last + 1];
+          real sz;
+          if constexpr (sizeof(real) == 8) sz = ra.z - Lbox * (real)tabs.image[uz];
+          else sz = zi - (real)(oz - zz % bc) * w;            // frame of this brick column
+          for (uint32_t j = jb; j < je; ++j) {
+            const typename Types<real>::res rj = rel[j];
+            const real dx = sx - rj.x, dy = sy - rj.y, dz = sz - rj.z;
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2 && r2 > real(0)) {
+              if (cnt < kQueueCap) {
+                q[cnt * 32] = j;
+                ++cnt;
+              } else {
+                // rare overflow: evaluate this pair at once
+                const typename Types<real>::atom aj = atoms[j];
+                real ex, ey, ez;
+                pair_geometry<real>(S, ai, aj, ex, ey, ez);
+                const real e2 = ex * ex + ey * ey + ez * ez;
+                const real rinv = rsqrt_real(e2);
+                const real y = e2 * inv_rc2x2 - real(1);
+                const real qj = (real)atom_q(aj);
+                pot += qj * (rinv - horner<real, NC>(nc.h, y) * inv_rc);
+                const real fs = qj * (rinv * rinv * rinv + horner<real, NC>(nc.k, y) * inv_rc3);
+                fx += fs * ex;
+                fy += fs * ey;
+                fz += fs * ez;
+              }
+            }
           }
+          oz = seg_last + 1;
         }
-        oz = seg_last + 1;
+      }
+      if (__any_sync(0xffffffffu, cnt >= kQueueFlush)) {
+        near_flush<real, NC>(S, ai, atoms, q, cnt, nc, rc2, inv_rc, inv_rc2x2, inv_rc3, pot, fx, fy, fz);
+        cnt = 0;
       }
     }
   }
+  near_flush<real, NC>(S, ai, atoms, q, cnt, nc, rc2, inv_rc, inv_rc2x2, inv_rc3, pot, fx, fy, fz);
+  if (!valid) return;
   const real qi = ra.w;
   const real k4 = real(1.0 / kFourPi);
   typename Types<real>::res out;

@@ -190,6 +190,12 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   int reach = o.cell_reach > 0 ? o.cell_reach : 3;
   if (reach < 1 || reach > 4) { msg = "cell_reach must be 1 ... 4"; return ESP_ERR_INVALID_ARG; }
   if (o.cell_reach <= 0 && std::floor(3.0 * L / r_c) < 9) reach = 2;
+  // the local part keeps per-axis cell tables in shared memory (512 entries)
+  if (o.cell_reach <= 0) while (reach > 1 && std::floor(reach * L / r_c) > 512) --reach;
+  if (std::floor(reach * L / r_c) > 512) {
+    msg = "more than 512 cell-list cells per axis: raise r_c or lower cell_reach";
+    return ESP_ERR_UNSUPPORTED;
+  }
   const int nc_max = std::max(1, (int)std::floor(reach * L / r_c * (1.0 - 1e-12)));
   // brick = bc^3 cells; prefer a brick edge near 8 grid points among shapes
   // that keep at least 90% of the finest admissible cell count
