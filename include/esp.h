@@ -98,7 +98,9 @@ typedef struct {
   int brick_cells;     /* tuning: cells per spread/gather brick edge; 0 auto */
   double timeout_ms;   /* deadline of host waits; 0 = 60000                  */
   int cell_reach;      /* tuning: cell edge ~ r_c / cell_reach (2 or 3; 0 auto) */
-  int reserved[7];
+  int near_variant;    /* tuning: local-part kernel, 1 = pairs evaluated in the
+                          scan, 2 = pairs queued per lane; 0 = default (1)   */
+  int reserved[6];
 } esp_plan_opts;
 
 /* Parameters a plan chose (esp_plan_info). */

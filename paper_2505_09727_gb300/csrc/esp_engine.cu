@@ -374,7 +374,7 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
   const espk::SICoef<real>& si = *reinterpret_cast<const espk::SICoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.si32 : (const void*)&hp.si64);
   ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
-                 hp.near_nc, st2));
+                 hp.near_nc, hp.near_queued, st2));
   rec(p, 10, st2);
   if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
 

@@ -120,18 +120,20 @@ template <>
 cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n_chunks,
                                    const void* atoms, const void* rel, const uint32_t* start,
                                    void* nearres, const NearCoef<ESP_REAL>& nc, int terms,
-                                   cudaStream_t st) {
+                                   bool queued, cudaStream_t st) {
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
-  auto kshort = k_near<ESP_REAL, ESP_NEAR_SHORT>;
-  auto klong = k_near<ESP_REAL, Deg<ESP_REAL>::nr>;
-  auto kern = terms == ESP_NEAR_SHORT ? kshort : (terms == Deg<ESP_REAL>::nr ? klong : nullptr);
+  decltype(&k_near<ESP_REAL, ESP_NEAR_SHORT, true>) kern = nullptr;
+  if (terms == ESP_NEAR_SHORT)
+    kern = queued ? k_near<ESP_REAL, ESP_NEAR_SHORT, true> : k_near<ESP_REAL, ESP_NEAR_SHORT, false>;
+  else if (terms == Deg<ESP_REAL>::nr)
+    kern = queued ? k_near<ESP_REAL, Deg<ESP_REAL>::nr, true> : k_near<ESP_REAL, Deg<ESP_REAL>::nr, false>;
   if (!kern) return cudaErrorInvalidValue;
-  cudaError_t e = detail::allow_smem(kern, kNearQueueBytes);
+  const size_t smem = queued ? kNearQueueBytes : 0;
+  cudaError_t e = detail::allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_chunks, kChunk, kNearQueueBytes, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start,
-                                                  (R*)nearres, nc);
+  kern<<<n_chunks, kChunk, smem, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc);
   return cudaGetLastError();
 }
 

@@ -508,8 +508,8 @@ constexpr int kMaxCellsAxis = 512;
 constexpr int kMaxReach = 4;
 constexpr int kTabPad = kMaxReach + 1;            // unwrapped cell indices -kTabPad ... n_c + kTabPad - 1
 constexpr int kNearWarps = kChunk / 32;
-constexpr int kQueueCap = 48;                      // pairs buffered per lane
-constexpr int kQueueFlush = 24;                    // flush when a lane holds this many
+constexpr int kQueueCap = 24;                      // pairs buffered per lane (queued variant)
+constexpr int kQueueFlush = 12;                    // flush when a lane holds this many
 constexpr size_t kNearQueueBytes = (size_t)kNearWarps * kQueueCap * 32 * sizeof(uint32_t);
 
 struct NearTabs {
@@ -565,7 +565,7 @@ __device__ __forceinline__ void near_flush(const SysDesc& S, const typename Type
   }
 }
 
-template <typename real, int NC>
+template <typename real, int NC, bool QUEUE>
 __global__ void __launch_bounds__(kChunk) k_near(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
     const typename Types<real>::atom* __restrict__ atoms,
@@ -660,7 +660,17 @@ __global__ void __launch_bounds__(kChunk) k_near(
             const real dx = sx - rj.x, dy = sy - rj.y, dz = sz - rj.z;
             const real r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < rc2 && r2 > real(0)) {
-              if (cnt < kQueueCap) {
+              if (!QUEUE) {
+                // inline variant: evaluate the pair in the scan (masked lanes idle)
+                const real rinv = rsqrt_real(r2);
+                const real y = r2 * inv_rc2x2 - real(1);
+                const real qj = rj.w;
+                pot += qj * (rinv - horner<real, NC>(nc.h, y) * inv_rc);
+                const real fs = qj * (rinv * rinv * rinv + horner<real, NC>(nc.k, y) * inv_rc3);
+                fx += fs * dx;
+                fy += fs * dy;
+                fz += fs * dz;
+              } else if (cnt < kQueueCap) {
                 q[cnt * 32] = j;
                 ++cnt;
               } else {
@@ -683,13 +693,14 @@ __global__ void __launch_bounds__(kChunk) k_near(
           oz = seg_last + 1;
         }
       }
-      if (__any_sync(0xffffffffu, cnt >= kQueueFlush)) {
+      if (QUEUE && __any_sync(0xffffffffu, cnt >= kQueueFlush)) {
         near_flush<real, NC>(S, ai, atoms, q, cnt, nc, rc2, inv_rc, inv_rc2x2, inv_rc3, pot, fx, fy, fz);
         cnt = 0;
       }
     }
   }
-  near_flush<real, NC>(S, ai, atoms, q, cnt, nc, rc2, inv_rc, inv_rc2x2, inv_rc3, pot, fx, fy, fz);
+  if (QUEUE)
+    near_flush<real, NC>(S, ai, atoms, q, cnt, nc, rc2, inv_rc, inv_rc2x2, inv_rc3, pot, fx, fy, fz);
   if (!valid) return;
   const real qi = ra.w;
   const real k4 = real(1.0 / kFourPi);

@@ -25,7 +25,7 @@ struct Launch {
                             const SICoef<real>& si, int* err, cudaStream_t st);
   static cudaError_t near(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                           const void* rel, const uint32_t* start, void* nearres,
-                          const NearCoef<real>& nc, int terms, cudaStream_t st);
+                          const NearCoef<real>& nc, int terms, bool queued, cudaStream_t st);
   static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                               const uint32_t* perm, const void* far, const void* nearres,
                               void* forces, void* pot, bool out_double, double* partials,

@@ -308,6 +308,8 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
 
   hp.tol = tol;
+  if (o.near_variant < 0 || o.near_variant > 2) { msg = "near_variant must be 0, 1 or 2"; return ESP_ERR_INVALID_ARG; }
+  hp.near_queued = o.near_variant == 2;
   hp.n_keys = (long long)n_c * n_c * n_c * espk::kSub;
   hp.grid_elems = (long long)n_f * n_f * n_f;
   hp.spec_elems = (long long)n_f * n_f * (n_f / 2 + 1);

@@ -26,6 +26,7 @@ struct HostPlan {
   long long spec_elems = 0;    // n_f^2 (n_f/2 + 1)
   int n_bricks = 0;            // nb^3
   int near_nc = 0;             // polynomial terms used by the local part
+  bool near_queued = false;    // local-part variant (queued pairs)
 };
 
 // Fill `hp` for a cubic box of edge L with N atoms. Returns ESP_OK or an

@@ -128,7 +128,7 @@ esp_status run_local(const espe::HostPlan& hp, unsigned char* scratch, const dou
   SCU(espk::launch_scan(d_count, d_start, d_tiles, hp.n_keys, st));
   SCU(L::scatter(d_desc, d_chunks, n_chunks, d_coord, d_key, d_rank, d_start, d_q, d_atoms, d_rel, d_perm,
                  st));
-  SCU(L::near(d_desc, d_chunks, n_chunks, d_atoms, d_rel, d_start, d_near, nc, hp.near_nc, st));
+  SCU(L::near(d_desc, d_chunks, n_chunks, d_atoms, d_rel, d_start, d_near, nc, hp.near_nc, hp.near_queued, st));
   SCU(L::finalize(d_desc, d_chunks, n_chunks, d_atoms, d_perm, d_far, d_near, forces, potential, true,
                   d_partials, st));
   SCU(espk::launch_energy(d_desc, 1, d_fourier, 1, d_partials, n_chunks, d_chunk_first, d_consts,

@@ -44,7 +44,7 @@ class esp_plan_opts(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("prefactor", ctypes.c_double),
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("allow_background", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("timeout_ms", ctypes.c_double),
-        ("cell_reach", ctypes.c_int), ("reserved", ctypes.c_int * 7),
+        ("cell_reach", ctypes.c_int), ("near_variant", ctypes.c_int), ("reserved", ctypes.c_int * 6),
     ]
 
 
