@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--molecules", type=int, default=WORKLOAD["molecules"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64, Gaussian and batched comparison lines")
     return ap.parse_args()
 
 
@@ -246,13 +248,116 @@ def run_gpu(args, world, rank, local):
     e2e_s = time.perf_counter() - t0
     esp.esp_destroy(h)
 
+    extras = {}
+    if not args.no_extras:
+        extras["plain_fp64"] = single_variant(args, local, stream, flush, s, precision=esp.ESP_FP64)
+        extras["gaussian"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS)
+        extras["batched"] = batched(args, local, stream, flush)
+
     if world > 1:
         t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms, e2e_s = float(t[0]), float(t[1])
     phases = {k: v / args.steps for k, v in phase_acc.items()}
     return dict(N=N, L=L, info=info, total_ms=total_ms, step_ms=step_ms, e2e_s=e2e_s,
-                e2e_steps=e2e_steps, phases=phases, clocks=clocks, energy=float(e.cpu()[0]))
+                e2e_steps=e2e_steps, phases=phases, clocks=clocks, energy=float(e.cpu()[0]), extras=extras)
+
+
+# ------------------------------------------------------------------ extras
+def time_steps(step, stream, steps: int, flush) -> list:
+    """Per-step device ms of `step` (CUDA events on `stream`, L2 flushed between steps)."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def single_variant(args, local, stream, flush, s, **opts):
+    """atoms/s of the single-system path with other plan options (same workload)."""
+    import torch
+    from paper_2505_09727_gb300 import esp
+    dev = torch.device("cuda", local)
+    h = esp.esp_plan(s.L, s.n, WORKLOAD["tolerance"], r_c=WORKLOAD["r_c_nm"], device=local,
+                     stream=stream.cuda_stream, **opts)
+    info = esp.esp_plan_info(h)
+    x = torch.tensor(s.pos, device=dev)
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    f = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
+    esp.esp_set_charges(h, torch.tensor(s.q, device=dev))
+
+    def step():
+        esp.esp_set_positions(h, x)
+        esp.esp_compute(h, e, f, None)
+
+    for _ in range(3):
+        step()
+    ms = time_steps(step, stream, max(3, min(args.steps, 20)), flush)
+    esp.esp_destroy(h)
+    t = statistics.median(ms)
+    return {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
+            "steps": len(ms)}
+
+
+BATCH = dict(workload="electrolyte_batch_64", systems=64, atoms_lo=3000, atoms_hi=200_000,
+             density_per_nm3=100.0, r_c_nm=1.0, tolerance=1e-4, seed=9727)
+
+
+def batched(args, local, stream, flush):
+    """64 independent electrolyte boxes, sizes log-uniform in [3e3, 2e5], one
+    batch: bucketed batched FFTs, whole step replayed from a CUDA graph."""
+    import torch
+    from paper_2505_09727_gb300 import esp, inputs
+    dev = torch.device("cuda", local)
+    sizes = inputs.batch_sizes(BATCH["systems"], BATCH["atoms_lo"], BATCH["atoms_hi"], seed=BATCH["seed"])
+    systems = inputs.electrolyte_batch(sizes, seed=BATCH["seed"])
+    pos, q = inputs.concat(systems)
+    n = int(pos.shape[0])
+    t0 = time.perf_counter()
+    b = esp.esp_batch_create([s.L for s in systems], [s.n for s in systems], BATCH["tolerance"],
+                             r_c=BATCH["r_c_nm"], device=local, stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    grids = sorted({esp.esp_batch_info(b, i)["n_f"] for i in range(len(systems))})
+    esp.esp_batch_set_charges(b, q)
+    x = torch.tensor(pos, device=dev)
+    e = torch.zeros(len(systems), dtype=torch.float64, device=dev)
+    f = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+
+    def step():
+        esp.esp_batch_compute(b, x, e, f, None)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    ms = time_steps(step, stream, max(3, min(args.steps, 20)), flush)
+    # phases (direct launches, serialised) for the breakdown
+    esp.esp_batch_set_timing(b, 2)
+    step()
+    phases = esp.esp_batch_phase_times(b)
+    esp.esp_batch_set_timing(b, 0)
+    # end to end with pinned host buffers
+    xh = torch.tensor(pos).pin_memory()
+    fh = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    eh = torch.zeros(len(systems), dtype=torch.float64).pin_memory()
+    esp.esp_batch_compute(b, xh, eh, fh, None, esp.ESP_HOST)
+    k = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        esp.esp_batch_compute(b, xh, eh, fh, None, esp.ESP_HOST)
+    e2e_s = (time.perf_counter() - t0) / k
+    esp.esp_batch_destroy(b)
+    t = statistics.median(ms)
+    return {"value": n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "atoms": n, "systems": len(systems),
+            "grid_sizes": grids, "create_s": round(t_create, 3), "steps": len(ms),
+            "phases_ms": {k2: round(v, 5) for k2, v in phases.items()},
+            "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 24,
+                    "d2h_bytes_per_step": n * 24 + 8 * len(systems)},
+            "config": BATCH}
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -339,6 +444,7 @@ def main():
         "step_ms_p99": float(np.percentile(r["step_ms"], 99)),
         "clocks": r["clocks"],
     }
+    line.update(r["extras"])
     line["roofline"] = roofline(r["phases"], r["info"], N, r["L"], r["clocks"], args.steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.molecules)

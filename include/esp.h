@@ -175,6 +175,52 @@ esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* 
 
 esp_status esp_destroy(esp_plan_t plan);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent systems (each its own cubic box, charges and positions)
+ * solved together in one step: the same pipeline as esp_compute runs once
+ * over all systems, with per-system cell lists, grids and influence
+ * functions, one batched cuFFT plan per grid size, and after the first call
+ * the whole step replayed from a CUDA graph. The paper treats one system at
+ * a time (Methods); the batch is the data-parallel form of that method for
+ * ensembles of small boxes, where one system cannot fill the GPU.
+ *
+ * Planning: every system is planned as by esp_plan with the same tolerance
+ * and options; r_c must be given (opts->r_c > 0) and be below L/2 of every
+ * box. The SI-kernel shape c1 is made common (the value most systems chose
+ * when planned alone) and each grid is raised to the next size of a ladder
+ * of FFT-friendly sizes >= 12% apart, so systems of similar size share a
+ * batched FFT; both only lower each system's aliasing estimate.
+ *
+ * Layout: the systems' atoms are concatenated in system order. Charges q
+ * (sum N[s]), positions xyz (sum N[s] x 3), forces (sum N[s] x 3) and
+ * potential (sum N[s]) use that order; energies has one entry per system.
+ * All FP64. `where` as for plans; outputs may be NULL. */
+typedef struct esp_batch_s* esp_batch_t;
+
+esp_status esp_batch_create(const esp_box* boxes, const int64_t* N, int n_systems,
+                            double tolerance, const esp_plan_opts* opts, esp_batch_t* out);
+/* Planner only (host, no GPU needed): the parameters esp_batch_create
+ * would choose, one esp_plan_params per system in out[n_systems]
+ * (device_bytes is 0). */
+esp_status esp_batch_query(const esp_box* boxes, const int64_t* N, int n_systems,
+                           double tolerance, const esp_plan_opts* opts, esp_plan_params* out);
+/* Parameters chosen for system `sys` (0-based). */
+esp_status esp_batch_info(esp_batch_t batch, int sys, esp_plan_params* out);
+/* Charges of all systems; rejects a non-neutral system when
+ * allow_background is 0. */
+esp_status esp_batch_set_charges(esp_batch_t batch, const double* q, int where);
+/* One step on positions xyz: ingest and bin sort, local and spectral parts,
+ * corrections, per-system compensated energies. With `where` = ESP_HOST it
+ * returns after the outputs are copied; with ESP_DEVICE it only enqueues. */
+esp_status esp_batch_compute(esp_batch_t batch, const double* xyz, double* energies,
+                             double* forces, double* potential, int where);
+esp_status esp_batch_synchronize(esp_batch_t batch);
+/* Phase timing as esp_set_timing / esp_phase_times; while timing is on the
+ * step runs as direct launches instead of the graph. */
+esp_status esp_batch_set_timing(esp_batch_t batch, int enable);
+esp_status esp_batch_phase_times(esp_batch_t batch, float* ms, int n);
+esp_status esp_batch_destroy(esp_batch_t batch);
+
 /* Local part without device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc (code running
  * while a framework's caching allocator owns the device heap, inside regions

@@ -1,14 +1,21 @@
-// Single-system execution engine and the C-ABI of include/esp.h.
+// Execution engine and the C-ABI of include/esp.h.
 //
-// A plan owns every device buffer of one system, two cuFFT plans and a
-// second stream on which the local part (Eq. localpart) runs concurrently with
-// the spectral part (Eqs. spread ... interp).
+// Everything runs on a pool of independent systems: the device arrays hold
+// the systems back to back (atoms, cell lists, grids, spectra, influence
+// tables), the kernels read per-system descriptors and work lists, and the
+// FFTs run as one batched cuFFT plan per grid size. A plan (esp_plan) is a
+// pool of one system; a batch (esp_batch_create) is a pool of many whose
+// whole step is replayed from a CUDA graph. The local part (Eq. localpart)
+// runs on a second stream concurrently with the spectral part
+// (Eqs. spread ... interp).
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <thread>
 #include <vector>
@@ -48,9 +55,20 @@ esp_status fail(esp_status s, const std::string& m) {
   } while (0)
 
 constexpr int kPhases = 9;
+constexpr int kFourierBlocks = 152 * 4;   // scale-kernel blocks per system, at most
 
 #define ESP_XSTR(x) #x
 #define ESP_STR(x) ESP_XSTR(x)
+
+// One batched FFT plan per grid size; the grids (and spectra) of its systems
+// are consecutive in the pool.
+struct Bucket {
+  int n_f = 0;
+  int count = 0;
+  long long grid0 = 0, spec0 = 0;
+  cufftHandle fwd = 0, inv = 0;
+  bool fwd_ok = false, inv_ok = false;
+};
 
 }  // namespace
 
@@ -59,19 +77,23 @@ void set_last_error(const std::string& msg) { g_error = msg; }
 }  // namespace espe
 
 struct esp_plan_s {
-  espe::HostPlan hp;
+  std::vector<espe::HostPlan> hps;     // per system, offsets zero
+  std::vector<espk::SysDesc> descs;    // per system, with pool offsets
+  int nsys = 0;
   int prec = ESP_FP32;
+  int P = 0;
   int device = 0;
   double timeout_ms = 60000.0;
   bool allow_bg = false;
-  long long N = 0;
-  int n_chunks = 0;
-  int n_fourier_blocks = 0;
-  size_t smem = 0;
-  double Q = 0, Q2 = 0;
+  long long N = 0;                     // atoms of all systems
+  long long n_keys = 0, grid_total = 0, spec_total = 0, tab_total = 0;
+  int n_chunks = 0, n_work = 0, F = 1;
+  size_t smem = 0;                     // spread/gather tile bytes (largest system)
+  std::vector<Bucket> buckets;
+  std::vector<double> Q, Q2;
   bool have_q = false, have_pos = false;
   bool timing = false;
-  int timing_mode = 0;          // 1: events, 2: events with serialised phases
+  int timing_mode = 0;                 // 1: events, 2: events with serialised phases
   bool own_stream = false;
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -81,7 +103,7 @@ struct esp_plan_s {
   int2* d_chunks = nullptr;
   int* d_chunk_first = nullptr;
   int2* d_work = nullptr;
-  void* d_pos = nullptr;       // staging for host positions (FP64, N x 3)
+  void* d_pos = nullptr;       // staging for positions (FP64, N x 3)
   void* d_coord = nullptr;
   uint32_t* d_key = nullptr;
   uint32_t* d_rank = nullptr;
@@ -89,10 +111,10 @@ struct esp_plan_s {
   uint32_t* d_start = nullptr;
   uint32_t* d_tiles = nullptr;   // scan tile totals
   void* d_atoms = nullptr;
-  void* d_rel = nullptr;         // cell-relative coordinates + charge (local part)
+  void* d_rel = nullptr;         // pair records of the local part
   uint32_t* d_perm = nullptr;
   void* d_q = nullptr;
-  void* d_qstage = nullptr;    // staging for host charges (FP64)
+  void* d_qstage = nullptr;      // staging for charges (FP64)
   void* d_grid = nullptr;
   void* d_spec = nullptr;
   void* d_tabs = nullptr;
@@ -101,19 +123,27 @@ struct esp_plan_s {
   double* d_fourier = nullptr;
   double* d_partials = nullptr;
   double* d_consts = nullptr;
-  double* d_eout = nullptr;
-  void* d_outF = nullptr;      // staging for host outputs (FP64)
+  double* d_eout = nullptr;      // per system: E, E_fourier, E_gather
+  double* d_energy = nullptr;    // per system: E (batch output)
+  void* d_outF = nullptr;        // staging for outputs (FP64)
   void* d_outU = nullptr;
   int* d_err = nullptr;
 
-  cufftHandle fwd = 0, inv = 0;
-  bool fwd_ok = false, inv_ok = false;
   cudaStream_t st = nullptr, st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t tev[13] = {};
   float phase_ms[kPhases] = {};
-  bool timed_valid = false;     // events of the last compute were recorded
-  double e_fourier = 0, e_gather = 0;
+  bool timed_valid = false;      // events of the last compute were recorded
+  std::vector<double> e_fourier, e_gather;
+
+  // batches: one step captured as a CUDA graph after a first direct run
+  int direct_runs = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+};
+
+struct esp_batch_s {
+  esp_plan_s pool;
 };
 
 namespace {
@@ -142,10 +172,14 @@ void release(esp_plan_s* p) {
   cudaSetDevice(p->device);
   if (p->st) cudaStreamSynchronize(p->st);
   if (p->st2) cudaStreamSynchronize(p->st2);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
   for (void* a : p->allocs) cudaFree(a);
   p->allocs.clear();
-  if (p->fwd_ok) cufftDestroy(p->fwd);
-  if (p->inv_ok) cufftDestroy(p->inv);
+  for (Bucket& b : p->buckets) {
+    if (b.fwd_ok) cufftDestroy(b.fwd);
+    if (b.inv_ok) cufftDestroy(b.inv);
+  }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   for (auto& e : p->tev) if (e) cudaEventDestroy(e);
@@ -193,76 +227,141 @@ void rec(esp_plan_s* p, int i, cudaStream_t s) {
   if (p->timing) cudaEventRecord(p->tev[i], s);
 }
 
+// Pool layout: per-system offsets, chunk and brick work lists, FFT buckets.
+void layout(esp_plan_s* p, std::vector<int2>& chunks, std::vector<int>& chunk_first,
+            std::vector<int2>& work) {
+  const int n = p->nsys;
+  p->descs.resize(n);
+  std::map<int, std::vector<int>> by_nf;
+  for (int s = 0; s < n; ++s) by_nf[p->hps[s].desc.n_f].push_back(s);
+  long long grid0 = 0, spec0 = 0;
+  p->buckets.clear();
+  for (auto& kv : by_nf) {
+    Bucket b;
+    b.n_f = kv.first;
+    b.count = (int)kv.second.size();
+    b.grid0 = grid0;
+    b.spec0 = spec0;
+    for (int s : kv.second) {
+      p->descs[s] = p->hps[s].desc;
+      p->descs[s].grid0 = grid0;
+      p->descs[s].spec0 = spec0;
+      grid0 += p->hps[s].grid_elems;
+      spec0 += p->hps[s].spec_elems;
+    }
+    p->buckets.push_back(b);
+  }
+  p->grid_total = grid0;
+  p->spec_total = spec0;
+  long long atom0 = 0, cell0 = 0, tab0 = 0, max_spec = 0;
+  chunks.clear();
+  work.clear();
+  chunk_first.assign(n + 1, 0);
+  p->smem = 0;
+  const size_t rb = p->prec == ESP_FP32 ? 4 : 8;
+  for (int s = 0; s < n; ++s) {
+    espk::SysDesc& d = p->descs[s];
+    const espe::HostPlan& hp = p->hps[s];
+    d.atom0 = atom0;
+    d.cell0 = cell0;
+    d.tab0 = tab0;
+    chunk_first[s] = (int)chunks.size();
+    for (int c = 0; c * espk::kChunk < d.n_atoms; ++c) chunks.push_back(make_int2(s, c * espk::kChunk));
+    for (int b = 0; b < hp.n_bricks; ++b) work.push_back(make_int2(s, b));
+    atom0 += d.n_atoms;
+    cell0 += hp.n_keys;
+    tab0 += (long long)(hp.G.size() + hp.W.size());
+    p->smem = std::max(p->smem, (size_t)d.T * d.T * d.T * rb);
+    max_spec = std::max(max_spec, hp.spec_elems);
+  }
+  chunk_first[n] = (int)chunks.size();
+  p->N = atom0;
+  p->n_keys = cell0;
+  p->tab_total = tab0;
+  p->n_chunks = (int)chunks.size();
+  p->n_work = (int)work.size();
+  // scale grid: enough blocks to fill the GPU, capped by the spectrum size
+  p->F = (int)std::min<long long>(kFourierBlocks, std::max<long long>(1, (max_spec + 255) / 256));
+}
+
 template <typename real>
 esp_status build_buffers(esp_plan_s* p) {
   using L = espk::Launch<real>;
-  const espe::HostPlan& hp = p->hp;
+  std::vector<int2> chunks, work;
+  std::vector<int> chunk_first;
+  layout(p, chunks, chunk_first, work);
   const long long N = p->N;
+  const int n = p->nsys;
   const size_t rb = sizeof(real);
-  p->n_chunks = (int)((N + espk::kChunk - 1) / espk::kChunk);
-  std::vector<int2> chunks(p->n_chunks);
-  for (int c = 0; c < p->n_chunks; ++c) chunks[c] = make_int2(0, c * espk::kChunk);
-  std::vector<int2> work(hp.n_bricks);
-  for (int b = 0; b < hp.n_bricks; ++b) work[b] = make_int2(0, b);
-  int chunk_first[2] = {0, p->n_chunks};
-  // scale grid: enough blocks to fill the GPU, capped by the spectrum size
-  long long spec_threads = hp.spec_elems;
-  p->n_fourier_blocks = (int)std::min<long long>(152 * 4, std::max<long long>(1, (spec_threads + 255) / 256));
 
-  ESP_TRY(dev_alloc_t(p, &p->d_desc, 1));
+  ESP_TRY(dev_alloc_t(p, &p->d_desc, n));
   ESP_TRY(dev_alloc_t(p, &p->d_chunks, std::max(1, p->n_chunks)));
-  ESP_TRY(dev_alloc_t(p, &p->d_chunk_first, 2));
-  ESP_TRY(dev_alloc_t(p, &p->d_work, std::max(1, hp.n_bricks)));
+  ESP_TRY(dev_alloc_t(p, &p->d_chunk_first, n + 1));
+  ESP_TRY(dev_alloc_t(p, &p->d_work, std::max(1, p->n_work)));
   ESP_TRY(dev_alloc(p, &p->d_pos, (size_t)N * 3 * sizeof(double)));
   ESP_TRY(dev_alloc(p, &p->d_coord, (size_t)N * L::atom_bytes()));
   ESP_TRY(dev_alloc_t(p, &p->d_key, N));
   ESP_TRY(dev_alloc_t(p, &p->d_rank, N));
-  ESP_TRY(dev_alloc_t(p, &p->d_count, hp.n_keys));
-  ESP_TRY(dev_alloc_t(p, &p->d_start, hp.n_keys + 1));
-  ESP_TRY(dev_alloc_t(p, &p->d_tiles, espk::scan_tiles(hp.n_keys)));
+  ESP_TRY(dev_alloc_t(p, &p->d_count, p->n_keys));
+  ESP_TRY(dev_alloc_t(p, &p->d_start, p->n_keys + 1));
+  ESP_TRY(dev_alloc_t(p, &p->d_tiles, espk::scan_tiles(p->n_keys)));
   ESP_TRY(dev_alloc(p, &p->d_rel, (size_t)N * L::res_bytes()));
   ESP_TRY(dev_alloc(p, &p->d_atoms, (size_t)N * L::atom_bytes()));
   ESP_TRY(dev_alloc_t(p, &p->d_perm, N));
   ESP_TRY(dev_alloc(p, &p->d_q, (size_t)N * rb));
   ESP_TRY(dev_alloc(p, &p->d_qstage, (size_t)N * sizeof(double)));
-  ESP_TRY(dev_alloc(p, &p->d_grid, (size_t)hp.grid_elems * rb));
-  ESP_TRY(dev_alloc(p, &p->d_spec, (size_t)hp.spec_elems * 2 * rb));
-  ESP_TRY(dev_alloc(p, &p->d_tabs, (hp.G.size() + hp.W.size()) * rb));
+  ESP_TRY(dev_alloc(p, &p->d_grid, (size_t)p->grid_total * rb));
+  ESP_TRY(dev_alloc(p, &p->d_spec, (size_t)p->spec_total * 2 * rb));
+  ESP_TRY(dev_alloc(p, &p->d_tabs, (size_t)p->tab_total * rb));
   ESP_TRY(dev_alloc(p, &p->d_far, (size_t)N * L::res_bytes()));
   ESP_TRY(dev_alloc(p, &p->d_near, (size_t)N * L::res_bytes()));
-  ESP_TRY(dev_alloc_t(p, &p->d_fourier, p->n_fourier_blocks));
+  ESP_TRY(dev_alloc_t(p, &p->d_fourier, (size_t)p->F * n));
   ESP_TRY(dev_alloc_t(p, &p->d_partials, 2 * std::max(1, p->n_chunks)));
-  ESP_TRY(dev_alloc_t(p, &p->d_consts, 2));
-  ESP_TRY(dev_alloc_t(p, &p->d_eout, 3));
+  ESP_TRY(dev_alloc_t(p, &p->d_consts, 2 * n));
+  ESP_TRY(dev_alloc_t(p, &p->d_eout, 3 * n));
+  ESP_TRY(dev_alloc_t(p, &p->d_energy, n));
   ESP_TRY(dev_alloc(p, &p->d_outF, (size_t)N * 3 * sizeof(double)));
   ESP_TRY(dev_alloc(p, &p->d_outU, (size_t)N * sizeof(double)));
   ESP_TRY(dev_alloc_t(p, &p->d_err, 1));
 
-  std::vector<real> tabs(hp.G.size() + hp.W.size());
-  for (size_t i = 0; i < hp.G.size(); ++i) tabs[i] = (real)hp.G[i];
-  for (size_t i = 0; i < hp.W.size(); ++i) tabs[hp.G.size() + i] = (real)hp.W[i];
-  espk::SysDesc d = hp.desc;
-  ESP_CU(cudaMemcpyAsync(p->d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, p->st));
+  std::vector<real> tabs(std::max<long long>(1, p->tab_total));
+  for (int s = 0; s < n; ++s) {
+    const espe::HostPlan& hp = p->hps[s];
+    const long long t0 = p->descs[s].tab0;
+    for (size_t i = 0; i < hp.G.size(); ++i) tabs[t0 + i] = (real)hp.G[i];
+    for (size_t i = 0; i < hp.W.size(); ++i) tabs[t0 + hp.G.size() + i] = (real)hp.W[i];
+  }
+  ESP_CU(cudaMemcpyAsync(p->d_desc, p->descs.data(), n * sizeof(espk::SysDesc), cudaMemcpyHostToDevice, p->st));
   if (p->n_chunks)
     ESP_CU(cudaMemcpyAsync(p->d_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, p->st));
-  ESP_CU(cudaMemcpyAsync(p->d_chunk_first, chunk_first, sizeof(chunk_first), cudaMemcpyHostToDevice, p->st));
-  ESP_CU(cudaMemcpyAsync(p->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, p->st));
-  ESP_CU(cudaMemcpyAsync(p->d_tabs, tabs.data(), tabs.size() * rb, cudaMemcpyHostToDevice, p->st));
+  ESP_CU(cudaMemcpyAsync(p->d_chunk_first, chunk_first.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, p->st));
+  if (p->n_work)
+    ESP_CU(cudaMemcpyAsync(p->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, p->st));
+  ESP_CU(cudaMemcpyAsync(p->d_tabs, tabs.data(), p->tab_total * rb, cudaMemcpyHostToDevice, p->st));
   ESP_CU(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->st));
-  ESP_CU(cudaMemsetAsync(p->d_consts, 0, 2 * sizeof(double), p->st));
-  p->smem = (size_t)hp.desc.T * hp.desc.T * hp.desc.T * rb;
+  ESP_CU(cudaMemsetAsync(p->d_consts, 0, 2 * n * sizeof(double), p->st));
 
-  const int n = hp.desc.n_f;
   const bool f32 = sizeof(real) == 4;
-  ESP_FFT(cufftPlan3d(&p->fwd, n, n, n, f32 ? CUFFT_R2C : CUFFT_D2Z));
-  p->fwd_ok = true;
-  ESP_FFT(cufftPlan3d(&p->inv, n, n, n, f32 ? CUFFT_C2R : CUFFT_Z2D));
-  p->inv_ok = true;
-  ESP_FFT(cufftSetStream(p->fwd, p->st));
-  ESP_FFT(cufftSetStream(p->inv, p->st));
-  size_t ws = 0;
-  if (cufftGetSize(p->fwd, &ws) == CUFFT_SUCCESS) p->bytes += ws;
-  if (cufftGetSize(p->inv, &ws) == CUFFT_SUCCESS) p->bytes += ws;
+  for (Bucket& b : p->buckets) {
+    int dims[3] = {b.n_f, b.n_f, b.n_f};
+    const int real_elems = b.n_f * b.n_f * b.n_f;
+    const int cplx_elems = b.n_f * b.n_f * (b.n_f / 2 + 1);
+    ESP_FFT(cufftPlanMany(&b.fwd, 3, dims, nullptr, 1, real_elems, nullptr, 1, cplx_elems,
+                          f32 ? CUFFT_R2C : CUFFT_D2Z, b.count));
+    b.fwd_ok = true;
+    ESP_FFT(cufftPlanMany(&b.inv, 3, dims, nullptr, 1, cplx_elems, nullptr, 1, real_elems,
+                          f32 ? CUFFT_C2R : CUFFT_Z2D, b.count));
+    b.inv_ok = true;
+    ESP_FFT(cufftSetStream(b.fwd, p->st));
+    ESP_FFT(cufftSetStream(b.inv, p->st));
+    size_t ws = 0;
+    if (cufftGetSize(b.fwd, &ws) == CUFFT_SUCCESS) p->bytes += ws;
+    if (cufftGetSize(b.inv, &ws) == CUFFT_SUCCESS) p->bytes += ws;
+  }
+  p->Q.assign(n, 0.0);
+  p->Q2.assign(n, 0.0);
+  p->e_fourier.assign(n, 0.0);
+  p->e_gather.assign(n, 0.0);
   ESP_CU(cudaStreamSynchronize(p->st));
   return ESP_OK;
 }
@@ -287,73 +386,79 @@ esp_status do_set_charges(esp_plan_s* p, const void* q, bool is_double, int wher
     }
     ESP_TRY(wait_stream(p, p->st));
   }
-  double Q = 0, Q2 = 0, Qa = 0;
-  for (long long i = 0; i < N; ++i) {
-    if (!std::isfinite(hq[i])) return fail(ESP_ERR_NONFINITE, "a charge is NaN or infinite");
-    Q += hq[i];
-    Q2 += hq[i] * hq[i];
-    Qa += std::fabs(hq[i]);
+  std::vector<double> Qs(p->nsys), Q2s(p->nsys), consts(2 * p->nsys);
+  for (int s = 0; s < p->nsys; ++s) {
+    const espk::SysDesc& d = p->descs[s];
+    double Q = 0, Q2 = 0, Qa = 0;
+    for (long long i = d.atom0; i < d.atom0 + d.n_atoms; ++i) {
+      if (!std::isfinite(hq[i])) return fail(ESP_ERR_NONFINITE, "a charge is NaN or infinite");
+      Q += hq[i];
+      Q2 += hq[i] * hq[i];
+      Qa += std::fabs(hq[i]);
+    }
+    const bool neutral = std::fabs(Q) <= 1e-10 * std::max(1.0, Qa);
+    if (!neutral && !p->allow_bg) {
+      const std::string who = p->nsys > 1 ? "of system " + std::to_string(s) + " " : "";
+      return fail(ESP_ERR_NOT_NEUTRAL, "sum of charges " + who + "is " + std::to_string(Q) +
+                                           "; set allow_background for a neutralising background");
+    }
+    Qs[s] = neutral ? 0.0 : Q;
+    Q2s[s] = Q2;
   }
-  if (std::fabs(Q) > 1e-10 * std::max(1.0, Qa) && !p->allow_bg)
-    return fail(ESP_ERR_NOT_NEUTRAL, "sum of charges is " + std::to_string(Q) +
-                                         "; set allow_background for a neutralising background");
-  if (std::fabs(Q) <= 1e-10 * std::max(1.0, Qa)) Q = 0.0;
+  for (int s = 0; s < p->nsys; ++s) {
+    double bg_shift;
+    espe::charge_constants(p->hps[s], Qs[s], Q2s[s], &consts[2 * s], &consts[2 * s + 1], &bg_shift);
+    p->descs[s].bg_shift = bg_shift;
+  }
   ESP_CU(cudaMemcpyAsync(p->d_qstage, hq.data(), N * sizeof(double), cudaMemcpyHostToDevice, p->st));
   ESP_CU((cudaError_t)L::convert_charges(p->d_qstage, true, (real*)p->d_q, N, p->st));
-  double consts[2], bg_shift;
-  espe::charge_constants(p->hp, Q, Q2, &consts[0], &consts[1], &bg_shift);
-  p->hp.desc.bg_shift = bg_shift;
-  espk::SysDesc d = p->hp.desc;
-  ESP_CU(cudaMemcpyAsync(p->d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, p->st));
-  ESP_CU(cudaMemcpyAsync(p->d_consts, consts, sizeof(consts), cudaMemcpyHostToDevice, p->st));
+  ESP_CU(cudaMemcpyAsync(p->d_desc, p->descs.data(), p->nsys * sizeof(espk::SysDesc),
+                         cudaMemcpyHostToDevice, p->st));
+  ESP_CU(cudaMemcpyAsync(p->d_consts, consts.data(), consts.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         p->st));
   ESP_TRY(wait_stream(p, p->st));
-  p->Q = Q;
-  p->Q2 = Q2;
+  p->Q = Qs;
+  p->Q2 = Q2s;
   p->have_q = true;
+  return ESP_OK;
+}
+
+// Steps A0-A1: ingest (wrap, convert, finite check, cell keys) and the
+// counting-sort scan of positions at `src` (device memory).
+template <typename real>
+esp_status launch_sort(esp_plan_s* p, const void* src, bool src_double) {
+  using L = espk::Launch<real>;
+  ESP_CU(cudaMemsetAsync(p->d_count, 0, p->n_keys * sizeof(uint32_t), p->st));
+  ESP_CU(L::ingest(p->d_desc, p->d_chunks, p->n_chunks, src, src_double, p->d_coord, p->d_key,
+                   p->d_rank, p->d_count, p->d_err, p->st));
+  ESP_CU(espk::launch_scan(p->d_count, p->d_start, p->d_tiles, p->n_keys, p->st));
   return ESP_OK;
 }
 
 template <typename real>
 esp_status do_set_positions(esp_plan_s* p, const void* xyz, bool is_double, int where) {
-  using L = espk::Launch<real>;
   const long long N = p->N;
   const void* src = xyz;
-  bool src_double = is_double;
   rec(p, 0, p->st);
   if (where == ESP_HOST && N > 0) {
     ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, N * 3 * (is_double ? sizeof(double) : sizeof(float)),
                            cudaMemcpyHostToDevice, p->st));
     src = p->d_pos;
   }
-  ESP_CU(cudaMemsetAsync(p->d_count, 0, p->hp.n_keys * sizeof(uint32_t), p->st));
-  ESP_CU(L::ingest(p->d_desc, p->d_chunks, p->n_chunks, src, src_double, p->d_coord, p->d_key,
-                   p->d_rank, p->d_count, p->d_err, p->st));
-  ESP_CU(espk::launch_scan(p->d_count, p->d_start, p->d_tiles, p->hp.n_keys, p->st));
+  ESP_TRY(launch_sort<real>(p, src, is_double));
   rec(p, 1, p->st);
   p->have_pos = true;
   if (where == ESP_HOST) return wait_stream(p, p->st);
   return ESP_OK;
 }
 
+// Every kernel and FFT of one compute on the pool, enqueued without any
+// host synchronisation (and therefore capturable in a CUDA graph).
 template <typename real>
-esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potential, bool out_double,
-                      int where) {
+esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double, double* outE) {
   using L = espk::Launch<real>;
-  if (!p->have_q) return fail(ESP_ERR_NOT_READY, "charges not set");
-  if (!p->have_pos) return fail(ESP_ERR_NOT_READY, "positions not set");
-  const espe::HostPlan& hp = p->hp;
-  const long long N = p->N;
-  const int P = hp.info.P;
+  const espe::HostPlan& hp = p->hps[0];   // P and the polynomial tables are common to the pool
   cudaStream_t st = p->st, st2 = p->st2;
-
-  void* outF = forces;
-  void* outU = potential;
-  double* outE = energy;
-  if (where == ESP_HOST) {
-    outF = forces ? p->d_outF : nullptr;
-    outU = potential ? p->d_outU : nullptr;
-    outE = nullptr;
-  }
 
   rec(p, 2, st);
   // A1b: scatter into cell order
@@ -380,47 +485,129 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
 
   // spectral part
   rec(p, 3, st);
-  ESP_CU(cudaMemsetAsync(p->d_grid, 0, hp.grid_elems * sizeof(real), st));
-  ESP_CU(L::spread(P, p->d_desc, p->d_work, hp.n_bricks, p->smem, p->d_atoms, p->d_start,
+  ESP_CU(cudaMemsetAsync(p->d_grid, 0, p->grid_total * sizeof(real), st));
+  ESP_CU(L::spread(p->P, p->d_desc, p->d_work, p->n_work, p->smem, p->d_atoms, p->d_start,
                    (real*)p->d_grid, si, p->d_err, st));
   rec(p, 4, st);
-  if (sizeof(real) == 4)
-    ESP_FFT(cufftExecR2C(p->fwd, (cufftReal*)p->d_grid, (cufftComplex*)p->d_spec));
-  else
-    ESP_FFT(cufftExecD2Z(p->fwd, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
+  for (Bucket& b : p->buckets) {
+    if (sizeof(real) == 4)
+      ESP_FFT(cufftExecR2C(b.fwd, (cufftReal*)p->d_grid + b.grid0, (cufftComplex*)p->d_spec + b.spec0));
+    else
+      ESP_FFT(cufftExecD2Z(b.fwd, (cufftDoubleReal*)p->d_grid + b.grid0,
+                           (cufftDoubleComplex*)p->d_spec + b.spec0));
+  }
   rec(p, 5, st);
-  ESP_CU(L::scale(p->d_desc, 1, p->n_fourier_blocks, p->d_spec, (const real*)p->d_tabs, p->d_fourier, st));
+  ESP_CU(L::scale(p->d_desc, p->nsys, p->F, p->d_spec, (const real*)p->d_tabs, p->d_fourier, st));
   rec(p, 6, st);
-  if (sizeof(real) == 4)
-    ESP_FFT(cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
-  else
-    ESP_FFT(cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
+  for (Bucket& b : p->buckets) {
+    if (sizeof(real) == 4)
+      ESP_FFT(cufftExecC2R(b.inv, (cufftComplex*)p->d_spec + b.spec0, (cufftReal*)p->d_grid + b.grid0));
+    else
+      ESP_FFT(cufftExecZ2D(b.inv, (cufftDoubleComplex*)p->d_spec + b.spec0,
+                           (cufftDoubleReal*)p->d_grid + b.grid0));
+  }
   rec(p, 7, st);
-  ESP_CU(L::gather(P, p->d_desc, p->d_work, hp.n_bricks, p->smem, p->d_atoms, p->d_start,
+  ESP_CU(L::gather(p->P, p->d_desc, p->d_work, p->n_work, p->smem, p->d_atoms, p->d_start,
                    (const real*)p->d_grid, p->d_far, si, p->d_err, st));
   rec(p, 8, st);
   // join and finish
   if (!serial) ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
   ESP_CU(L::finalize(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_perm, p->d_far, p->d_near,
                      outF, outU, out_double, p->d_partials, st));
-  ESP_CU(espk::launch_energy(p->d_desc, 1, p->d_fourier, p->n_fourier_blocks, p->d_partials,
-                             p->n_chunks, p->d_chunk_first, p->d_consts, p->d_eout, outE, st));
+  ESP_CU(espk::launch_energy(p->d_desc, p->nsys, p->d_fourier, p->F, p->d_partials, p->n_chunks,
+                             p->d_chunk_first, p->d_consts, p->d_eout, outE, st));
   rec(p, 11, st);
+  return ESP_OK;
+}
 
-  if (where == ESP_HOST) {
-    const size_t ob = out_double ? sizeof(double) : sizeof(float);
-    if (forces) ESP_CU(cudaMemcpyAsync(forces, p->d_outF, N * 3 * ob, cudaMemcpyDeviceToHost, st));
-    if (potential) ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * ob, cudaMemcpyDeviceToHost, st));
-    double e3[3];
-    ESP_CU(cudaMemcpyAsync(e3, p->d_eout, sizeof(e3), cudaMemcpyDeviceToHost, st));
-    ESP_TRY(wait_stream(p, st));
-    if (energy) *energy = e3[0];
-    p->e_fourier = e3[1];
-    p->e_gather = e3[2];
-    ESP_TRY(check_err_flag(p));
+// Host tail of a compute with host outputs: copies, bounded wait, energies,
+// device error flag.
+esp_status finish_host(esp_plan_s* p, double* energy, void* forces, void* potential, bool out_double) {
+  const long long N = p->N;
+  const size_t ob = out_double ? sizeof(double) : sizeof(float);
+  if (forces) ESP_CU(cudaMemcpyAsync(forces, p->d_outF, N * 3 * ob, cudaMemcpyDeviceToHost, p->st));
+  if (potential) ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * ob, cudaMemcpyDeviceToHost, p->st));
+  std::vector<double> e3(3 * p->nsys);
+  ESP_CU(cudaMemcpyAsync(e3.data(), p->d_eout, e3.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ESP_TRY(wait_stream(p, p->st));
+  for (int s = 0; s < p->nsys; ++s) {
+    if (energy) energy[s] = e3[3 * s];
+    p->e_fourier[s] = e3[3 * s + 1];
+    p->e_gather[s] = e3[3 * s + 2];
   }
+  return check_err_flag(p);
+}
+
+template <typename real>
+esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potential, bool out_double,
+                      int where) {
+  if (!p->have_q) return fail(ESP_ERR_NOT_READY, "charges not set");
+  if (!p->have_pos) return fail(ESP_ERR_NOT_READY, "positions not set");
+  void* outF = forces;
+  void* outU = potential;
+  double* outE = energy;
+  if (where == ESP_HOST) {
+    outF = forces ? p->d_outF : nullptr;
+    outU = potential ? p->d_outU : nullptr;
+    outE = nullptr;
+  }
+  ESP_TRY(launch_compute<real>(p, outF, outU, out_double, outE));
+  if (where == ESP_HOST) ESP_TRY(finish_host(p, energy, forces, potential, out_double));
   p->timed_valid = p->timing;
   return ESP_OK;
+}
+
+esp_status create_streams(esp_plan_s* p, const esp_plan_opts& o) {
+  if (o.stream) {
+    p->st = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(ESP_ERR_CUDA, "stream creation failed");
+    p->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(ESP_ERR_CUDA, "stream/event creation failed");
+  for (auto& e : p->tev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(ESP_ERR_CUDA, "event creation failed");
+  return ESP_OK;
+}
+
+// Device state of a pool whose host plans p->hps are made.
+esp_status finish_pool(esp_plan_s* p, const esp_plan_opts& o) {
+  p->prec = o.precision;
+  p->device = o.device;
+  p->timeout_ms = o.timeout_ms > 0 ? o.timeout_ms : 60000.0;
+  p->allow_bg = o.allow_background != 0;
+  p->nsys = (int)p->hps.size();
+  p->P = p->hps[0].info.P;
+  for (const espe::HostPlan& hp : p->hps)
+    if (hp.info.P != p->P || hp.near_nc != p->hps[0].near_nc)
+      return fail(ESP_ERR_INTERNAL, "systems of one pool differ in stencil width or local-part terms");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(ESP_ERR_CUDA, "no CUDA device available");
+  }
+  if (o.device < 0 || o.device >= ndev) return fail(ESP_ERR_INVALID_ARG, "device ordinal out of range");
+  DeviceGuard g(p->device);
+  ESP_TRY(create_streams(p, o));
+  ESP_TRY(p->prec == ESP_FP32 ? build_buffers<float>(p) : build_buffers<double>(p));
+  for (espe::HostPlan& hp : p->hps) hp.info.device_bytes = p->bytes;
+  return ESP_OK;
+}
+
+esp_plan_opts resolve_opts(const esp_plan_opts* opts) {
+  esp_plan_opts o;
+  if (opts) o = *opts;
+  else esp_plan_opts_init(&o);
+  return o;
+}
+
+bool cubic(const esp_box& b) {
+  const double L = b.L[0];
+  return std::fabs(b.L[1] - L) <= 1e-12 * std::fabs(L) && std::fabs(b.L[2] - L) <= 1e-12 * std::fabs(L);
 }
 
 }  // namespace
@@ -442,57 +629,23 @@ esp_status esp_plan(const esp_box* box, int64_t N, double tolerance, const esp_p
                     esp_plan_t* out) {
   if (!box || !out) return fail(ESP_ERR_INVALID_ARG, "box and out must not be NULL");
   *out = nullptr;
-  esp_plan_opts o;
-  if (opts) o = *opts;
-  else esp_plan_opts_init(&o);
-  const double L = box->L[0];
-  if (!(std::fabs(box->L[1] - L) <= 1e-12 * std::fabs(L) && std::fabs(box->L[2] - L) <= 1e-12 * std::fabs(L)))
-    return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
+  const esp_plan_opts o = resolve_opts(opts);
+  if (!cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
   esp_plan_s* p = new esp_plan_s();
+  p->hps.resize(1);
   std::string msg;
-  esp_status s = espe::make_host_plan(L, N, tolerance, o, p->hp, msg);
+  esp_status s = espe::make_host_plan(box->L[0], N, tolerance, o, p->hps[0], msg);
   if (s != ESP_OK) {
     delete p;
     return fail(s, msg);
   }
-  p->prec = o.precision;
-  p->device = o.device;
-  p->timeout_ms = o.timeout_ms > 0 ? o.timeout_ms : 60000.0;
-  p->allow_bg = o.allow_background != 0;
-  p->N = N;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
-    delete p;
-    return fail(ESP_ERR_CUDA, "no CUDA device available");
-  }
-  if (o.device < 0 || o.device >= ndev) {
-    delete p;
-    return fail(ESP_ERR_INVALID_ARG, "device ordinal out of range");
-  }
-  DeviceGuard g(p->device);
-  auto bail = [&](esp_status st) {
-    std::string m = g_error;
+  s = finish_pool(p, o);
+  if (s != ESP_OK) {
+    const std::string m = g_error;
     release(p);
     delete p;
-    return fail(st, m);
-  };
-  if (o.stream) {
-    p->st = (cudaStream_t)o.stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess)
-      return bail(fail(ESP_ERR_CUDA, "stream creation failed"));
-    p->own_stream = true;
+    return fail(s, m);
   }
-  if (cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
-    return bail(fail(ESP_ERR_CUDA, "stream/event creation failed"));
-  for (auto& e : p->tev)
-    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(ESP_ERR_CUDA, "event creation failed"));
-  s = p->prec == ESP_FP32 ? build_buffers<float>(p) : build_buffers<double>(p);
-  if (s != ESP_OK) return bail(s);
-  p->hp.info.device_bytes = p->bytes;
   *out = p;
   return ESP_OK;
 }
@@ -500,15 +653,11 @@ esp_status esp_plan(const esp_box* box, int64_t N, double tolerance, const esp_p
 esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const esp_plan_opts* opts,
                           esp_plan_params* out) {
   if (!box || !out) return fail(ESP_ERR_INVALID_ARG, "box and out must not be NULL");
-  esp_plan_opts o;
-  if (opts) o = *opts;
-  else esp_plan_opts_init(&o);
-  const double L = box->L[0];
-  if (!(std::fabs(box->L[1] - L) <= 1e-12 * std::fabs(L) && std::fabs(box->L[2] - L) <= 1e-12 * std::fabs(L)))
-    return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
+  const esp_plan_opts o = resolve_opts(opts);
+  if (!cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
   espe::HostPlan hp;
   std::string msg;
-  esp_status s = espe::make_host_plan(L, N, tolerance, o, hp, msg);
+  esp_status s = espe::make_host_plan(box->L[0], N, tolerance, o, hp, msg);
   if (s != ESP_OK) return fail(s, msg);
   const size_t rb = o.precision == ESP_FP32 ? 4 : 8;
   const size_t ab = o.precision == ESP_FP32 ? 16 : 32;
@@ -522,7 +671,7 @@ esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const
 
 esp_status esp_plan_info(esp_plan_t p, esp_plan_params* out) {
   if (!p || !out) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
-  *out = p->hp.info;
+  *out = p->hps[0].info;
   return ESP_OK;
 }
 
@@ -582,6 +731,7 @@ esp_status esp_synchronize(esp_plan_t p) {
 
 esp_status esp_set_timing(esp_plan_t p, int enable) {
   if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL plan");
+  if (enable < 0 || enable > 2) return fail(ESP_ERR_INVALID_ARG, "timing mode must be 0, 1 or 2");
   p->timing = enable != 0;
   p->timing_mode = enable;
   return ESP_OK;
@@ -612,8 +762,8 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
 
 esp_status esp_last_spectral_energy(esp_plan_t p, double* e_fourier, double* e_gather) {
   if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL plan");
-  if (e_fourier) *e_fourier = p->e_fourier;
-  if (e_gather) *e_gather = p->e_gather;
+  if (e_fourier) *e_fourier = p->e_fourier[0];
+  if (e_gather) *e_gather = p->e_gather[0];
   return ESP_OK;
 }
 
@@ -627,5 +777,217 @@ esp_status esp_destroy(esp_plan_t p) {
 const char* esp_last_error(void) { return g_error.c_str(); }
 
 const char* esp_version(void) { return "esp_gb300 0.1 (sm_103a; CUDA " ESP_STR(CUDART_VERSION) ")"; }
+
+}  // extern "C"
+
+// ==================================================================== batches
+namespace {
+
+// Grid sizes of a batch: even 2^a 3^b 5^c 7^d sizes at least 12% apart, so
+// systems of similar size share one batched FFT plan.
+int bucket_size(int n_f) {
+  static const std::vector<int> ladder = [] {
+    std::vector<int> v;
+    int last = 0;
+    for (int n = 4; n <= 1024; n += 2) {
+      if (!espm::is_smooth(n)) continue;
+      if (last == 0 || n >= 1.12 * last) {
+        v.push_back(n);
+        last = n;
+      }
+    }
+    return v;
+  }();
+  for (int n : ladder)
+    if (n >= n_f) return n;
+  return n_f;
+}
+
+// Host plans of a batch: every system plans alone, the most frequent
+// SI-kernel shape c1/c becomes common (the spread and gather kernels take one
+// coefficient set), each system re-plans with it, and its grid is raised to
+// the next ladder size. A larger grid at fixed c1 only lowers the aliasing
+// estimate, so each system still meets the tolerance.
+esp_status batch_plans(const esp_box* boxes, const int64_t* N, int nsys, double tol, const esp_plan_opts& o,
+                       std::vector<espe::HostPlan>& hps) {
+  hps.assign(nsys, espe::HostPlan());
+  std::string msg;
+  std::map<long long, int> votes;
+  double c = 0.0;
+  for (int s = 0; s < nsys; ++s) {
+    if (!cubic(boxes[s]))
+      return fail(ESP_ERR_INVALID_ARG, "system " + std::to_string(s) + ": only cubic boxes are supported");
+    esp_status st = espe::make_host_plan(boxes[s].L[0], N[s], tol, o, hps[s], msg);
+    if (st != ESP_OK) return fail(st, "system " + std::to_string(s) + ": " + msg);
+    c = hps[s].info.c;
+    votes[std::llround(hps[s].info.c1 / c * 1000.0)] += 1;
+  }
+  long long ratio = votes.begin()->first;
+  int most = -1;
+  for (auto& kv : votes)
+    if (kv.second > most) { ratio = kv.first; most = kv.second; }
+  for (int s = 0; s < nsys; ++s) {
+    esp_plan_opts oo = o;
+    oo.c = c;
+    oo.c1 = c * (double)ratio / 1000.0;
+    espe::HostPlan tmp;
+    esp_status st = espe::make_host_plan(boxes[s].L[0], N[s], tol, oo, tmp, msg);
+    if (st == ESP_OK && o.n_f <= 0) {
+      oo.n_f = bucket_size(tmp.info.n_f);
+      st = espe::make_host_plan(boxes[s].L[0], N[s], tol, oo, hps[s], msg);
+    } else if (st == ESP_OK) {
+      hps[s] = tmp;
+    }
+    if (st != ESP_OK) return fail(st, "system " + std::to_string(s) + ": " + msg);
+  }
+  return ESP_OK;
+}
+
+template <typename real>
+esp_status batch_step(esp_plan_s* p) {
+  rec(p, 0, p->st);
+  ESP_TRY(launch_sort<real>(p, p->d_pos, true));
+  rec(p, 1, p->st);
+  return launch_compute<real>(p, p->d_outF, p->d_outU, true, p->d_energy);
+}
+
+esp_status run_batch_step(esp_plan_s* p) {
+  return p->prec == ESP_FP32 ? batch_step<float>(p) : batch_step<double>(p);
+}
+
+// Capture one step into p->gexec (after a first direct run has set every
+// kernel attribute and loaded every module).
+esp_status capture_batch_step(esp_plan_s* p) {
+  cudaGraph_t graph = nullptr;
+  ESP_CU(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+  esp_status s = run_batch_step(p);
+  cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+  if (s != ESP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(ESP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  p->graph = graph;
+  ESP_CU(cudaGraphInstantiate(&p->gexec, graph, 0));
+  return ESP_OK;
+}
+
+esp_plan_s* pool_of(esp_batch_t b) { return b ? &b->pool : nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+esp_status esp_batch_create(const esp_box* boxes, const int64_t* N, int n_systems, double tolerance,
+                            const esp_plan_opts* opts, esp_batch_t* out) {
+  if (!boxes || !N || !out) return fail(ESP_ERR_INVALID_ARG, "boxes, N and out must not be NULL");
+  *out = nullptr;
+  if (n_systems <= 0) return fail(ESP_ERR_INVALID_ARG, "n_systems must be positive");
+  const esp_plan_opts o = resolve_opts(opts);
+  if (!(o.r_c > 0)) return fail(ESP_ERR_INVALID_ARG, "a batch needs an explicit cutoff r_c");
+  for (int s = 0; s < n_systems; ++s)
+    if (N[s] <= 0) return fail(ESP_ERR_INVALID_ARG, "system " + std::to_string(s) + " has no atoms");
+  esp_batch_s* b = new esp_batch_s();
+  esp_plan_s* p = &b->pool;
+  esp_status s = batch_plans(boxes, N, n_systems, tolerance, o, p->hps);
+  if (s != ESP_OK) {
+    delete b;
+    return s;
+  }
+  s = finish_pool(p, o);
+  if (s != ESP_OK) {
+    const std::string m = g_error;
+    release(p);
+    delete b;
+    return fail(s, m);
+  }
+  *out = b;
+  return ESP_OK;
+}
+
+esp_status esp_batch_query(const esp_box* boxes, const int64_t* N, int n_systems, double tolerance,
+                           const esp_plan_opts* opts, esp_plan_params* out) {
+  if (!boxes || !N || !out) return fail(ESP_ERR_INVALID_ARG, "boxes, N and out must not be NULL");
+  if (n_systems <= 0) return fail(ESP_ERR_INVALID_ARG, "n_systems must be positive");
+  const esp_plan_opts o = resolve_opts(opts);
+  if (!(o.r_c > 0)) return fail(ESP_ERR_INVALID_ARG, "a batch needs an explicit cutoff r_c");
+  std::vector<espe::HostPlan> hps;
+  ESP_TRY(batch_plans(boxes, N, n_systems, tolerance, o, hps));
+  for (int s = 0; s < n_systems; ++s) out[s] = hps[s].info;
+  return ESP_OK;
+}
+
+esp_status esp_batch_info(esp_batch_t b, int sys, esp_plan_params* out) {
+  esp_plan_s* p = pool_of(b);
+  if (!p || !out) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  if (sys < 0 || sys >= p->nsys) return fail(ESP_ERR_INVALID_ARG, "system index out of range");
+  *out = p->hps[sys].info;
+  return ESP_OK;
+}
+
+esp_status esp_batch_set_charges(esp_batch_t b, const double* q, int where) {
+  esp_plan_s* p = pool_of(b);
+  if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL batch");
+  return set_charges_any(p, q, true, where);
+}
+
+esp_status esp_batch_compute(esp_batch_t b, const double* xyz, double* energies, double* forces,
+                             double* potential, int where) {
+  esp_plan_s* p = pool_of(b);
+  if (!p || !xyz) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  if (where != ESP_HOST && where != ESP_DEVICE) return fail(ESP_ERR_INVALID_ARG, "bad 'where'");
+  if (!p->have_q) return fail(ESP_ERR_NOT_READY, "charges not set");
+  DeviceGuard g(p->device);
+  const long long N = p->N;
+  ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, N * 3 * sizeof(double),
+                         where == ESP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, p->st));
+  p->have_pos = true;
+  if (p->timing) {
+    ESP_TRY(run_batch_step(p));
+  } else if (p->gexec) {
+    ESP_CU(cudaGraphLaunch(p->gexec, p->st));
+  } else if (p->direct_runs == 0) {
+    ESP_TRY(run_batch_step(p));
+    p->direct_runs = 1;
+  } else {
+    ESP_TRY(capture_batch_step(p));
+    ESP_CU(cudaGraphLaunch(p->gexec, p->st));
+  }
+  p->timed_valid = p->timing;
+  const cudaMemcpyKind kind = where == ESP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (forces) ESP_CU(cudaMemcpyAsync(forces, p->d_outF, N * 3 * sizeof(double), kind, p->st));
+  if (potential) ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * sizeof(double), kind, p->st));
+  if (energies) ESP_CU(cudaMemcpyAsync(energies, p->d_energy, p->nsys * sizeof(double), kind, p->st));
+  if (where == ESP_HOST) {
+    ESP_TRY(wait_stream(p, p->st));
+    return check_err_flag(p);
+  }
+  return ESP_OK;
+}
+
+esp_status esp_batch_synchronize(esp_batch_t b) {
+  esp_plan_s* p = pool_of(b);
+  if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL batch");
+  return esp_synchronize(p);
+}
+
+esp_status esp_batch_set_timing(esp_batch_t b, int enable) {
+  esp_plan_s* p = pool_of(b);
+  if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL batch");
+  return esp_set_timing(p, enable);
+}
+
+esp_status esp_batch_phase_times(esp_batch_t b, float* ms, int n) {
+  esp_plan_s* p = pool_of(b);
+  if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL batch");
+  return esp_phase_times(p, ms, n);
+}
+
+esp_status esp_batch_destroy(esp_batch_t b) {
+  if (!b) return ESP_OK;
+  release(&b->pool);
+  delete b;
+  return ESP_OK;
+}
 
 }  // extern "C"

@@ -15,10 +15,59 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace espe {
 
 static const double kPi = 3.14159265358979323846;
+
+// The PSWF solves depend only on (eps), (c) and (c1, P); batches plan many
+// systems with the same values, so the results are kept per process.
+static std::mutex g_cache_mu;
+
+static double cached_c(double eps) {
+  static std::map<double, double> cache;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache.find(eps);
+    if (it != cache.end()) return it->second;
+  }
+  const double c = espm::c_from_tolerance(eps);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  cache[eps] = c;
+  return c;
+}
+
+static espm::Split cached_pswf_split(double c) {
+  static std::map<double, espm::Split> cache;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache.find(c);
+    if (it != cache.end()) return it->second;
+  }
+  espm::Split s = espm::make_pswf_split(c);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  if (cache.size() > 64) cache.clear();
+  cache[c] = s;
+  return s;
+}
+
+static espm::Window cached_window(double c1, int P) {
+  static std::map<std::pair<double, int>, espm::Window> cache;
+  const auto key = std::make_pair(c1, P);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  espm::Window w = espm::make_window(c1, P);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  if (cache.size() > 256) cache.clear();
+  cache[key] = w;
+  return w;
+}
 
 // Sum over ky, kz of |chihat(2 pi r_c |k| / L)| / |k|^2 for each kx in I.
 static std::vector<double> alias_rows(const espm::Split& s, int n_f, double L, double r_c) {
@@ -105,6 +154,103 @@ static double fit(F f, int deg, std::vector<double>& out) {
   return err;
 }
 
+// Piecewise SI-kernel polynomials: piece a of phi on t in [a - P/2 + 1 ... ]
+// as a polynomial in y = 2 delta - 1, both precisions.
+struct SiTables {
+  espk::SICoef<float> si32{};
+  espk::SICoef<double> si64{};
+  double err32 = 0, err64 = 0;
+};
+
+static SiTables make_si_tables(const espm::Window& win, int P) {
+  SiTables t;
+  std::vector<double> co;
+  for (int a = 0; a < P; ++a) {
+    auto fa = [&](double y) { return win.phi(0.5 * (y + 1.0) + 0.5 * P - 1.0 - a); };
+    t.err32 = std::max(t.err32, fit(fa, espk::Deg<float>::si - 1, co));
+    for (int k = 0; k < espk::Deg<float>::si; ++k) t.si32.c[a][k] = (float)co[k];
+    t.err64 = std::max(t.err64, fit(fa, espk::Deg<double>::si - 1, co));
+    for (int k = 0; k < espk::Deg<double>::si; ++k) t.si64.c[a][k] = co[k];
+  }
+  return t;
+}
+
+static const SiTables& si_tables(const espm::Window& win, int P) {
+  static std::map<std::pair<double, int>, SiTables> cache;
+  const auto key = std::make_pair(win.c1, P);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  SiTables t = make_si_tables(win, P);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  return cache.emplace(key, t).first->second;
+}
+
+// Local-part polynomials in y = 2s - 1, s = (r/r_c)^2:
+// H(s) = g(x)/x and K(s) = (x chi(x) - g(x))/x^3, x = sqrt(s), with K in the
+// cancellation-free form K = (1/x) int_0^1 u chi'(x u) du.
+struct NearTables {
+  espk::NearCoef<float> nc32{};
+  espk::NearCoef<double> nc64{};
+  int terms32 = 0;
+  double err32 = 0, err64 = 0;
+};
+
+static NearTables make_near_tables(const espm::Split& split, double tol) {
+  NearTables t;
+  std::vector<double> gq_x, gq_w, co;
+  espm::gauss_legendre(48, gq_x, gq_w);
+  for (size_t i = 0; i < gq_x.size(); ++i) { gq_x[i] = 0.5 * (gq_x[i] + 1.0); gq_w[i] *= 0.5; }
+  auto g_of = [&](double x) {
+    return split.kind == 1 ? std::erf(std::sqrt(split.alpha) * x) : split.psi.integral0(x) / split.C0;
+  };
+  auto fh = [&](double y) {
+    const double x = std::sqrt(std::max(0.0, 0.5 * (y + 1.0)));
+    return x > 1e-12 ? g_of(x) / x : split.chi0();
+  };
+  auto fk = [&](double y) {
+    const double x = std::max(1e-9, std::sqrt(std::max(0.0, 0.5 * (y + 1.0))));
+    double acc = 0.0;
+    for (size_t i = 0; i < gq_x.size(); ++i) acc += gq_w[i] * gq_x[i] * split.dchi(x * gq_x[i]);
+    return acc / x;
+  };
+  // FP32: 10 terms when that fit is 100x below the tolerance, else 12
+  const double scale = std::max(std::fabs(fh(-1.0)), std::fabs(fk(1.0)));
+  for (int terms : {10, espk::Deg<float>::nr}) {
+    std::vector<double> ch, ck;
+    const double e1 = fit(fh, terms - 1, ch);
+    const double e2 = fit(fk, terms - 1, ck);
+    t.terms32 = terms;
+    t.err32 = std::max(e1, e2);
+    for (int k = 0; k < espk::Deg<float>::nr; ++k) {
+      t.nc32.h[k] = k < terms ? (float)ch[k] : 0.0f;
+      t.nc32.k[k] = k < terms ? (float)ck[k] : 0.0f;
+    }
+    if (t.err32 <= 0.01 * tol * std::max(1.0, scale)) break;
+  }
+  const double e3 = fit(fh, espk::Deg<double>::nr - 1, co);
+  for (int k = 0; k < espk::Deg<double>::nr; ++k) t.nc64.h[k] = co[k];
+  const double e4 = fit(fk, espk::Deg<double>::nr - 1, co);
+  for (int k = 0; k < espk::Deg<double>::nr; ++k) t.nc64.k[k] = co[k];
+  t.err64 = std::max(e3, e4);
+  return t;
+}
+
+static const NearTables& near_tables(const espm::Split& split, double tol) {
+  static std::map<std::pair<std::pair<int, double>, double>, NearTables> cache;
+  const auto key = std::make_pair(std::make_pair(split.kind, split.kind == 1 ? split.alpha : split.c), tol);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  NearTables t = make_near_tables(split, tol);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  return cache.emplace(key, t).first->second;
+}
+
 static int tile_edge(const espk::SysDesc& d, int P, int precision) {
   int T = 0;
   for (int cb = 0; cb < d.nb; ++cb) {
@@ -134,14 +280,14 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   if (kernel != ESP_KERNEL_PSWF && kernel != ESP_KERNEL_GAUSS) { msg = "unknown kernel"; return ESP_ERR_INVALID_ARG; }
   const int pmax = prec == ESP_FP32 ? 12 : 16;
 
-  const double c = o.c > 0 ? o.c : espm::c_from_tolerance(tol);
+  const double c = o.c > 0 ? o.c : cached_c(tol);
   const int P = o.P > 0 ? o.P : espm::stencil_width(tol);
   if (P < espk::kMinP || P > pmax) {
     msg = "stencil width P=" + std::to_string(P) + " outside the compiled range [4, " + std::to_string(pmax) + "]";
     return ESP_ERR_UNSUPPORTED;
   }
   const double alpha = kernel == ESP_KERNEL_GAUSS ? (o.alpha > 0 ? o.alpha : std::log(1.0 / tol)) : 0.0;
-  espm::Split split = kernel == ESP_KERNEL_PSWF ? espm::make_pswf_split(c) : espm::make_gauss_split(alpha);
+  espm::Split split = kernel == ESP_KERNEL_PSWF ? cached_pswf_split(c) : espm::make_gauss_split(alpha);
 
   double r_c = o.r_c;
   if (!(r_c > 0)) {
@@ -171,7 +317,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   if (n_f > 1024) { msg = "grid too large (n_f > 1024): raise r_c or the tolerance"; return ESP_ERR_UNSUPPORTED; }
   double best_c1 = ratios[0] * c, best_alias = 1e300;
   std::vector<espm::Window> windows;
-  for (double r : ratios) windows.push_back(espm::make_window(r * c, P));
+  for (double r : ratios) windows.push_back(cached_window(r * c, P));
   for (int step = 0; step < 8; ++step) {
     const std::vector<double> rows = alias_rows(split, n_f, L, r_c);
     best_alias = 1e300;
@@ -182,7 +328,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     if (o.n_f > 0 || best_alias <= 0.5 * tol || n_f >= 1024) break;
     n_f = espm::round_grid(n_f + 1);
   }
-  const espm::Window win = espm::make_window(best_c1, P);
+  const espm::Window win = cached_window(best_c1, P);
 
   // cell list and bricks: cell edge w >= r_c / reach. A reach of 3 (smaller
   // cells) reads fewer non-neighbours in the local part; it needs at least a
@@ -244,56 +390,15 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.prefactor = o.prefactor > 0 ? o.prefactor : 1.0;
 
   // polynomial tables
-  double si_err = 0.0, near_err = 0.0;
-  std::vector<double> co;
-  for (int a = 0; a < P; ++a) {
-    auto fa = [&](double y) { return win.phi(0.5 * (y + 1.0) + 0.5 * P - 1.0 - a); };
-    si_err = std::max(si_err, fit(fa, espk::Deg<float>::si - 1, co) * (prec == ESP_FP32 ? 1.0 : 0.0));
-    for (int k = 0; k < espk::Deg<float>::si; ++k) hp.si32.c[a][k] = (float)co[k];
-    const double e64 = fit(fa, espk::Deg<double>::si - 1, co);
-    if (prec == ESP_FP64) si_err = std::max(si_err, e64);
-    for (int k = 0; k < espk::Deg<double>::si; ++k) hp.si64.c[a][k] = co[k];
-  }
-  // local part: H(s) = g(x)/x and K(s) = (x chi(x) - g(x))/x^3, s = x^2 = (y+1)/2;
-  // K by the cancellation-free form K = (1/x) int_0^1 u chi'(x u) du
-  std::vector<double> gq_x, gq_w;
-  espm::gauss_legendre(48, gq_x, gq_w);
-  for (size_t i = 0; i < gq_x.size(); ++i) { gq_x[i] = 0.5 * (gq_x[i] + 1.0); gq_w[i] *= 0.5; }
-  auto g_of = [&](double x) {
-    return split.kind == 1 ? std::erf(std::sqrt(split.alpha) * x) : split.psi.integral0(x) / split.C0;
-  };
-  auto fh = [&](double y) {
-    const double x = std::sqrt(std::max(0.0, 0.5 * (y + 1.0)));
-    return x > 1e-12 ? g_of(x) / x : split.chi0();
-  };
-  auto fk = [&](double y) {
-    const double x = std::max(1e-9, std::sqrt(std::max(0.0, 0.5 * (y + 1.0))));
-    double acc = 0.0;
-    for (size_t i = 0; i < gq_x.size(); ++i) acc += gq_w[i] * gq_x[i] * split.dchi(x * gq_x[i]);
-    return acc / x;
-  };
-  {
-    // FP32: 10 terms when that fit is 100x below the tolerance, else 12
-    double e1 = 0, e2 = 0;
-    for (int terms : {10, espk::Deg<float>::nr}) {
-      std::vector<double> ch, ck;
-      e1 = fit(fh, terms - 1, ch);
-      e2 = fit(fk, terms - 1, ck);
-      const double scale = std::max(std::fabs(fh(-1.0)), std::fabs(fk(1.0)));
-      hp.near_nc = terms;
-      for (int k = 0; k < espk::Deg<float>::nr; ++k) {
-        hp.nc32.h[k] = k < terms ? (float)ch[k] : 0.0f;
-        hp.nc32.k[k] = k < terms ? (float)ck[k] : 0.0f;
-      }
-      if (std::max(e1, e2) <= 0.01 * tol * std::max(1.0, scale)) break;
-    }
-    double e3 = fit(fh, espk::Deg<double>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.h[k] = co[k];
-    double e4 = fit(fk, espk::Deg<double>::nr - 1, co);
-    for (int k = 0; k < espk::Deg<double>::nr; ++k) hp.nc64.k[k] = co[k];
-    near_err = prec == ESP_FP32 ? std::max(e1, e2) : std::max(e3, e4);
-    if (prec == ESP_FP64) hp.near_nc = espk::Deg<double>::nr;
-  }
+  const SiTables& sit = si_tables(win, P);
+  hp.si32 = sit.si32;
+  hp.si64 = sit.si64;
+  const double si_err = prec == ESP_FP32 ? sit.err32 : sit.err64;
+  const NearTables& nt = near_tables(split, tol);
+  hp.nc32 = nt.nc32;
+  hp.nc64 = nt.nc64;
+  hp.near_nc = prec == ESP_FP32 ? nt.terms32 : espk::Deg<double>::nr;
+  const double near_err = prec == ESP_FP32 ? nt.err32 : nt.err64;
 
   // influence tables (Eq. pk, Phi in grid units)
   hp.G.assign(d.gsize, 0.0);

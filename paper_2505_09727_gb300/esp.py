@@ -85,6 +85,18 @@ _SIGNATURES = {
     "esp_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "esp_last_spectral_energy": (ctypes.c_int, [_P, _D, _D]),
     "esp_destroy": (ctypes.c_int, [_P]),
+    "esp_batch_create": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
+    "esp_batch_query": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                       ctypes.c_double, ctypes.POINTER(esp_plan_opts),
+                                       ctypes.POINTER(esp_plan_params)]),
+    "esp_batch_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(esp_plan_params)]),
+    "esp_batch_set_charges": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "esp_batch_compute": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+    "esp_batch_synchronize": (ctypes.c_int, [_P]),
+    "esp_batch_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "esp_batch_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "esp_batch_destroy": (ctypes.c_int, [_P]),
     "esp_local_part_static": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
                                              ctypes.POINTER(esp_plan_opts), _P, _P, _P, _P, _P]),
     "esp_last_error": (ctypes.c_char_p, []),
@@ -253,6 +265,69 @@ def esp_local_part_static(L: float, N: int, tolerance: float, xyz, q, energy=Non
         _ptr(energy)[0], _ptr(forces)[0], _ptr(potential)[0]))
 
 
+def esp_batch_create(boxes, N, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> int:
+    """Batch of independent cubic systems: boxes[s] is the edge L of system s."""
+    if opts is None:
+        opts = make_opts(**kw)
+    n = len(boxes)
+    if len(N) != n:
+        raise ValueError("boxes and N differ in length")
+    arr = (esp_box * n)(*[esp_box((ctypes.c_double * 3)(L, L, L)) for L in boxes])
+    counts = (ctypes.c_int64 * n)(*[int(x) for x in N])
+    out = _P()
+    _check(load_library().esp_batch_create(arr, counts, n, float(tolerance), ctypes.byref(opts),
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def esp_batch_query(boxes, N, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> list:
+    """Planner only (no GPU needed): per-system parameters esp_batch_create would choose."""
+    if opts is None:
+        opts = make_opts(**kw)
+    n = len(boxes)
+    arr = (esp_box * n)(*[esp_box((ctypes.c_double * 3)(L, L, L)) for L in boxes])
+    counts = (ctypes.c_int64 * n)(*[int(x) for x in N])
+    out = (esp_plan_params * n)()
+    _check(load_library().esp_batch_query(arr, counts, n, float(tolerance), ctypes.byref(opts), out))
+    return [out[i].as_dict() for i in range(n)]
+
+
+def esp_batch_info(batch: int, sys: int) -> dict:
+    p = esp_plan_params()
+    _check(load_library().esp_batch_info(_P(batch), int(sys), ctypes.byref(p)))
+    return p.as_dict()
+
+
+def esp_batch_set_charges(batch: int, q, where: int | None = None):
+    ptr, w = _ptr(q, np.float64 if isinstance(q, np.ndarray) else None)
+    _check(load_library().esp_batch_set_charges(_P(batch), ptr, where if where is not None else w))
+
+
+def esp_batch_compute(batch: int, xyz, energies=None, forces=None, potential=None, where: int | None = None):
+    """FP64 buffers in the concatenated atom order; energies has one entry per system."""
+    ptr, w = _ptr(xyz, np.float64 if isinstance(xyz, np.ndarray) else None)
+    _check(load_library().esp_batch_compute(_P(batch), ptr, _ptr(energies)[0], _ptr(forces)[0],
+                                            _ptr(potential)[0], where if where is not None else w))
+
+
+def esp_batch_synchronize(batch: int):
+    _check(load_library().esp_batch_synchronize(_P(batch)))
+
+
+def esp_batch_set_timing(batch: int, enable: int = 1):
+    _check(load_library().esp_batch_set_timing(_P(batch), int(enable)))
+
+
+def esp_batch_phase_times(batch: int) -> dict:
+    buf = (ctypes.c_float * len(PHASES))()
+    _check(load_library().esp_batch_phase_times(_P(batch), buf, len(PHASES)))
+    return dict(zip(PHASES, list(buf)))
+
+
+def esp_batch_destroy(batch: int):
+    _check(load_library().esp_batch_destroy(_P(batch)))
+
+
 def esp_last_error() -> str:
     msg = load_library().esp_last_error()
     return msg.decode() if msg else ""
@@ -290,6 +365,46 @@ class Plan:
     def close(self):
         if self.handle:
             esp_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning handle of a batch: host arrays in, host arrays out."""
+
+    def __init__(self, boxes, N, tolerance: float, **opts):
+        self.handle = esp_batch_create(boxes, N, tolerance, **opts)
+        self.N = [int(x) for x in N]
+        self.offsets = np.concatenate([[0], np.cumsum(self.N)]).astype(np.int64)
+
+    def info(self, sys: int) -> dict:
+        return esp_batch_info(self.handle, sys)
+
+    def set_charges(self, q, where=None):
+        esp_batch_set_charges(self.handle, q, where)
+
+    def compute(self, xyz):
+        """Returns (energies (S,), forces (sum N, 3), potential (sum N,))."""
+        e = np.zeros(len(self.N))
+        f = np.zeros((int(self.offsets[-1]), 3))
+        u = np.zeros(int(self.offsets[-1]))
+        esp_batch_compute(self.handle, np.ascontiguousarray(xyz, dtype=np.float64), e, f, u, ESP_HOST)
+        return e, f, u
+
+    def close(self):
+        if self.handle:
+            esp_batch_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

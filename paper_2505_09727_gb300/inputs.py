@@ -168,3 +168,14 @@ def perturb(system: System, sigma: float, seed: int) -> System:
     rng = np.random.default_rng(seed)
     pos = _wrap(system.pos + rng.normal(0.0, sigma, size=system.pos.shape), system.L)
     return System(pos, system.q.copy(), system.L, system.name)
+
+
+def electrolyte_batch(sizes, seed: int = 9727) -> list[System]:
+    """One electrolyte box per atom count; system s uses seed + s."""
+    return [electrolyte(int(n), seed=seed + s) for s, n in enumerate(sizes)]
+
+
+def concat(systems: list[System]) -> tuple[np.ndarray, np.ndarray]:
+    """Positions (sum N, 3) and charges (sum N,) of systems in order."""
+    return (np.ascontiguousarray(np.concatenate([s.pos for s in systems])),
+            np.ascontiguousarray(np.concatenate([s.q for s in systems])))

@@ -101,7 +101,12 @@ def test_fp32_matches_oracle(esp, name):
     g = gpu_solve(esp, s, eps, r_c=r_c, precision=esp.ESP_FP32)
     ref = oracle_same(s, eps, g["info"])
     assert force_error(s, g["forces"], ref["forces"]) <= FP32_PARITY
-    assert abs(g["energy"] - ref["energy"]) <= FP32_PARITY * abs(ref["energy"])
+    # The FP32 spectral potential at each charge still holds its own smooth
+    # self-interaction q_i chi(0)/(4 pi r_c), removed afterwards in FP64; its
+    # rounding is relative to that part, which for random +-1 charges is far
+    # larger than the (cancelling) total energy.
+    e_self = 0.5 * float(np.sum(s.q * ref["self_term"]))
+    assert abs(g["energy"] - ref["energy"]) <= FP32_PARITY * max(abs(ref["energy"]), abs(e_self))
     assert rel_rms(g["potential"], ref["potential"]) <= FP32_PARITY
 
 
