@@ -98,8 +98,10 @@ typedef struct {
   int brick_cells;     /* tuning: cells per spread/gather brick edge; 0 auto */
   double timeout_ms;   /* deadline of host waits; 0 = 60000                  */
   int cell_reach;      /* tuning: cell edge ~ r_c / cell_reach (2 or 3; 0 auto) */
-  int near_variant;    /* tuning: local-part kernel, 1 = pairs evaluated in the
-                          scan, 2 = pairs queued per lane; 0 = default (1)   */
+  int near_variant;    /* tuning: local-part kernel, 1 = one thread per atom,
+                          pairs evaluated in the scan, 2 = the same with pairs
+                          queued per lane, 3 = one warp per cluster of 8 atoms
+                          (FP32 only); 0 = default (3 in FP32, 1 in FP64)     */
   int reserved[6];
 } esp_plan_opts;
 

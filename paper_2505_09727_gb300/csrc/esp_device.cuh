@@ -40,6 +40,9 @@ template <> struct Deg<double> { static constexpr int si = 18; static constexpr 
 // (cell, slab), so the local part reads only the slabs a cutoff sphere meets.
 constexpr int kSub = 4;
 
+// Atoms per i-cluster of the FP32 local part (host-visible for buffer sizes).
+constexpr int kClusterAtomsHost = 8;
+
 // SI kernel: P pieces, piece a gives the weight of grid point l0 + a as a
 // polynomial in y = 2 delta - 1, delta = t - l0 - (P/2 - 1) in (0, 1].
 template <typename real> struct SICoef { real c[kMaxP][Deg<real>::si]; };
@@ -67,6 +70,7 @@ struct SysDesc {
   long long grid0;   // first element of the system's real grid
   long long spec0;   // first element of the system's half spectrum
   long long tab0;    // first element of the system's G table (w follows G)
+  long long col0;    // first cell-list column (cx, cy) of the system in pooled column arrays
   double L, inv_L, h, inv_h;
   double r_c, rc2, inv_rc, inv_rc2, inv_rc3;
   double w;          // cell edge L / n_c
@@ -74,6 +78,8 @@ struct SysDesc {
   double self_coef;  // chi(0) / (4 pi r_c)
   double bg_shift;   // -(Q/V) (r_c^2/2) int_0^1 x^2 chi
   double prefactor;
+  // FP32 copies for the FP32 local part
+  float wf, r_cf, rc2f, inv_rcf, inv_rc2x2f, inv_rc3f;
 };
 
 // ------------------------------------------------------------ coordinates

@@ -87,6 +87,7 @@ struct esp_plan_s {
   bool allow_bg = false;
   long long N = 0;                     // atoms of all systems
   long long n_keys = 0, grid_total = 0, spec_total = 0, tab_total = 0;
+  long long n_cols = 0, cmap_cap = 0;  // cell-list columns, cluster-list capacity
   int n_chunks = 0, n_work = 0, F = 1;
   size_t smem = 0;                     // spread/gather tile bytes (largest system)
   std::vector<Bucket> buckets;
@@ -128,6 +129,11 @@ struct esp_plan_s {
   void* d_outF = nullptr;        // staging for outputs (FP64)
   void* d_outU = nullptr;
   int* d_err = nullptr;
+  uint32_t* d_ccount = nullptr;  // clusters per column (local part, FP32)
+  uint32_t* d_cstart = nullptr;
+  uint32_t* d_ctiles = nullptr;
+  int2* d_cmap = nullptr;
+  int2* d_catoms = nullptr;
 
   cudaStream_t st = nullptr, st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -253,7 +259,7 @@ void layout(esp_plan_s* p, std::vector<int2>& chunks, std::vector<int>& chunk_fi
   }
   p->grid_total = grid0;
   p->spec_total = spec0;
-  long long atom0 = 0, cell0 = 0, tab0 = 0, max_spec = 0;
+  long long atom0 = 0, cell0 = 0, tab0 = 0, col0 = 0, max_spec = 0;
   chunks.clear();
   work.clear();
   chunk_first.assign(n + 1, 0);
@@ -265,12 +271,14 @@ void layout(esp_plan_s* p, std::vector<int2>& chunks, std::vector<int>& chunk_fi
     d.atom0 = atom0;
     d.cell0 = cell0;
     d.tab0 = tab0;
+    d.col0 = col0;
     chunk_first[s] = (int)chunks.size();
     for (int c = 0; c * espk::kChunk < d.n_atoms; ++c) chunks.push_back(make_int2(s, c * espk::kChunk));
     for (int b = 0; b < hp.n_bricks; ++b) work.push_back(make_int2(s, b));
     atom0 += d.n_atoms;
     cell0 += hp.n_keys;
     tab0 += (long long)(hp.G.size() + hp.W.size());
+    col0 += (long long)d.n_c * d.n_c;
     p->smem = std::max(p->smem, (size_t)d.T * d.T * d.T * rb);
     max_spec = std::max(max_spec, hp.spec_elems);
   }
@@ -278,6 +286,8 @@ void layout(esp_plan_s* p, std::vector<int2>& chunks, std::vector<int>& chunk_fi
   p->N = atom0;
   p->n_keys = cell0;
   p->tab_total = tab0;
+  p->n_cols = col0;
+  p->cmap_cap = atom0 / espk::kClusterAtomsHost + col0 + 1;
   p->n_chunks = (int)chunks.size();
   p->n_work = (int)work.size();
   // scale grid: enough blocks to fill the GPU, capped by the spectrum size
@@ -323,6 +333,13 @@ esp_status build_buffers(esp_plan_s* p) {
   ESP_TRY(dev_alloc(p, &p->d_outF, (size_t)N * 3 * sizeof(double)));
   ESP_TRY(dev_alloc(p, &p->d_outU, (size_t)N * sizeof(double)));
   ESP_TRY(dev_alloc_t(p, &p->d_err, 1));
+  if (p->hps[0].near_clusters) {
+    ESP_TRY(dev_alloc_t(p, &p->d_ccount, std::max<long long>(1, p->n_cols)));
+    ESP_TRY(dev_alloc_t(p, &p->d_cstart, p->n_cols + 1));
+    ESP_TRY(dev_alloc_t(p, &p->d_ctiles, espk::scan_tiles(p->n_cols)));
+    ESP_TRY(dev_alloc_t(p, &p->d_cmap, p->cmap_cap));
+    ESP_TRY(dev_alloc_t(p, &p->d_catoms, p->cmap_cap * espk::kClusterAtomsHost));
+  }
 
   std::vector<real> tabs(std::max<long long>(1, p->tab_total));
   for (int s = 0; s < n; ++s) {
@@ -478,8 +495,14 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
       sizeof(real) == 4 ? (const void*)&hp.nc32 : (const void*)&hp.nc64);
   const espk::SICoef<real>& si = *reinterpret_cast<const espk::SICoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.si32 : (const void*)&hp.si64);
-  ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
-                 hp.near_nc, hp.near_queued, st2));
+  if (hp.near_clusters)
+    ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
+                            p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
+                            hp.near_half,
+                            p->N, p->d_err, st2));
+  else
+    ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
+                   hp.near_nc, hp.near_queued, st2));
   rec(p, 10, st2);
   if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
 

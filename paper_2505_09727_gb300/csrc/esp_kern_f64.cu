@@ -12,3 +12,16 @@
   ESP_P_CASE(14, FN, __VA_ARGS__) ESP_P_CASE(15, FN, __VA_ARGS__)         \
   ESP_P_CASE(16, FN, __VA_ARGS__)
 #include "esp_kern_impl.cuh"
+
+namespace espk {
+
+// The cluster form of the local part is FP32 only; FP64 plans use k_near.
+template <>
+cudaError_t Launch<double>::near_clusters(const SysDesc*, int, long long, const uint32_t*, const void*,
+                                          void*, const NearCoef<double>&, int, uint32_t*, uint32_t*,
+                                          uint32_t*, int2*, int2*, long long, bool, long long, int*,
+                                          cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+
+}  // namespace espk

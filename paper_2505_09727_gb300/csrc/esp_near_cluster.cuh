@@ -1,0 +1,458 @@
+// Local part (Eq. localpart) in FP32 with one warp per i-cluster.
+//
+// An i-cluster is up to kClusterAtoms consecutive atoms of one cell-list
+// column (cx, cy), taken in z order across the column's bricks; a small
+// kernel lists every cluster's atoms once per step. The warp of a cluster
+//  1. loads the cluster's atoms into shared memory, in a frame whose origin is
+//     the column's cell corner (x, y) and the bottom of the first atom's brick
+//     (z), and forms their bounding box;
+//  2. visits the (2R+1)^2 neighbouring image columns (one per lane); a column
+//     whose xy gap to the box is >= r_c is skipped, otherwise the z window of
+//     the cutoff around the box is cut at brick boundaries into contiguous
+//     slab ranges, appended to a per-warp list of ranges (first atom, prefix
+//     count, image offsets);
+//  3. walks the listed candidates with all 32 lanes, kWalk consecutive
+//     candidates per lane and step (a lane finds its range by a binary search
+//     over the prefix counts), moves each into the cluster frame and keeps
+//     those within r_c of the box in a per-warp queue, and
+//  4. whenever 32 are queued, lane k takes queued candidate k and evaluates it
+//     against every atom of the cluster (masked by 0 < r < r_c); at the end the
+//     per-lane sums are summed over the warp.
+#pragma once
+#include "esp_kernels.cuh"
+
+namespace espk {
+
+constexpr int kClusterAtoms = kClusterAtomsHost;
+constexpr int kClusterWarps = 8;                 // warps per block
+constexpr int kWalk = 4;                         // consecutive candidates per lane and step
+constexpr int kClusterQueue = 32 + 32 * kWalk;   // queued candidates per warp
+constexpr int kSegCap = 96;                      // listed ranges per warp
+
+__device__ __forceinline__ int system_of_column(const SysDesc* __restrict__ sys, int nsys, long long g) {
+  int lo = 0, hi = nsys - 1;                      // last system with col0 <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sys[mid].col0 <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cluster count per pooled column: ceil(atoms in the column / kClusterAtoms).
+static __global__ void __launch_bounds__(256) k_col_clusters(
+    const SysDesc* __restrict__ sys, int nsys, long long n_cols, const uint32_t* __restrict__ start,
+    uint32_t* __restrict__ ccount) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_cols) return;
+  const SysDesc& S = sys[system_of_column(sys, nsys, g)];
+  const int c = (int)(g - S.col0);
+  const int cx = c / S.n_c, cy = c - cx * S.n_c;
+  const uint32_t* st = start + S.cell0;
+  uint32_t total = 0;
+  for (int bz = 0; bz < S.nb; ++bz) {
+    const long long k0 = cell_key(S, cx, cy, bz * S.bc);
+    total += st[(k0 + S.bc) * kSub] - st[k0 * kSub];
+  }
+  ccount[g] = (total + kClusterAtoms - 1) / kClusterAtoms;
+}
+
+// Cluster list: cmap[q] = (system, column) and catoms[q][t] = (atom index,
+// brick z index) of the t-th atom of cluster q = cstart[column] + k
+// (index -1 in the empty slots of a column's last cluster).
+static __global__ void __launch_bounds__(256) k_cluster_expand(
+    const SysDesc* __restrict__ sys, int nsys, long long n_cols, const uint32_t* __restrict__ ccount,
+    const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ start, int2* __restrict__ cmap,
+    int2* __restrict__ catoms, long long capacity, int* __restrict__ err) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_cols) return;
+  const int s = system_of_column(sys, nsys, g);
+  const SysDesc& S = sys[s];
+  const int c = (int)(g - S.col0);
+  const int cx = c / S.n_c, cy = c - cx * S.n_c;
+  const uint32_t n = ccount[g], b = cstart[g];
+  if ((long long)b + n > capacity) {
+    atomicOr(err, 4);
+    return;
+  }
+  for (uint32_t k = 0; k < n; ++k) cmap[b + k] = make_int2(s, c);
+  const uint32_t* st = start + S.cell0;
+  const long long slots = (long long)n * kClusterAtoms;
+  long long p = 0;
+  for (int bz = 0; bz < S.nb; ++bz) {
+    const long long k0 = cell_key(S, cx, cy, bz * S.bc);
+    const uint32_t j0 = st[k0 * kSub], j1 = st[(k0 + S.bc) * kSub];
+    for (uint32_t j = j0; j < j1 && p < slots; ++j, ++p)
+      catoms[(long long)b * kClusterAtoms + p] = make_int2((int)j, bz);
+  }
+  for (; p < slots; ++p) catoms[(long long)b * kClusterAtoms + p] = make_int2(-1, 0);
+}
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) { return fmaxf(fmaxf(a, b), c); }
+
+template <int NC>
+__device__ __forceinline__ float horner_f(const float* c, float y) {
+  float v = c[NC - 1];
+#pragma unroll
+  for (int k = NC - 2; k >= 0; --k) v = fmaf(v, y, c[k]);
+  return v;
+}
+
+// Per-warp shared state of the cluster kernel.
+template <bool HALF>
+struct ClusterSmem {
+  float4 queue[kClusterQueue];          // queued candidates (cluster frame, charge)
+  int qidx[HALF ? kClusterQueue : 1];   // their atom indices (HALF)
+  float4 idata[kClusterAtoms];          // the cluster's atoms
+  float4 seg_off[kSegCap];              // image offsets of each listed range
+  uint32_t seg_pos[kSegCap];            // first atom of each listed range
+  int seg_pre[kSegCap + 1];             // exclusive prefix counts (+ total)
+};
+
+// HALF = false: every pair is evaluated from both sides (each warp owns its
+// atoms' sums; plain stores). HALF = true: every pair is evaluated once
+// (Newton's third law): a cluster takes the image columns of one half plane,
+// (oy > 0) or (oy = 0, ox > 0), plus the atoms that follow it in its own
+// column (upwards, including the periodic images above), and its pairs among
+// themselves; the reaction on each candidate is added to its result with one
+// float4 atomic, and the cluster's own sums likewise (results zeroed before).
+template <int NC, bool HALF>
+__global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ cmap, const int2* __restrict__ catoms,
+    const uint32_t* __restrict__ n_clusters, const float4* __restrict__ rel,
+    const uint32_t* __restrict__ start, float4* __restrict__ nearres, const NearCoef<float> nc,
+    int* __restrict__ err) {
+  __shared__ ClusterSmem<HALF> smem_all[kClusterWarps];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  ClusterSmem<HALF>& W = smem_all[wib];
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const float k4 = (float)(1.0 / kFourPi);
+  const float far_away = 1e18f;
+  // each block takes a contiguous run of clusters (neighbours in z share most
+  // candidates, so they meet in the block's L1)
+  const long long total_clusters = *n_clusters;
+  const long long per_block = (total_clusters + gridDim.x - 1) / gridDim.x;
+  const long long g_begin = (long long)blockIdx.x * per_block;
+  const long long g_end = min(total_clusters, g_begin + per_block);
+
+  for (long long g = g_begin + wib; g < g_end; g += kClusterWarps) {
+    const int2 cm = cmap[g];
+    const SysDesc& S = sys[cm.x];
+    const int n_c = S.n_c, bc = S.bc, R = S.reach;
+    const int cx = cm.y / n_c, cy = cm.y - (cm.y / n_c) * n_c;
+    const uint32_t* st = start + S.cell0;
+    const float w = S.wf;
+    const float bcw = (float)bc * w;
+    const long long a_lo = S.atom0, a_hi = S.atom0 + S.n_atoms;
+
+    // ---- 1. the cluster's atoms
+    int2 ca = make_int2(-1, 0);
+    if (lane < kClusterAtoms) ca = catoms[g * kClusterAtoms + lane];
+    const long long my_idx = ca.x;
+    const int my_bz = ca.y;
+    const bool mine = lane < kClusterAtoms && my_idx >= a_lo && my_idx < a_hi;
+    if (lane < kClusterAtoms && my_idx >= 0 && !mine) atomicOr(err, 4);
+    const int m = __popc(__ballot_sync(full, mine));
+    if (m == 0) continue;
+    const int bz_0 = __shfl_sync(full, my_bz, 0);
+    float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mine) {
+      ri = rel[my_idx];
+      ri.z += (float)(my_bz - bz_0) * bcw;
+    }
+    // bounding box (all coordinates are >= 0 in this frame, so the float bit
+    // patterns order like the values)
+    const unsigned inf_bits = 0x7f800000u;
+    const float bx_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.x) : inf_bits));
+    const float by_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.y) : inf_bits));
+    const float bz_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.z) : inf_bits));
+    const float bx_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.x) : 0u));
+    const float by_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.y) : 0u));
+    const float bz_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.z) : 0u));
+    // missing atoms (m < 8) sit far away with zero charge: every pair with
+    // them is masked off, so the eight pair evaluations need no branch
+    if (lane < kClusterAtoms)
+      W.idata[lane] = mine ? ri : make_float4(far_away, far_away, far_away, 0.f);
+    __syncwarp();
+
+    float pu[kClusterAtoms], px[kClusterAtoms], py[kClusterAtoms], pz[kClusterAtoms];
+#pragma unroll
+    for (int t = 0; t < kClusterAtoms; ++t) pu[t] = px[t] = py[t] = pz[t] = 0.f;
+
+    const float rc2 = S.rc2f, inv_rc = S.inv_rcf;
+    const float inv_rc2x2 = S.inv_rc2x2f, inv_rc3 = S.inv_rc3f;
+    const float margin = 1e-4f * w;
+    const float cull2 = rc2 + 2.f * margin * S.r_cf;
+    const float slab_per_len = (float)kSub / w;
+    int qn = 0;                                   // queued candidates
+    int nseg = 0, total = 0;                      // listed ranges, their candidates
+
+    // pair work on queued candidate `jd` (atom index jx or -1)
+    auto evaluate = [&](const float4 jd, int jx) {
+      float uj = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f;
+#pragma unroll
+      for (int t = 0; t < kClusterAtoms; ++t) {
+        const float4 ci = W.idata[t];
+        const float dx = ci.x - jd.x, dy = ci.y - jd.y, dz = ci.z - jd.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool in = r2 < rc2 && r2 > 0.f;
+        const float r2m = in ? r2 : rc2;
+        const float qe = in ? jd.w : 0.f;
+        const float rinv = rsqrtf(r2m);
+        const float y = fmaf(r2m, inv_rc2x2, -1.f);
+        const float h = horner_f<NC>(nc.h, y);
+        const float kk = horner_f<NC>(nc.k, y);
+        const float t1 = fmaf(-h, inv_rc, rinv);
+        const float t2 = fmaf(kk, inv_rc3, rinv * rinv * rinv);
+        pu[t] = fmaf(qe, t1, pu[t]);
+        const float fs = qe * t2;
+        px[t] = fmaf(fs, dx, px[t]);
+        py[t] = fmaf(fs, dy, py[t]);
+        pz[t] = fmaf(fs, dz, pz[t]);
+        if constexpr (HALF) {
+          const float qie = in ? ci.w : 0.f;
+          uj = fmaf(qie, t1, uj);
+          const float fsj = qie * t2;
+          fjx = fmaf(fsj, dx, fjx);
+          fjy = fmaf(fsj, dy, fjy);
+          fjz = fmaf(fsj, dz, fjz);
+        }
+      }
+      if constexpr (HALF) {
+        if (jx >= 0) {
+          const float qk = -jd.w * k4;
+          atomicAdd(nearres + jx, make_float4(uj * k4, qk * fjx, qk * fjy, qk * fjz));
+        }
+      }
+    };
+
+    // ---- 2. neighbouring image columns, in passes of 32 (one per lane). The
+    // per-lane column state survives the walks, so listing resumes where it
+    // stopped when the range list was full.
+    const int side = 2 * R + 1;
+    const int ncol = side * side;
+    long long idx_last = 0;                        // HALF: last atom of the cluster
+    int bz_last = 0;
+    if constexpr (HALF) {
+      idx_last = __shfl_sync(full, my_idx, m - 1);
+      bz_last = __shfl_sync(full, my_bz, m - 1);
+    }
+    int c0 = 0;                                    // next column pass
+    bool pass_open = false;
+    int cur = 0, u_hi = -1;                        // this lane's unwrapped slab cursor, last slab
+    int xx = 0, yy = 0;
+    float offx = 0.f, offy = 0.f;
+    long long own_pos = 0, own_end = 0;
+    bool own_first = false;
+    for (;;) {
+      // list ranges until the list is nearly full or no column is left
+      while (nseg <= kSegCap - 32) {
+        if (!pass_open) {
+          if (c0 >= ncol) break;
+          const int ci = c0 + lane;
+          c0 += 32;
+          pass_open = true;
+          const int ox = ci % side - R, oy = ci / side - R;
+          const bool own = ox == 0 && oy == 0;
+          bool use = ci < ncol;
+          if constexpr (HALF) use = use && (oy > 0 || (oy == 0 && ox >= 0));
+          const float gx = fmax3(0.f, (float)ox * w - bx_hi, bx_lo - (float)(ox + 1) * w);
+          const float gy = fmax3(0.f, (float)oy * w - by_hi, by_lo - (float)(oy + 1) * w);
+          const float d2 = gx * gx + gy * gy;
+          const bool col_on = use && d2 < cull2;
+          cur = 0;
+          u_hi = -1;
+          own_first = false;
+          if (col_on) {
+            const float hz = sqrtf(rc2 - fminf(d2, rc2)) + margin;
+            const int base_slab = bz_0 * bc * kSub;
+            cur = base_slab + (int)floorf((bz_lo - hz) * slab_per_len);
+            u_hi = base_slab + (int)floorf((bz_hi + hz) * slab_per_len);
+            xx = wrap_index(cx + ox, n_c);
+            yy = wrap_index(cy + oy, n_c);
+          }
+          offx = (float)ox * w;
+          offy = (float)oy * w;
+          // HALF, own column: the first range runs from just after the
+          // cluster's last atom to the window top inside that atom's brick;
+          // the listing then continues with the next brick up
+          if (HALF && own && col_on) {
+            const int top_brick_end = (bz_last + 1) * bc * kSub - 1;
+            const int send = min(u_hi, top_brick_end);
+            const long long k1 = cell_key(S, xx, yy, send >> 2);   // inside brick bz_last: no wrap
+            own_pos = idx_last + 1;
+            own_end = st[k1 * kSub + (send & 3) + 1];
+            if (own_end < own_pos) own_end = own_pos;
+            cur = top_brick_end + 1;
+            own_first = true;
+          }
+        }
+        if (!__any_sync(full, cur <= u_hi || own_first)) {
+          pass_open = false;
+          continue;
+        }
+        // one round: each lane with slabs left lists its next brick range
+        long long pos = 0, end = 0;
+        float offz = 0.f;
+        if (own_first) {
+          pos = own_pos;
+          end = own_end;
+          offz = (float)(bz_last - bz_0) * bcw;
+          own_first = false;
+        } else if (cur <= u_hi) {
+          const int ucell = cur >> 2;                               // kSub = 4
+          const int ubrick = ucell >= 0 ? ucell / bc : -((-ucell + bc - 1) / bc);
+          const int send = min(u_hi, (ubrick + 1) * bc * kSub - 1);
+          const int zz = wrap_index(ucell, n_c);
+          const long long k0 = cell_key(S, xx, yy, zz);
+          const long long k1 = k0 + ((send >> 2) - ucell);
+          pos = st[k0 * kSub + (cur & 3)];
+          end = st[k1 * kSub + (send & 3) + 1];
+          offz = (float)(ubrick - bz_0) * bcw;
+          cur = send + 1;
+        }
+        if (pos < end && (pos < a_lo || end > a_hi)) {
+          atomicOr(err, 4);
+          pos = end = 0;
+        }
+        const int cnt = pos < end ? (int)(end - pos) : 0;
+        const unsigned bal = __ballot_sync(full, cnt > 0);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(full, incl, o);
+          if (lane >= o) incl += t;
+        }
+        __syncwarp();
+        if (cnt > 0) {
+          const int slot = nseg + __popc(bal & lt_mask);
+          W.seg_pos[slot] = (uint32_t)pos;
+          W.seg_pre[slot] = total + incl - cnt;
+          W.seg_off[slot] = make_float4(offx, offy, offz, 0.f);
+        }
+        nseg += __popc(bal);
+        total += __shfl_sync(full, incl, 31);
+        __syncwarp();
+        if (lane == 0) W.seg_pre[nseg] = total;
+      }
+      const bool last_walk = !pass_open && c0 >= ncol;
+
+      // ---- 3. walk the listed candidates; evaluate every 32 kept (on the
+      // last walk the final partial batch too, padded with far-away
+      // chargeless candidates)
+      __syncwarp();
+      int base = 0;
+      for (;;) {
+        if (qn >= 32 || (last_walk && qn > 0 && base >= total)) {
+          const bool has = lane < qn;
+          const int slot = qn >= 32 ? qn - 32 + lane : lane;
+          __syncwarp();
+          const float4 jd = W.queue[slot];
+          const int jx = HALF ? W.qidx[slot] : -1;
+          evaluate(qn >= 32 || has ? jd : make_float4(far_away, far_away, far_away, 0.f),
+                   (HALF && (qn >= 32 || has)) ? jx : -1);
+          __syncwarp();
+          qn = qn >= 32 ? qn - 32 : 0;
+          continue;
+        }
+        if (base >= total) break;
+        const int f0 = base + lane * kWalk;
+        base += 32 * kWalk;
+        float4 v[kWalk];
+        int jv[kWalk];
+        int s = 0;
+        if (f0 < total) {
+          int lo = 0, hi = nseg - 1;               // last range whose prefix is <= f0
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (W.seg_pre[mid] <= f0) lo = mid; else hi = mid - 1;
+          }
+          s = lo;
+        }
+#pragma unroll
+        for (int u = 0; u < kWalk; ++u) {
+          const int f = f0 + u;
+          jv[u] = -1;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (f < total) {
+            while (W.seg_pre[s + 1] <= f) ++s;
+            const int j = (int)W.seg_pos[s] + (f - W.seg_pre[s]);
+            const float4 o = W.seg_off[s];
+            v[u] = rel[j];
+            v[u].x += o.x;
+            v[u].y += o.y;
+            v[u].z += o.z;
+            jv[u] = j;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kWalk; ++u) {
+          const float ex = fmax3(0.f, bx_lo - v[u].x, v[u].x - bx_hi);
+          const float ey = fmax3(0.f, by_lo - v[u].y, v[u].y - by_hi);
+          const float ez = fmax3(0.f, bz_lo - v[u].z, v[u].z - bz_hi);
+          const bool pass = jv[u] >= 0 && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < cull2;
+          const unsigned bal = __ballot_sync(full, pass);
+          if (pass) {
+            const int slot = qn + __popc(bal & lt_mask);
+            W.queue[slot] = v[u];
+            if constexpr (HALF) W.qidx[slot] = jv[u];
+          }
+          qn += __popc(bal);
+        }
+      }
+      nseg = 0;
+      total = 0;
+      __syncwarp();
+      if (last_walk) break;
+    }
+
+    // ---- 4. warp sums, output
+    __syncwarp();
+    float ou = 0.f, ofx = 0.f, ofy = 0.f, ofz = 0.f;
+#pragma unroll
+    for (int t = 0; t < kClusterAtoms; ++t) {
+      if (t < m) {
+        float a = pu[t], b = px[t], c = py[t], d = pz[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(full, a, o);
+          b += __shfl_xor_sync(full, b, o);
+          c += __shfl_xor_sync(full, c, o);
+          d += __shfl_xor_sync(full, d, o);
+        }
+        if (lane == t) { ou = a; ofx = b; ofy = c; ofz = d; }
+      }
+    }
+    if constexpr (HALF) {
+      // pairs inside the cluster (same image): each lane sums its own atom's
+      // pairs with the others
+      if (mine) {
+#pragma unroll
+        for (int t = 0; t < kClusterAtoms; ++t) {
+          const float4 ci = W.idata[t];
+          const float dx = ri.x - ci.x, dy = ri.y - ci.y, dz = ri.z - ci.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const bool in = t != lane && r2 < rc2 && r2 > 0.f;
+          const float r2m = in ? r2 : rc2;
+          const float qe = in ? ci.w : 0.f;
+          const float rinv = rsqrtf(r2m);
+          const float y = fmaf(r2m, inv_rc2x2, -1.f);
+          const float h = horner_f<NC>(nc.h, y);
+          const float kk = horner_f<NC>(nc.k, y);
+          ou = fmaf(qe, fmaf(-h, inv_rc, rinv), ou);
+          const float fs = qe * fmaf(kk, inv_rc3, rinv * rinv * rinv);
+          ofx = fmaf(fs, dx, ofx);
+          ofy = fmaf(fs, dy, ofy);
+          ofz = fmaf(fs, dz, ofz);
+        }
+        atomicAdd(nearres + my_idx, make_float4(ou * k4, ri.w * ofx * k4, ri.w * ofy * k4, ri.w * ofz * k4));
+      }
+    } else if (mine) {
+      nearres[my_idx] = make_float4(ou * k4, ri.w * ofx * k4, ri.w * ofy * k4, ri.w * ofz * k4);
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace espk

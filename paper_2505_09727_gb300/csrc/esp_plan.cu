@@ -383,6 +383,12 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.inv_rc2 = d.inv_rc * d.inv_rc; d.inv_rc3 = d.inv_rc2 * d.inv_rc;
   d.w = L / n_c;
   d.fix_scale = L / 4294967296.0;
+  d.wf = (float)d.w;
+  d.r_cf = (float)r_c;
+  d.rc2f = (float)d.rc2;
+  d.inv_rcf = (float)d.inv_rc;
+  d.inv_rc2x2f = (float)(2.0 * d.inv_rc2);
+  d.inv_rc3f = (float)d.inv_rc3;
   hp.self_unit = split.chi0() / (4.0 * kPi * r_c);
   hp.m2 = split.second_moment();
   d.self_coef = hp.self_unit;
@@ -413,8 +419,10 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
 
   hp.tol = tol;
-  if (o.near_variant < 0 || o.near_variant > 2) { msg = "near_variant must be 0, 1 or 2"; return ESP_ERR_INVALID_ARG; }
+  if (o.near_variant < 0 || o.near_variant > 4) { msg = "near_variant must be 0 ... 4"; return ESP_ERR_INVALID_ARG; }
   hp.near_queued = o.near_variant == 2;
+  hp.near_clusters = prec == ESP_FP32 && (o.near_variant >= 3 || o.near_variant == 0);
+  hp.near_half = hp.near_clusters && o.near_variant != 3;
   hp.n_keys = (long long)n_c * n_c * n_c * espk::kSub;
   hp.grid_elems = (long long)n_f * n_f * n_f;
   hp.spec_elems = (long long)n_f * n_f * (n_f / 2 + 1);

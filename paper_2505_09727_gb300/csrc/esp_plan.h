@@ -27,6 +27,8 @@ struct HostPlan {
   int n_bricks = 0;            // nb^3
   int near_nc = 0;             // polynomial terms used by the local part
   bool near_queued = false;    // local-part variant (queued pairs)
+  bool near_clusters = false;  // local-part variant (one warp per i-cluster, FP32)
+  bool near_half = false;      // ... with each pair evaluated once
 };
 
 // Fill `hp` for a cubic box of edge L with N atoms. Returns ESP_OK or an
