@@ -1,6 +1,7 @@
 // Launcher bodies shared by the FP32 and FP64 instantiation units. Each unit
 // defines ESP_REAL and the P range it compiles, then includes this file.
 #pragma once
+#include <algorithm>
 #include "esp_kernels.cuh"
 #include "esp_launch.h"
 
@@ -19,6 +20,20 @@ __global__ void __launch_bounds__(256) k_convert(const In* __restrict__ src, rea
                                                  long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = (real)src[i];
+}
+
+// CTAs per brick so that small grids of bricks still fill the device: at
+// least two CTAs per SM in total, at most 16 per brick.
+static int brick_splits(int n_work) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int want = 2 * sms;
+  return std::max(1, std::min(16, (want + n_work - 1) / std::max(1, n_work)));
 }
 
 }  // namespace detail
@@ -57,6 +72,22 @@ static cudaError_t spread_p(const SysDesc* sys, const int2* work, int n_work, si
                             const void* atoms, const uint32_t* start, ESP_REAL* grids,
                             const SICoef<ESP_REAL>& si, int* err, cudaStream_t st) {
   using A = typename Types<ESP_REAL>::atom;
+  if constexpr (sizeof(ESP_REAL) == 4) {
+    // private tile per warp while up to 8 tiles fit in ~110 KB (two CTAs per
+    // SM); otherwise one shared tile with shared-memory atomics
+    const size_t stride = (smem / sizeof(float) + 31) & ~size_t(31);   // floats, bank-aligned
+    const int nwarps = (int)std::min<size_t>(8, (110u * 1024u) / (stride * sizeof(float)));
+    if (nwarps >= 2) {
+      auto kw = k_spread_warps<P>;
+      const size_t bytes = (size_t)((P * Deg<float>::si + 3) & ~3) * sizeof(float) + nwarps * stride * sizeof(float);
+      cudaError_t e = detail::allow_smem(kw, bytes);
+      if (e != cudaSuccess) return e;
+      const int splits = detail::brick_splits(n_work);
+      kw<<<n_work * splits, 256, bytes, st>>>(sys, work, (const uint4*)atoms, start, (float*)grids, si, nwarps,
+                                              (int)stride, splits, err);
+      return cudaGetLastError();
+    }
+  }
   auto kern = k_spread<ESP_REAL, P>;
   cudaError_t e = detail::allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -73,7 +104,8 @@ static cudaError_t gather_p(const SysDesc* sys, const int2* work, int n_work, si
   auto kern = k_gather<ESP_REAL, P>;
   cudaError_t e = detail::allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_work, 256, smem, st>>>(sys, work, (const A*)atoms, start, grids, (R*)far, si, err);
+  const int splits = detail::brick_splits(n_work);
+  kern<<<n_work * splits, 256, smem, st>>>(sys, work, (const A*)atoms, start, grids, (R*)far, si, splits, err);
   return cudaGetLastError();
 }
 

@@ -366,6 +366,116 @@ __global__ void __launch_bounds__(256) k_spread(
   }
 }
 
+// A2 (FP32): spread with one private tile per warp and no atomics inside the
+// block. The warps of a CTA take the brick's atoms in turn; for each atom,
+// lanes 0 ... 3P-1 evaluate the 3P one-dimensional weights (coefficients in
+// shared memory), every lane takes whole stencil rows (b, c) of the atom, and
+// the row points of one atom are distinct, so plain read-add-write needs no
+// atomics; atoms of one warp follow each other after a warp barrier. The
+// private tiles are summed point by point and flushed to the grid with
+// global atomics (bricks overlap by P - 1 points).
+template <int P>
+__global__ void __launch_bounds__(256) k_spread_warps(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ work, const uint4* __restrict__ atoms,
+    const uint32_t* __restrict__ start, float* __restrict__ grids, const SICoef<float> si, int nwarps,
+    int tile_stride, int splits, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NC = Deg<float>::si;
+  float* coef = reinterpret_cast<float*>(smem_raw);                  // [P][NC]
+  float* tiles = coef + ((P * NC + 3) & ~3);                        // [nwarps][tile_stride]
+  const int2 wk = work[blockIdx.x / splits];
+  const int split = blockIdx.x % splits;
+  const SysDesc& S = sys[wk.x];
+  const int nb = S.nb, T = S.T, n_f = S.n_f, bc = S.bc;
+  const int b = wk.y;
+  const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+  const int ox = tile_origin(S, bx, P, 0.f), oy = tile_origin(S, by, P, 0.f), oz = tile_origin(S, bz, P, 0.f);
+  const int T2 = T * T, T3 = T2 * T;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < P * NC; j += blockDim.x) coef[j] = si.c[j / NC][j % NC];
+  for (int j = threadIdx.x; j < nwarps * tile_stride; j += blockDim.x) tiles[j] = 0.f;
+  __syncthreads();
+  const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
+  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
+  if (wid < nwarps) {
+    float* tile = tiles + (size_t)wid * tile_stride;
+    // this lane's weight: axis lane / P, point lane % P (coefficients kept in
+    // registers for the whole kernel)
+    const int w_axis = lane / P, w_point = lane - (lane / P) * P;
+    float wc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) wc[k] = coef[w_point * NC + k];
+    constexpr int kRows = P * P;
+    constexpr int kPass = (kRows + 31) / 32;
+    int row_off[kPass];
+#pragma unroll
+    for (int k = 0; k < kPass; ++k) {
+      const int r = min(lane + 32 * k, kRows - 1);
+      row_off[k] = (r / P) * T2 + (r % P) * T;
+    }
+    // chunks of 32 consecutive atoms: one coalesced load, stencil origins and
+    // fractions computed lane-parallel, then the atoms one after another
+    const int n_here = (int)(a_end - a_begin);
+    const int n_chunks = (n_here + 31) / 32;
+    for (int ch = split * nwarps + wid; ch < n_chunks; ch += nwarps * splits) {
+      const int a0 = ch * 32;
+      const int cnt = min(32, n_here - a0);
+      int sl = 0;                                  // packed tile offset of this lane's atom
+      float syx = 0.f, syy = 0.f, syz = 0.f, sq = 0.f;
+      bool sok = false;
+      if (lane < cnt) {
+        const uint4 at = atoms[a_begin + a0 + lane];
+        const int lx = stencil(S, at.x, P, syx) - ox;
+        const int ly = stencil(S, at.y, P, syy) - oy;
+        const int lz = stencil(S, at.z, P, syz) - oz;
+        sok = !(lx < 0 || ly < 0 || lz < 0 || lx > T - P || ly > T - P || lz > T - P);
+        if (!sok) atomicOr(err, 2);
+        sl = lz * T2 + ly * T + lx;
+        sq = __uint_as_float(at.w);
+      }
+      const unsigned okmask = __ballot_sync(0xffffffffu, sok);
+      for (int t = 0; t < cnt; ++t) {
+        if (!((okmask >> t) & 1u)) continue;
+        const int off = __shfl_sync(0xffffffffu, sl, t);
+        const float yx = __shfl_sync(0xffffffffu, syx, t);
+        const float yy = __shfl_sync(0xffffffffu, syy, t);
+        const float yz = __shfl_sync(0xffffffffu, syz, t);
+        const float q = __shfl_sync(0xffffffffu, sq, t);
+        const float y = w_axis == 0 ? yx : (w_axis == 1 ? yy : yz);
+        float wv = wc[NC - 1];
+#pragma unroll
+        for (int k = NC - 2; k >= 0; --k) wv = fmaf(wv, y, wc[k]);
+        if (lane >= 3 * P) wv = 0.f;
+        float wx[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) wx[a] = __shfl_sync(0xffffffffu, wv, a);
+#pragma unroll
+        for (int k = 0; k < kPass; ++k) {
+          const int r = min(lane + 32 * k, kRows - 1);
+          const float wyz = q * __shfl_sync(0xffffffffu, wv, P + r % P) * __shfl_sync(0xffffffffu, wv, 2 * P + r / P);
+          if (lane + 32 * k < kRows) {
+            float* row = tile + off + row_off[k];
+#pragma unroll
+            for (int a = 0; a < P; ++a) row[a] = fmaf(wyz, wx[a], row[a]);
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  float* grid = grids + S.grid0;
+  for (int j = threadIdx.x; j < T3; j += blockDim.x) {
+    float v = 0.f;
+    for (int k = 0; k < nwarps; ++k) v += tiles[(size_t)k * tile_stride + j];
+    if (v != 0.f) {
+      const int jx = j % T, jy = (j / T) % T, jz = j / T2;
+      const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f), gz = wrap_index(oz + jz, n_f);
+      atomicAdd(grid + ((long long)gz * n_f + gy) * n_f + gx, v);
+    }
+  }
+}
+
 // A4: influence scale fused with the spectral energy (Eq. pk). Grid-stride
 // over the half spectrum [kz][ky][kx], kx in [0, n_f/2]; blockIdx.y = system.
 template <typename real>
@@ -406,10 +516,11 @@ __global__ void __launch_bounds__(256) k_gather(
     const SysDesc* __restrict__ sys, const int2* __restrict__ work,
     const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ start,
     const real* __restrict__ grids, typename Types<real>::res* __restrict__ far,
-    const SICoef<real> si, int* __restrict__ err) {
+    const SICoef<real> si, int splits, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* tile = reinterpret_cast<real*>(smem_raw);
-  const int2 wk = work[blockIdx.x];
+  const int2 wk = work[blockIdx.x / splits];
+  const int split = blockIdx.x % splits;
   const SysDesc& S = sys[wk.x];
   const int nb = S.nb, T = S.T, n_f = S.n_f, bc = S.bc;
   const int b = wk.y;
@@ -428,7 +539,7 @@ __global__ void __launch_bounds__(256) k_gather(
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
   const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
   const real inv_h = (real)S.inv_h;
-  for (uint32_t i = a_begin + threadIdx.x; i < a_end; i += blockDim.x) {
+  for (uint32_t i = a_begin + split * blockDim.x + threadIdx.x; i < a_end; i += blockDim.x * splits) {
     const typename Types<real>::atom at = atoms[i];
     real yx, yy, yz;
     const int lx = stencil(S, at.x, P, yx) - ox;
