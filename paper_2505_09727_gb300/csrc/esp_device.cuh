@@ -79,7 +79,7 @@ struct SysDesc {
   double bg_shift;   // -(Q/V) (r_c^2/2) int_0^1 x^2 chi
   double prefactor;
   // FP32 copies for the FP32 local part
-  float wf, r_cf, rc2f, inv_rcf, inv_rc2x2f, inv_rc3f;
+  float wf, r_cf, rc2f, inv_rcf, inv_rc2x2f, inv_rc3f, inv_bcf;
 };
 
 // ------------------------------------------------------------ coordinates

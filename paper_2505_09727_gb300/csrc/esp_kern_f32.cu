@@ -25,7 +25,7 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
                                          long long cmap_cap, bool half, long long n_atoms, int* err,
                                          cudaStream_t st) {
   if (n_cols == 0) return cudaSuccess;
-  const int cb = (int)((n_cols + 255) / 256);
+  const int cb = (int)((n_cols * 32 + 255) / 256);     // one warp per column
   k_col_clusters<<<cb, 256, 0, st>>>(sys, nsys, n_cols, start, ccount);
   cudaError_t e = launch_scan(ccount, cstart, ctiles, n_cols, st);
   if (e != cudaSuccess) return e;

@@ -38,22 +38,25 @@ __device__ __forceinline__ int system_of_column(const SysDesc* __restrict__ sys,
   return lo;
 }
 
-// Cluster count per pooled column: ceil(atoms in the column / kClusterAtoms).
+// One warp per pooled column (lanes over the column's bricks).
+// Cluster count per column: ceil(atoms in the column / kClusterAtoms).
 static __global__ void __launch_bounds__(256) k_col_clusters(
     const SysDesc* __restrict__ sys, int nsys, long long n_cols, const uint32_t* __restrict__ start,
     uint32_t* __restrict__ ccount) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (g >= n_cols) return;
   const SysDesc& S = sys[system_of_column(sys, nsys, g)];
   const int c = (int)(g - S.col0);
   const int cx = c / S.n_c, cy = c - cx * S.n_c;
   const uint32_t* st = start + S.cell0;
   uint32_t total = 0;
-  for (int bz = 0; bz < S.nb; ++bz) {
+  for (int bz = lane; bz < S.nb; bz += 32) {
     const long long k0 = cell_key(S, cx, cy, bz * S.bc);
     total += st[(k0 + S.bc) * kSub] - st[k0 * kSub];
   }
-  ccount[g] = (total + kClusterAtoms - 1) / kClusterAtoms;
+  total = __reduce_add_sync(0xffffffffu, total);
+  if (lane == 0) ccount[g] = (total + kClusterAtoms - 1) / kClusterAtoms;
 }
 
 // Cluster list: cmap[q] = (system, column) and catoms[q][t] = (atom index,
@@ -63,7 +66,8 @@ static __global__ void __launch_bounds__(256) k_cluster_expand(
     const SysDesc* __restrict__ sys, int nsys, long long n_cols, const uint32_t* __restrict__ ccount,
     const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ start, int2* __restrict__ cmap,
     int2* __restrict__ catoms, long long capacity, int* __restrict__ err) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (g >= n_cols) return;
   const int s = system_of_column(sys, nsys, g);
   const SysDesc& S = sys[s];
@@ -71,20 +75,22 @@ static __global__ void __launch_bounds__(256) k_cluster_expand(
   const int cx = c / S.n_c, cy = c - cx * S.n_c;
   const uint32_t n = ccount[g], b = cstart[g];
   if ((long long)b + n > capacity) {
-    atomicOr(err, 4);
+    if (lane == 0) atomicOr(err, 4);
     return;
   }
-  for (uint32_t k = 0; k < n; ++k) cmap[b + k] = make_int2(s, c);
+  for (uint32_t k = lane; k < n; k += 32) cmap[b + k] = make_int2(s, c);
   const uint32_t* st = start + S.cell0;
   const long long slots = (long long)n * kClusterAtoms;
-  long long p = 0;
+  int2* out = catoms + (long long)b * kClusterAtoms;
+  long long p = 0;                                  // position of the brick's first atom
   for (int bz = 0; bz < S.nb; ++bz) {
     const long long k0 = cell_key(S, cx, cy, bz * S.bc);
     const uint32_t j0 = st[k0 * kSub], j1 = st[(k0 + S.bc) * kSub];
-    for (uint32_t j = j0; j < j1 && p < slots; ++j, ++p)
-      catoms[(long long)b * kClusterAtoms + p] = make_int2((int)j, bz);
+    for (uint32_t j = j0 + lane; j < j1; j += 32)
+      if (p + (j - j0) < slots) out[p + (j - j0)] = make_int2((int)j, bz);
+    p += j1 - j0;
   }
-  for (; p < slots; ++p) catoms[(long long)b * kClusterAtoms + p] = make_int2(-1, 0);
+  for (long long q = p + lane; q < slots; q += 32) out[q] = make_int2(-1, 0);
 }
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) { return fmaxf(fmaxf(a, b), c); }
@@ -139,7 +145,9 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
   for (long long g = g_begin + wib; g < g_end; g += kClusterWarps) {
     const int2 cm = cmap[g];
     const SysDesc& S = sys[cm.x];
-    const int n_c = S.n_c, bc = S.bc, R = S.reach;
+    const int n_c = S.n_c, bc = S.bc, nb = S.nb, R = S.reach;
+    const float inv_bc = S.inv_bcf;
+    const long long brick_plane = (long long)nb * nb * bc * bc * bc;   // key stride of one z brick
     const int cx = cm.y / n_c, cy = cm.y - (cm.y / n_c) * n_c;
     const uint32_t* st = start + S.cell0;
     const float w = S.wf;
@@ -242,6 +250,7 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
     bool pass_open = false;
     int cur = 0, u_hi = -1;                        // this lane's unwrapped slab cursor, last slab
     int xx = 0, yy = 0;
+    long long kxy = 0;                             // cell key of (xx, yy, 0)
     float offx = 0.f, offy = 0.f;
     long long own_pos = 0, own_end = 0;
     bool own_first = false;
@@ -271,6 +280,7 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
             u_hi = base_slab + (int)floorf((bz_hi + hz) * slab_per_len);
             xx = wrap_index(cx + ox, n_c);
             yy = wrap_index(cy + oy, n_c);
+            kxy = cell_key(S, xx, yy, 0);
           }
           offx = (float)ox * w;
           offy = (float)oy * w;
@@ -302,10 +312,15 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
           own_first = false;
         } else if (cur <= u_hi) {
           const int ucell = cur >> 2;                               // kSub = 4
-          const int ubrick = ucell >= 0 ? ucell / bc : -((-ucell + bc - 1) / bc);
+          // floor(ucell / bc) through the FP32 reciprocal (exact for the
+          // small |ucell| here: the +0.5 keeps the product off integers)
+          const int ubrick = __float2int_rd(((float)ucell + 0.5f) * inv_bc);
+          const int lz = ucell - ubrick * bc;
+          int wb = ubrick;                                          // periodic brick index
+          while (wb < 0) wb += nb;
+          while (wb >= nb) wb -= nb;
           const int send = min(u_hi, (ubrick + 1) * bc * kSub - 1);
-          const int zz = wrap_index(ucell, n_c);
-          const long long k0 = cell_key(S, xx, yy, zz);
+          const long long k0 = kxy + (long long)wb * brick_plane + lz;
           const long long k1 = k0 + ((send >> 2) - ucell);
           pos = st[k0 * kSub + (cur & 3)];
           end = st[k1 * kSub + (send & 3) + 1];

@@ -389,6 +389,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.inv_rcf = (float)d.inv_rc;
   d.inv_rc2x2f = (float)(2.0 * d.inv_rc2);
   d.inv_rc3f = (float)d.inv_rc3;
+  d.inv_bcf = (float)(1.0 / bc);
   hp.self_unit = split.chi0() / (4.0 * kPi * r_c);
   hp.m2 = split.second_moment();
   d.self_coef = hp.self_unit;
