@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--molecules", type=int, default=WORKLOAD["molecules"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FP64, Gaussian and batched comparison lines")
+                    help="skip the FP64, Gaussian, batched and served comparison lines")
+    ap.add_argument("--served-full", action="store_true",
+                    help="served line on the full 256-system, 1e4-request stream (minutes of setup)")
     return ap.parse_args()
 
 
@@ -253,6 +255,7 @@ def run_gpu(args, world, rank, local):
         extras["plain_fp64"] = single_variant(args, local, stream, flush, s, precision=esp.ESP_FP64)
         extras["gaussian"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS)
         extras["batched"] = batched(args, local, stream, flush)
+        extras["served"] = served(args, local)
 
     if world > 1:
         t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
@@ -358,6 +361,94 @@ def batched(args, local, stream, flush):
             "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 24,
                     "d2h_bytes_per_step": n * 24 + 8 * len(systems)},
             "config": BATCH}
+
+
+SERVE = dict(workload="served_electrolyte", systems=64, atoms_lo=1000, atoms_hi=200_000, requests=2000,
+             tolerances=[1e-3, 1e-4, 1e-5], sigma_nm=0.01, density_per_nm3=100.0, r_c_nm=1.0,
+             budget_gb=150.0, loads=[0.5, 0.8, 0.95], seed=1000)
+SERVE_FULL = dict(SERVE, systems=256, atoms_hi=1_000_000, requests=10_000)
+
+
+def served(args, local):
+    """Request server: resident systems, Poisson arrivals, p50/p99 latency.
+
+    Saturation: every request submitted at once (closed loop); then Poisson
+    arrivals at the given fractions of the saturated request rate."""
+    import threading
+    from paper_2505_09727_gb300 import esp, inputs
+    cfg = SERVE_FULL if args.served_full else SERVE
+    rng = np.random.default_rng(cfg["seed"])
+    sizes = inputs.batch_sizes(cfg["systems"], cfg["atoms_lo"], cfg["atoms_hi"], seed=cfg["seed"])
+    systems = inputs.electrolyte_batch(sizes, seed=cfg["seed"])
+    nmax = int(max(sizes))
+    noise = [rng.normal(0.0, cfg["sigma_nm"], size=(nmax, 3)) for _ in range(4)]
+    reqs = []
+    for k in range(cfg["requests"]):
+        i = int(rng.integers(len(systems)))
+        reqs.append((i, float(rng.choice(cfg["tolerances"])), k % len(noise)))
+
+    def positions(i, k):
+        s = systems[i]
+        return np.mod(s.pos + noise[k][: s.n], s.L)
+
+    srv = esp.Server(cfg["r_c_nm"], memory_budget=int(cfg["budget_gb"] * 1e9), device=local, max_inflight=8)
+    ids = [srv.add_system(s.L, s.q) for s in systems]
+    # plans for every (system, tolerance) the stream uses, created before timing
+    t0 = time.perf_counter()
+    for i, eps in sorted({(i, e) for i, e, _ in reqs}):
+        srv.wait(srv.submit(ids[i], eps, systems[i].pos), forces=False, potential=False)
+    t_plans = time.perf_counter() - t0
+    pos_cache = {}
+
+    def run(rate):
+        """rate None: closed loop with 64 requests outstanding; else Poisson."""
+        import queue
+        esp.esp_server_reset_stats(srv.handle)
+        window = threading.Semaphore(64 if rate is None else 512)
+        pending = queue.Queue()
+
+        def waiter():
+            while True:
+                t = pending.get()
+                if t is None:
+                    return
+                srv.wait(t, forces=False, potential=False)
+                window.release()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t_start = time.perf_counter()
+        next_t = t_start
+        for i, eps, k in reqs:
+            if rate:
+                next_t += rng.exponential(1.0 / rate)
+                d = next_t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+            window.acquire()
+            pending.put(srv.submit(ids[i], eps, pos_cache[(i, k)]))
+        pending.put(None)
+        th.join()
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        return dict(wall_s=wall, requests_per_s=len(reqs) / wall, atoms_per_s=st["atoms_done"] / wall,
+                    p50_ms=st["latency_p50_ms"], p99_ms=st["latency_p99_ms"])
+
+    for i, eps, k in reqs:                        # positions prepared outside the timed runs
+        pos_cache.setdefault((i, k), positions(i, k))
+    sat = run(None)
+    loads = {}
+    for f in cfg["loads"]:
+        r = run(f * sat["requests_per_s"])
+        loads[str(f)] = {k: round(v, 4) for k, v in r.items()}
+    st = srv.stats()
+    srv.close()
+    atoms = float(sum(systems[i].n for i, _, _ in reqs))
+    return {"value": sat["atoms_per_s"], "unit": UNIT, "requests": len(reqs), "atoms_per_pass": atoms,
+            "saturated": {k: round(v, 4) for k, v in sat.items()}, "poisson": loads,
+            "plans": st["plans_created"], "evictions": st["evictions"],
+            "device_gb": round(st["device_bytes"] / 1e9, 3), "plan_setup_s": round(t_plans, 2),
+            "config": dict(cfg, scaled=not args.served_full)}
 
 
 # --------------------------------------------------------------- CPU oracle

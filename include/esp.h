@@ -223,6 +223,70 @@ esp_status esp_batch_set_timing(esp_batch_t batch, int enable);
 esp_status esp_batch_phase_times(esp_batch_t batch, float* ms, int n);
 esp_status esp_batch_destroy(esp_batch_t batch);
 
+/* ------------------------------------------------------------------ server
+ * Request server on one device. The paper treats one solve at a time; the
+ * server is the serving form of the same solve: systems are registered once
+ * (box, N, charges, copied), and each request (system id, tolerance,
+ * positions N x 3 FP64, copied at submit) is answered with the energy, forces
+ * and potential of esp_compute for that system.
+ *  - Plans: one per (system, tolerance), created on the first request and
+ *    kept resident (sorted bins, grids, FFT plans) for the next ones. A plan
+ *    that would exceed memory_budget first evicts idle plans, least recently
+ *    used first; a request whose plan cannot fit waits until running requests
+ *    finish, and fails with ESP_ERR_BUSY if it could never fit.
+ *  - Continuous batching: a worker thread keeps up to max_inflight requests
+ *    on the device at once, each on its plan's own streams (copies and
+ *    kernels asynchronous through pinned host buffers); a request submitted
+ *    while others run starts as soon as a slot and its plan are free. Two
+ *    requests for the same plan run one after the other.
+ *  - Results equal those of esp_plan + esp_compute on the same inputs up to
+ *    FP32 rounding (atomic summation order).
+ * The server is internally synchronized: submit, poll and wait may be called
+ * from any thread. Latency = completion - submission, in ms. */
+typedef struct esp_server_s* esp_server_t;
+
+typedef struct {
+  size_t memory_budget;  /* device bytes the server's plans may hold; 0 = 80% of free */
+  int device;            /* CUDA device ordinal                                        */
+  int max_inflight;      /* requests on the device at once; 0 = 8                      */
+  double r_c;            /* cutoff of every plan (required, > 0)                        */
+  int precision;         /* ESP_FP32 (default) or ESP_FP64                             */
+  int kernel;            /* ESP_KERNEL_PSWF (default) or ESP_KERNEL_GAUSS              */
+  double timeout_ms;     /* deadline of a running request and of waits; 0 = 60000    */
+  int reserved[8];
+} esp_server_opts;
+
+typedef struct {
+  int64_t completed, failed, pending, running;
+  double atoms_done;          /* atoms of completed requests                          */
+  int64_t plans_resident, plans_created, evictions;
+  size_t device_bytes;        /* bytes held by resident plans                         */
+  size_t memory_budget;
+  double latency_p50_ms, latency_p99_ms, latency_max_ms;
+  double wall_ms;             /* first submission to last completion                  */
+} esp_server_counters;
+
+void esp_server_opts_init(esp_server_opts* opts);
+esp_status esp_server_create(const esp_server_opts* opts, esp_server_t* out);
+/* Register a system; q[N] host FP64 (copied). *id is the handle of requests. */
+esp_status esp_server_add_system(esp_server_t server, const esp_box* box, int64_t N,
+                                 const double* q, int* id);
+/* Queue a request; xyz[3N] host FP64 (copied before return). */
+esp_status esp_server_submit(esp_server_t server, int id, double tolerance, const double* xyz,
+                             int64_t* ticket);
+/* *done = 1 once the request has finished (successfully or not). */
+esp_status esp_server_poll(esp_server_t server, int64_t ticket, int* done);
+/* Wait (at most timeout_ms; 0 = the server deadline) and copy the results to
+ * host buffers (any may be NULL); the ticket is released unless the wait or
+ * the request timed out. Returns the request's status. */
+esp_status esp_server_wait(esp_server_t server, int64_t ticket, double timeout_ms, double* energy,
+                           double* forces, double* potential, double* latency_ms);
+esp_status esp_server_stats(esp_server_t server, esp_server_counters* out);
+/* Clear the completion counters and latencies (resident plans stay). */
+esp_status esp_server_reset_stats(esp_server_t server);
+/* Stop the worker, wait for running requests, free every plan. */
+esp_status esp_server_destroy(esp_server_t server);
+
 /* Local part without device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc (code running
  * while a framework's caching allocator owns the device heap, inside regions

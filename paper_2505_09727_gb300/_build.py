@@ -18,10 +18,10 @@ LIB = os.path.join(OUT, "libesp_gb300.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-Wno-deprecated-declarations", "--expt-relaxed-constexpr"]
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall"]
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-pthread"]
 
 CU_SOURCES = ["esp_kern_f32.cu", "esp_kern_f64.cu", "esp_plan.cu", "esp_engine.cu", "esp_static.cu"]
-CPP_SOURCES = ["esp_math.cpp"]
+CPP_SOURCES = ["esp_math.cpp", "esp_server.cpp"]
 
 
 def cuda_home() -> str:

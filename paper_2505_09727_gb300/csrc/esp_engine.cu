@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/esp.h"
+#include "esp_engine.h"
 #include "esp_launch.h"
 #include "esp_plan.h"
 
@@ -687,6 +688,12 @@ esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const
   size_t bytes = (size_t)N * (24 + 2 * ab + 4 * 3 + rb + 8 + 2 * ab + 32) +
                  (size_t)hp.n_keys * 8 + (size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb +
                  (hp.G.size() + hp.W.size()) * rb;
+  if (hp.near_clusters) {
+    // cluster counts, offsets and lists of the local part
+    const size_t n_cols = (size_t)hp.desc.n_c * hp.desc.n_c;
+    const size_t cap = (size_t)N / espk::kClusterAtomsHost + n_cols + 1;
+    bytes += n_cols * 8 + cap * (8 + 8 * espk::kClusterAtomsHost);
+  }
   hp.info.device_bytes = bytes;
   *out = hp.info;
   return ESP_OK;
@@ -802,6 +809,46 @@ const char* esp_last_error(void) { return g_error.c_str(); }
 const char* esp_version(void) { return "esp_gb300 0.1 (sm_103a; CUDA " ESP_STR(CUDART_VERSION) ")"; }
 
 }  // extern "C"
+
+// ============================================================ server hooks
+namespace {
+
+template <typename real>
+esp_status enqueue_step(esp_plan_s* p, const double* xyz, double* forces, double* potential, double* energy,
+                        int* err_host, cudaEvent_t done) {
+  const long long N = p->N;
+  ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, N * 3 * sizeof(double), cudaMemcpyHostToDevice, p->st));
+  ESP_TRY(launch_sort<real>(p, p->d_pos, true));
+  p->have_pos = true;
+  ESP_TRY(launch_compute<real>(p, p->d_outF, p->d_outU, true, nullptr));
+  ESP_CU(cudaMemcpyAsync(forces, p->d_outF, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ESP_CU(cudaMemcpyAsync(energy, p->d_eout, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ESP_CU(cudaMemcpyAsync(err_host, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  ESP_CU(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->st));
+  ESP_CU(cudaEventRecord(done, p->st));
+  return ESP_OK;
+}
+
+}  // namespace
+
+namespace espe {
+
+esp_status plan_enqueue_step(esp_plan_t p, const double* xyz, double* forces, double* potential,
+                             double* energy, int* err_host, cudaEvent_t done) {
+  if (!p || !xyz || !forces || !potential || !energy || !err_host) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  if (!p->have_q) return fail(ESP_ERR_NOT_READY, "charges not set");
+  if (p->N == 0) return fail(ESP_ERR_INVALID_ARG, "empty system");
+  DeviceGuard g(p->device);
+  return p->prec == ESP_FP32 ? enqueue_step<float>(p, xyz, forces, potential, energy, err_host, done)
+                             : enqueue_step<double>(p, xyz, forces, potential, energy, err_host, done);
+}
+
+size_t plan_device_bytes(esp_plan_t p) { return p ? p->bytes : 0; }
+
+int plan_device(esp_plan_t p) { return p ? p->device : 0; }
+
+}  // namespace espe
 
 // ==================================================================== batches
 namespace {

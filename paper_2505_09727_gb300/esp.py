@@ -65,6 +65,27 @@ class esp_plan_params(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class esp_server_opts(ctypes.Structure):
+    _fields_ = [
+        ("memory_budget", ctypes.c_size_t), ("device", ctypes.c_int), ("max_inflight", ctypes.c_int),
+        ("r_c", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+        ("timeout_ms", ctypes.c_double), ("reserved", ctypes.c_int * 8),
+    ]
+
+
+class esp_server_counters(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("pending", ctypes.c_int64),
+        ("running", ctypes.c_int64), ("atoms_done", ctypes.c_double), ("plans_resident", ctypes.c_int64),
+        ("plans_created", ctypes.c_int64), ("evictions", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+        ("memory_budget", ctypes.c_size_t), ("latency_p50_ms", ctypes.c_double),
+        ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _SIGNATURES = {
@@ -97,6 +118,16 @@ _SIGNATURES = {
     "esp_batch_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "esp_batch_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "esp_batch_destroy": (ctypes.c_int, [_P]),
+    "esp_server_opts_init": (None, [ctypes.POINTER(esp_server_opts)]),
+    "esp_server_create": (ctypes.c_int, [ctypes.POINTER(esp_server_opts), ctypes.POINTER(_P)]),
+    "esp_server_add_system": (ctypes.c_int, [_P, ctypes.POINTER(esp_box), ctypes.c_int64, _P,
+                                             ctypes.POINTER(ctypes.c_int)]),
+    "esp_server_submit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "esp_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+    "esp_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _D]),
+    "esp_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(esp_server_counters)]),
+    "esp_server_reset_stats": (ctypes.c_int, [_P]),
+    "esp_server_destroy": (ctypes.c_int, [_P]),
     "esp_local_part_static": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
                                              ctypes.POINTER(esp_plan_opts), _P, _P, _P, _P, _P]),
     "esp_last_error": (ctypes.c_char_p, []),
@@ -405,6 +436,111 @@ class Batch:
     def close(self):
         if self.handle:
             esp_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def esp_server_opts_init() -> esp_server_opts:
+    o = esp_server_opts()
+    load_library().esp_server_opts_init(ctypes.byref(o))
+    return o
+
+
+def esp_server_create(r_c: float, **kw) -> int:
+    o = esp_server_opts_init()
+    o.r_c = float(r_c)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    out = _P()
+    _check(load_library().esp_server_create(ctypes.byref(o), ctypes.byref(out)))
+    return out.value
+
+
+def esp_server_add_system(server: int, L: float, q) -> int:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    box = esp_box((ctypes.c_double * 3)(L, L, L))
+    sid = ctypes.c_int()
+    _check(load_library().esp_server_add_system(_P(server), ctypes.byref(box), int(q.shape[0]),
+                                                _ptr(q)[0], ctypes.byref(sid)))
+    return sid.value
+
+
+def esp_server_submit(server: int, sid: int, tolerance: float, xyz) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    t = ctypes.c_int64()
+    _check(load_library().esp_server_submit(_P(server), int(sid), float(tolerance), _ptr(xyz)[0],
+                                            ctypes.byref(t)))
+    return t.value
+
+
+def esp_server_poll(server: int, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(load_library().esp_server_poll(_P(server), int(ticket), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def esp_server_wait(server: int, ticket: int, n_atoms: int, timeout_ms: float = 0.0, forces: bool = True,
+                    potential: bool = True):
+    """Returns (energy, forces (N,3) or None, potential (N,) or None, latency ms)."""
+    e = np.zeros(1)
+    f = np.zeros((n_atoms, 3)) if forces else None
+    u = np.zeros(n_atoms) if potential else None
+    lat = ctypes.c_double()
+    _check(load_library().esp_server_wait(_P(server), int(ticket), float(timeout_ms), _ptr(e)[0], _ptr(f)[0],
+                                          _ptr(u)[0], ctypes.byref(lat)))
+    return float(e[0]), f, u, lat.value
+
+
+def esp_server_stats(server: int) -> dict:
+    c = esp_server_counters()
+    _check(load_library().esp_server_stats(_P(server), ctypes.byref(c)))
+    return c.as_dict()
+
+
+def esp_server_reset_stats(server: int):
+    _check(load_library().esp_server_reset_stats(_P(server)))
+
+
+def esp_server_destroy(server: int):
+    _check(load_library().esp_server_destroy(_P(server)))
+
+
+class Server:
+    """Owning handle of a request server (host arrays in, host arrays out)."""
+
+    def __init__(self, r_c: float, **opts):
+        self.handle = esp_server_create(r_c, **opts)
+        self.sizes = []
+
+    def add_system(self, L: float, q) -> int:
+        sid = esp_server_add_system(self.handle, L, q)
+        self.sizes.append(int(np.asarray(q).shape[0]))
+        return sid
+
+    def submit(self, sid: int, tolerance: float, xyz) -> tuple:
+        return esp_server_submit(self.handle, sid, tolerance, xyz), sid
+
+    def wait(self, req: tuple, **kw):
+        ticket, sid = req
+        return esp_server_wait(self.handle, ticket, self.sizes[sid], **kw)
+
+    def stats(self) -> dict:
+        return esp_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            esp_server_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

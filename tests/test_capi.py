@@ -110,3 +110,14 @@ def test_null_arguments(lib):
     assert so.esp_plan_query(None, 10, 1e-4, None, None) == 1
     assert so.esp_destroy(None) == 0
     assert so.esp_plan_info(None, None) == 1
+
+
+def test_server_argument_checks_without_device(lib):
+    so = lib.load_library()
+    o = lib.esp_server_opts_init()
+    assert o.max_inflight == 8 and o.precision == lib.ESP_FP32
+    out = ctypes.c_void_p()
+    assert so.esp_server_create(ctypes.byref(o), ctypes.byref(out)) == 1     # r_c missing
+    assert "r_c" in lib.esp_last_error()
+    assert so.esp_server_create(None, None) == 1
+    assert so.esp_server_destroy(None) == 0
