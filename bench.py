@@ -57,10 +57,8 @@ def parse():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2505_09727_gb300 import replicas
+    return replicas.dist_env()
 
 
 # ------------------------------------------------------------------ clocks
@@ -198,9 +196,10 @@ def run_gpu(args, world, rank, local):
         step()
     torch.cuda.synchronize(dev)
 
+    from paper_2505_09727_gb300 import replicas
+
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -251,16 +250,13 @@ def run_gpu(args, world, rank, local):
     esp.esp_destroy(h)
 
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and world == 1:
         extras["plain_fp64"] = single_variant(args, local, stream, flush, s, precision=esp.ESP_FP64)
         extras["gaussian"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS)
         extras["batched"] = batched(args, local, stream, flush)
         extras["served"] = served(args, local)
 
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
+    total_ms, e2e_s = replicas.max_over_ranks([total_ms, e2e_s], device=dev)
     phases = {k: v / args.steps for k, v in phase_acc.items()}
     return dict(N=N, L=L, info=info, total_ms=total_ms, step_ms=step_ms, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, phases=phases, clocks=clocks, energy=float(e.cpu()[0]), extras=extras)
@@ -511,14 +507,13 @@ def main():
         print(json.dumps(line))
         return 0
 
+    from paper_2505_09727_gb300 import replicas
     if world > 1:
-        import torch
-        torch.distributed.init_process_group("nccl")
+        replicas.init("nccl")
     r = run_gpu(args, world, rank, local)
     N = r["N"]
-    atoms_total = N * args.steps * world
-    value = atoms_total / (r["total_ms"] * 1e-3)
-    e2e_value = N * r["e2e_steps"] * world / r["e2e_s"]
+    value = replicas.whole_job_rate(N * args.steps, world, r["total_ms"] * 1e-3)
+    e2e_value = replicas.whole_job_rate(N * r["e2e_steps"], world, r["e2e_s"])
     # our kernels per step (cuFFT's own and memsets not counted): ingest, 3 scan
     # passes, scatter, local part (column clusters, 3 scan passes, cluster
     # list, pair kernel), spread, scale, gather, finalize, energy
@@ -545,9 +540,7 @@ def main():
         line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line))
-    if world > 1:
-        import torch
-        torch.distributed.destroy_process_group()
+    replicas.finalize()
     return 0
 
 
