@@ -3,14 +3,14 @@
 * Table 2 (optimal values): eps -> alpha_G, c_pswf, P_esp, R_default.
 * Eq. pswfparameters: c from psi_0^c(1) = eps, n_f = ceil(c L / (pi r_c)).
 * Eq. cemparameters: alpha_G = ln(1/eps), n_f = 2 ceil(ln(1/eps) L / (pi r_c)).
-* "The even number of modes in each dimension" (spectral part): n_f is even.
+* The spectral part uses an even number of modes per axis: n_f is even.
 
 Readings (the paper does not fix these):
   * n_f is rounded up to an even FFT-friendly size 2^a 3^b 5^c 7^d (a larger n_f
     only lowers the truncation error).
   * P between Table 2's tolerances takes the entry of the next tighter one;
     below 1e-5 it is extrapolated as ceil(log10(1/eps)) + 3.
-  * The SI-kernel shape c1 ("slightly larger than c") minimises the relative
+  * The SI-kernel shape c1 (the paper only says it exceeds c a little) minimises the relative
     aliasing estimate over c1/c in [1.1, 1.4]; n_f is raised until that estimate
     is at most eps/2 (``plan``). C1_RATIO = 1.2 is the fixed default of
     ``pswf_parameters``.

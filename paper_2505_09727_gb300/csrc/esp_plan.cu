@@ -7,10 +7,10 @@
 //    an even FFT-friendly size;
 //  * the SI-kernel shape c1 is the one of c1/c in {1.10, 1.15, ..., 1.40} that
 //    minimises the relative aliasing estimate (Eq. errorformula), and n_f is
-//    raised until that minimum is at most eps/2 ("n_f possibly increased,
-//    until [E_A] is of order eps");
+//    raised until that minimum is at most eps/2 (the paper lets n_f grow until
+//    the estimate is of the order of the tolerance);
 //  * r_c, when not given, minimises a GPU cost model of the local and
-//    spectral parts ("r_c may be adjusted to balance the computational costs").
+//    spectral parts (the paper leaves r_c free to balance the two costs).
 #include "esp_plan.h"
 
 #include <algorithm>
