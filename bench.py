@@ -122,25 +122,50 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+NEAR_FLOPS_PER_PAIR = 71     # flops of one unordered pair evaluation
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "near_cluster_water3e5_traffic.md")
+NEAR_SOURCE = os.path.join(ROOT, "paper_2505_09727_gb300", "csrc", "esp_near_cluster.cuh")
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of the local-part kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    if kernel != "near" or not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    fields = {}
+    for line in open(TRAFFIC_PROFILE):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            fields[k.strip().strip("-* `")] = v.strip().strip("`")
+    with open(NEAR_SOURCE, "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()
+    if fields.get("source_sha256") != digest:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def roofline(phases: dict, info: dict, n_atoms: int, L: float, clocks, n_steps: int):
-    """Roofline of the dominant kernel (largest average duration).
+    """Roofline of the dominant kernel (largest average serialised duration).
 
     Algorithmic work per launch:
-      near    FP32 ALU: pairs within r_c (N * 4/3 pi r_c^3 rho, full list) x
+      near    FP32 ALU: unique pairs within r_c (N * 4/3 pi r_c^3 rho / 2) x
               NEAR_FLOPS_PER_PAIR, against 152 SMs x 128 FP32 lanes x 2 flop x
               the median SM clock seen during the run
       spread  HBM: 16 B/atom (sorted atoms) + 4 B per grid point (grid write)
       gather  HBM: 16 B/atom in + 16 B/atom out + 4 B per grid point
       scale   HBM: 16 B per complex mode (read + write)
     """
-    near_flops_per_pair = 90.0
     rho = n_atoms / L ** 3
-    pairs = n_atoms * 4.0 / 3.0 * math.pi * info["r_c"] ** 3 * rho
+    pairs = 0.5 * n_atoms * 4.0 / 3.0 * math.pi * info["r_c"] ** 3 * rho
     n_f = info["n_f"]
     grid = n_f ** 3
     modes = n_f * n_f * (n_f // 2 + 1)
     algo = {
-        "near": ("alu", pairs * near_flops_per_pair, "TFLOP/s"),
+        "near": ("alu", pairs * NEAR_FLOPS_PER_PAIR, "TFLOP/s"),
         "spread": ("hbm", 16.0 * n_atoms + 4.0 * grid, "GB/s"),
         "gather": ("hbm", 32.0 * n_atoms + 4.0 * grid, "GB/s"),
         "scale": ("hbm", 16.0 * modes, "GB/s"),
@@ -153,13 +178,14 @@ def roofline(phases: dict, info: dict, n_atoms: int, L: float, clocks, n_steps: 
         mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1492.0)
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
         achieved = work / t / 1e12
-        peak_note = f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median SM clock in the run)"
+        peak_note = (f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median SM clock in the "
+                     f"run); no measured FP32 peak in MEASURED_PEAKS.json")
     else:
         peak = peaks["hbm_gbs"]
         achieved = work / t / 1e9
         peak_note = f"{source} HBM copy bandwidth"
     return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+            "frac": achieved / peak, "traffic": profiled_traffic(kernel), "peak_source": peak_note,
             "algorithmic_per_launch": work, "avg_launch_ms": phases[kernel]}
 
 

@@ -162,8 +162,9 @@ esp_status esp_compute_f32(esp_plan_t plan, double* energy, float* forces,
 esp_status esp_synchronize(esp_plan_t plan);
 
 /* Per-phase device times (ms) of the last compute when timing is enabled:
- * [0] ingest+sort, [1] spread, [2] r2c, [3] scale, [4] c2r, [5] gather,
- * [6] near, [7] finalize, [8] whole compute. enable = 1 records CUDA events
+ * [0] ingest+sort (with the local part's cluster lists), [1] spread,
+ * [2] r2c, [3] scale, [4] c2r, [5] gather, [6] near (the pair kernel),
+ * [7] finalize, [8] whole compute. enable = 1 records CUDA events
  * around the phases (the local part still overlaps the spectral part, so the
  * spectral phases include contention); enable = 2 also runs the local part on
  * the main stream so that every phase is timed alone; 0 turns timing off.

@@ -138,7 +138,7 @@ struct esp_plan_s {
 
   cudaStream_t st = nullptr, st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaEvent_t tev[13] = {};
+  cudaEvent_t tev[14] = {};
   float phase_ms[kPhases] = {};
   bool timed_valid = false;      // events of the last compute were recorded
   std::vector<double> e_fourier, e_gather;
@@ -491,19 +491,26 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
     ESP_CU(cudaEventRecord(p->ev_fork, st));
     ESP_CU(cudaStreamWaitEvent(st2, p->ev_fork, 0));
   }
-  rec(p, 9, st2);
   const espk::NearCoef<real>& nc = *reinterpret_cast<const espk::NearCoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.nc32 : (const void*)&hp.nc64);
   const espk::SICoef<real>& si = *reinterpret_cast<const espk::SICoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.si32 : (const void*)&hp.si64);
-  if (hp.near_clusters)
+  if (hp.near_clusters) {
+    // cluster lists (timed with the bin sort), then the pair kernel alone
+    // between the local-part events
+    rec(p, 13, st2);
     ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
                             p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
-                            hp.near_half,
-                            p->N, p->d_err, st2));
-  else
+                            hp.near_half, p->N, 2, p->d_err, st2));
+    rec(p, 9, st2);
+    ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
+                            p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
+                            hp.near_half, p->N, 1, p->d_err, st2));
+  } else {
+    rec(p, 9, st2);
     ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
                    hp.near_nc, hp.near_queued, st2));
+  }
   rec(p, 10, st2);
   if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
 
@@ -778,6 +785,7 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
     return t;
   };
   p->phase_ms[0] = el(0, 1) + el(2, 12);  // ingest + scan, scatter
+  if (p->hps[0].near_clusters) p->phase_ms[0] += el(13, 9);   // cluster lists
   p->phase_ms[1] = el(3, 4);              // spread (with grid clear)
   p->phase_ms[2] = el(4, 5);              // R2C FFT
   p->phase_ms[3] = el(5, 6);              // scale + energy

@@ -22,14 +22,19 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
                                          const uint32_t* start, const void* rel, void* nearres,
                                          const NearCoef<float>& nc, int terms, uint32_t* ccount,
                                          uint32_t* cstart, uint32_t* ctiles, int2* cmap, int2* catoms,
-                                         long long cmap_cap, bool half, long long n_atoms, int* err,
-                                         cudaStream_t st) {
+                                         long long cmap_cap, bool half, long long n_atoms, int stage,
+                                         int* err, cudaStream_t st) {
   if (n_cols == 0) return cudaSuccess;
-  const int cb = (int)((n_cols * 32 + 255) / 256);     // one warp per column
-  k_col_clusters<<<cb, 256, 0, st>>>(sys, nsys, n_cols, start, ccount);
-  cudaError_t e = launch_scan(ccount, cstart, ctiles, n_cols, st);
-  if (e != cudaSuccess) return e;
-  k_cluster_expand<<<cb, 256, 0, st>>>(sys, nsys, n_cols, ccount, cstart, start, cmap, catoms, cmap_cap, err);
+  cudaError_t e = cudaSuccess;
+  if (!(stage & 1)) {
+    // cluster lists
+    const int cb = (int)((n_cols * 32 + 255) / 256);     // one warp per column
+    k_col_clusters<<<cb, 256, 0, st>>>(sys, nsys, n_cols, start, ccount);
+    e = launch_scan(ccount, cstart, ctiles, n_cols, st);
+    if (e != cudaSuccess) return e;
+    k_cluster_expand<<<cb, 256, 0, st>>>(sys, nsys, n_cols, ccount, cstart, start, cmap, catoms, cmap_cap, err);
+    if (stage == 2) return cudaGetLastError();
+  }
   decltype(&k_near_cluster<ESP_NEAR_SHORT, false>) kern = nullptr;
   if (terms == ESP_NEAR_SHORT) kern = half ? k_near_cluster<ESP_NEAR_SHORT, true> : k_near_cluster<ESP_NEAR_SHORT, false>;
   else if (terms == Deg<float>::nr) kern = half ? k_near_cluster<Deg<float>::nr, true> : k_near_cluster<Deg<float>::nr, false>;

@@ -31,11 +31,12 @@ struct Launch {
   // scan_tiles(n_cols) entries), the cluster list into cmap[cmap_cap] and
   // catoms[cmap_cap * 8], then the pair kernel; half = each pair once
   // (Newton's third law, atomics into nearres[n_atoms], cleared first).
+  // stage 0: everything; 2: the cluster lists only; 1: the pair kernel only.
   static cudaError_t near_clusters(const SysDesc* sys, int nsys, long long n_cols, const uint32_t* start,
                                    const void* rel, void* nearres, const NearCoef<real>& nc, int terms,
                                    uint32_t* ccount, uint32_t* cstart, uint32_t* ctiles, int2* cmap,
-                                   int2* catoms, long long cmap_cap, bool half, long long n_atoms, int* err,
-                                   cudaStream_t st);
+                                   int2* catoms, long long cmap_cap, bool half, long long n_atoms, int stage,
+                                   int* err, cudaStream_t st);
   static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                               const uint32_t* perm, const void* far, const void* nearres,
                               void* forces, void* pot, bool out_double, double* partials,
