@@ -281,6 +281,7 @@ def run_gpu(args, world, rank, local):
         extras["gaussian"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS)
         extras["batched"] = batched(args, local, stream, flush)
         extras["served"] = served(args, local)
+        extras["large"] = large(args, local, stream, flush)
 
     total_ms, e2e_s = replicas.max_over_ranks([total_ms, e2e_s], device=dev)
     phases = {k: v / args.steps for k, v in phase_acc.items()}
@@ -303,13 +304,13 @@ def time_steps(step, stream, steps: int, flush) -> list:
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
-def single_variant(args, local, stream, flush, s, **opts):
-    """atoms/s of the single-system path with other plan options (same workload)."""
+def single_variant(args, local, stream, flush, s, tolerance=None, **opts):
+    """atoms/s of the single-system path with other plan options."""
     import torch
     from paper_2505_09727_gb300 import esp
     dev = torch.device("cuda", local)
-    h = esp.esp_plan(s.L, s.n, WORKLOAD["tolerance"], r_c=WORKLOAD["r_c_nm"], device=local,
-                     stream=stream.cuda_stream, **opts)
+    tol = WORKLOAD["tolerance"] if tolerance is None else tolerance
+    h = esp.esp_plan(s.L, s.n, tol, r_c=WORKLOAD["r_c_nm"], device=local, stream=stream.cuda_stream, **opts)
     info = esp.esp_plan_info(h)
     x = torch.tensor(s.pos, device=dev)
     e = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -326,7 +327,23 @@ def single_variant(args, local, stream, flush, s, **opts):
     esp.esp_destroy(h)
     t = statistics.median(ms)
     return {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
-            "steps": len(ms)}
+            "tolerance": tol, "steps": len(ms)}
+
+
+LARGE = dict(workload="spce_water_1e6_molecules", molecules=1_000_000, atoms=3_000_000, density_per_nm3=33.4,
+             r_c_nm=1.0, tolerance=1e-5, seed=2505)
+
+
+def large(args, local, stream, flush):
+    """3e6-atom water box at 1e-5: PSWF split against the Gaussian split on
+    the same machinery (the grid ratio is the method's point)."""
+    from paper_2505_09727_gb300 import inputs
+    s = inputs.spce_water(LARGE["molecules"], seed=LARGE["seed"])
+    pswf = single_variant(args, local, stream, flush, s, tolerance=LARGE["tolerance"])
+    gauss = single_variant(args, local, stream, flush, s, tolerance=LARGE["tolerance"], kernel=1)
+    return {"value": pswf["value"], "unit": UNIT, "pswf": pswf, "gaussian": gauss,
+            "grid_points_ratio": (gauss["n_f"] / pswf["n_f"]) ** 3, "speedup_vs_gaussian": pswf["value"] / gauss["value"],
+            "config": dict(LARGE, L_nm=s.L)}
 
 
 BATCH = dict(workload="electrolyte_batch_64", systems=64, atoms_lo=3000, atoms_hi=200_000,

@@ -178,6 +178,23 @@ esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* 
 
 esp_status esp_destroy(esp_plan_t plan);
 
+/* Autotuner. The paper has no counterpart (its kernels are CPU code): the
+ * shapes this implementation is free to choose -- cell-list reach (cell edge
+ * r_c/2 or r_c/3), local-part kernel (near_variant 3: every pair from both
+ * sides; 4: every pair once) and the brick edge of spread/gather (the
+ * planner's choice and one cell either side) -- are timed on the caller's own
+ * system: for each candidate a plan is made, charges q[N] and positions
+ * xyz[N*3] (FP64, host or device per `where`) are set, one warm-up compute
+ * runs, then `reps` timed computes (0 = 5); the median whole-compute time
+ * decides. Options fixed in `opts` (non-zero) are kept. *out receives opts
+ * with the winning shapes (and the planner's r_c); *best_ms its time. Results
+ * are cached per process by (N, L, tolerance, r_c, precision, kernel,
+ * device), so a second call returns at once. Allocates and frees a plan per
+ * candidate; synchronous. */
+esp_status esp_autotune(const esp_box* box, int64_t N, double tolerance, const esp_plan_opts* opts,
+                        const double* xyz, const double* q, int where, int reps,
+                        esp_plan_opts* out, double* best_ms);
+
 /* ------------------------------------------------------------------ batches
  * Many independent systems (each its own cubic box, charges and positions)
  * solved together in one step: the same pipeline as esp_compute runs once

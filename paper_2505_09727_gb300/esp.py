@@ -118,6 +118,9 @@ _SIGNATURES = {
     "esp_batch_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "esp_batch_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "esp_batch_destroy": (ctypes.c_int, [_P]),
+    "esp_autotune": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
+                                    ctypes.POINTER(esp_plan_opts), _P, _P, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(esp_plan_opts), _D]),
     "esp_server_opts_init": (None, [ctypes.POINTER(esp_server_opts)]),
     "esp_server_create": (ctypes.c_int, [ctypes.POINTER(esp_server_opts), ctypes.POINTER(_P)]),
     "esp_server_add_system": (ctypes.c_int, [_P, ctypes.POINTER(esp_box), ctypes.c_int64, _P,
@@ -294,6 +297,23 @@ def esp_local_part_static(L: float, N: int, tolerance: float, xyz, q, energy=Non
     _check(load_library().esp_local_part_static(
         ctypes.byref(box), int(N), float(tolerance), ctypes.byref(opts), _ptr(xyz)[0], _ptr(q)[0],
         _ptr(energy)[0], _ptr(forces)[0], _ptr(potential)[0]))
+
+
+def esp_autotune(L: float, tolerance: float, xyz, q, reps: int = 5, opts: esp_plan_opts | None = None,
+                 **kw) -> tuple[dict, float]:
+    """Time candidate shapes on this system; returns (chosen options, ms)."""
+    if opts is None:
+        opts = make_opts(**kw)
+    pxyz, w = _ptr(xyz)
+    pq, _ = _ptr(q)
+    n = int(getattr(q, "shape", [len(q)])[0])
+    box = esp_box((ctypes.c_double * 3)(L, L, L))
+    out = esp_plan_opts()
+    ms = ctypes.c_double()
+    _check(load_library().esp_autotune(ctypes.byref(box), n, float(tolerance), ctypes.byref(opts), pxyz, pq,
+                                       w, int(reps), ctypes.byref(out), ctypes.byref(ms)))
+    chosen = {name: getattr(out, name) for name, _ in out._fields_ if name not in ("reserved", "stream")}
+    return chosen, ms.value
 
 
 def esp_batch_create(boxes, N, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> int:

@@ -121,3 +121,10 @@ def test_server_argument_checks_without_device(lib):
     assert "r_c" in lib.esp_last_error()
     assert so.esp_server_create(None, None) == 1
     assert so.esp_server_destroy(None) == 0
+
+
+def test_autotune_argument_checks(lib):
+    so = lib.load_library()
+    box = lib.esp_box((ctypes.c_double * 3)(5.0, 5.0, 5.0))
+    out = lib.esp_plan_opts()
+    assert so.esp_autotune(ctypes.byref(box), 10, 1e-4, None, None, None, 0, 3, ctypes.byref(out), None) == 1
