@@ -98,7 +98,7 @@ def test_small_budget_evicts_and_still_answers(esp):
 
 def test_system_larger_than_budget_is_refused(esp):
     s = inputs.electrolyte(20000, seed=320)
-    with esp.Server(1.0, memory_budget=8 << 20) as srv:
+    with esp.Server(1.0, memory_budget=1 << 20) as srv:     # below any plan's need
         sid = srv.add_system(s.L, s.q)
         with pytest.raises(esp.EspError) as exc:
             srv.wait(srv.submit(sid, 1e-4, s.pos))
