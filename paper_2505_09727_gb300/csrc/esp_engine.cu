@@ -779,9 +779,15 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
   if (!p->timing || !p->timed_valid) return fail(ESP_ERR_NOT_READY, "timing is off or no timed compute yet");
   DeviceGuard g(p->device);
   ESP_TRY(wait_stream(p, p->st));
+  // a pair of events that was not recorded (e.g. positions set before timing
+  // was enabled) reads as 0; its error is cleared so that later launches do
+  // not see it
   auto el = [&](int a, int b) {
     float t = 0.f;
-    cudaEventElapsedTime(&t, p->tev[a], p->tev[b]);
+    if (cudaEventElapsedTime(&t, p->tev[a], p->tev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
     return t;
   };
   p->phase_ms[0] = el(0, 1) + el(2, 12);  // ingest + scan, scatter

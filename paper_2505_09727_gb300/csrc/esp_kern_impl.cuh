@@ -157,7 +157,8 @@ cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
   decltype(&k_near<ESP_REAL, ESP_NEAR_SHORT, true>) kern = nullptr;
-  if (terms == ESP_NEAR_SHORT)
+  // fewer terms run on the shorter instance: the unused coefficients are zero
+  if (terms <= ESP_NEAR_SHORT)
     kern = queued ? k_near<ESP_REAL, ESP_NEAR_SHORT, true> : k_near<ESP_REAL, ESP_NEAR_SHORT, false>;
   else if (terms == Deg<ESP_REAL>::nr)
     kern = queued ? k_near<ESP_REAL, Deg<ESP_REAL>::nr, true> : k_near<ESP_REAL, Deg<ESP_REAL>::nr, false>;

@@ -204,24 +204,24 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
         const float4 ci = W.idata[t];
         const float dx = ci.x - jd.x, dy = ci.y - jd.y, dz = ci.z - jd.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const bool in = r2 < rc2 && r2 > 0.f;
-        const float r2m = in ? r2 : rc2;
-        const float qe = in ? jd.w : 0.f;
-        const float rinv = rsqrtf(r2m);
-        const float y = fmaf(r2m, inv_rc2x2, -1.f);
+        // HALF never queues a cluster atom against itself, so 0 < r2 holds
+        // for distinct positions; the full form meets the cluster's own atoms
+        const bool in = HALF ? r2 < rc2 : (r2 < rc2 && r2 > 0.f);
+        // masked pairs may give inf or NaN here; the selects below drop them
+        const float rinv = rsqrtf(r2);
+        const float y = fmaf(r2, inv_rc2x2, -1.f);
         const float h = horner_f<NC>(nc.h, y);
         const float kk = horner_f<NC>(nc.k, y);
-        const float t1 = fmaf(-h, inv_rc, rinv);
-        const float t2 = fmaf(kk, inv_rc3, rinv * rinv * rinv);
-        pu[t] = fmaf(qe, t1, pu[t]);
-        const float fs = qe * t2;
+        const float t1 = in ? fmaf(-h, inv_rc, rinv) : 0.f;
+        const float t2 = in ? fmaf(kk, inv_rc3, rinv * rinv * rinv) : 0.f;
+        pu[t] = fmaf(jd.w, t1, pu[t]);
+        const float fs = jd.w * t2;
         px[t] = fmaf(fs, dx, px[t]);
         py[t] = fmaf(fs, dy, py[t]);
         pz[t] = fmaf(fs, dz, pz[t]);
         if constexpr (HALF) {
-          const float qie = in ? ci.w : 0.f;
-          uj = fmaf(qie, t1, uj);
-          const float fsj = qie * t2;
+          uj = fmaf(ci.w, t1, uj);
+          const float fsj = ci.w * t2;
           fjx = fmaf(fsj, dx, fjx);
           fjy = fmaf(fsj, dy, fjy);
           fjz = fmaf(fsj, dz, fjz);

@@ -216,9 +216,10 @@ static NearTables make_near_tables(const espm::Split& split, double tol) {
     for (size_t i = 0; i < gq_x.size(); ++i) acc += gq_w[i] * gq_x[i] * split.dchi(x * gq_x[i]);
     return acc / x;
   };
-  // FP32: 10 terms when that fit is 100x below the tolerance, else 12
+  // FP32: the fewest of 8, 9, 10 or 12 terms whose fit error is 100x below
+  // the tolerance
   const double scale = std::max(std::fabs(fh(-1.0)), std::fabs(fk(1.0)));
-  for (int terms : {10, espk::Deg<float>::nr}) {
+  for (int terms : {8, 9, 10, espk::Deg<float>::nr}) {
     std::vector<double> ch, ck;
     const double e1 = fit(fh, terms - 1, ch);
     const double e2 = fit(fk, terms - 1, ck);
@@ -330,10 +331,12 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
   const espm::Window win = cached_window(best_c1, P);
 
-  // cell list and bricks: cell edge w >= r_c / reach. A reach of 3 (smaller
-  // cells) reads fewer non-neighbours in the local part; it needs at least a
-  // few cells per axis to pay off.
-  int reach = o.cell_reach > 0 ? o.cell_reach : 3;
+  // cell list and bricks: cell edge w >= r_c / reach. For the one-thread-per-
+  // atom local part a reach of 3 (smaller cells) reads fewer non-neighbours;
+  // the cluster form lists whole columns and runs faster with reach 2 (fewer
+  // ranges per cluster). Reach 3 needs a few cells per axis to pay off.
+  const bool cluster_form = prec == ESP_FP32 && (o.near_variant >= 3 || o.near_variant == 0);
+  int reach = o.cell_reach > 0 ? o.cell_reach : (cluster_form ? 2 : 3);
   if (reach < 1 || reach > 4) { msg = "cell_reach must be 1 ... 4"; return ESP_ERR_INVALID_ARG; }
   if (o.cell_reach <= 0 && std::floor(3.0 * L / r_c) < 9) reach = 2;
   // the local part keeps per-axis cell tables in shared memory (512 entries)
@@ -343,7 +346,8 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     return ESP_ERR_UNSUPPORTED;
   }
   const int nc_max = std::max(1, (int)std::floor(reach * L / r_c * (1.0 - 1e-12)));
-  // brick = bc^3 cells; prefer a brick edge near 8 grid points among shapes
+  // brick = bc^3 cells; prefer a brick edge near 6.5 grid points (measured
+  // best for the spread and gather tiles) among shapes
   // that keep at least 90% of the finest admissible cell count
   const double h = L / n_f;
   int n_c = 0, bc = 0, T = 0;
@@ -360,7 +364,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     if ((size_t)t * t * t * rb > 200 * 1024) continue;
     const double edge = (double)b * n_f / nc;            // brick edge in grid points
     const double keep = (double)nc / nc_max;
-    double score = -std::fabs(std::log(edge / 8.0));
+    double score = -std::fabs(std::log(edge / 6.5));
     if (keep < 0.9) score -= 10.0 + (1.0 - keep) * 10.0;
     if (score > best_score) { best_score = score; n_c = nc; bc = b; T = t; }
   }

@@ -167,8 +167,10 @@ extern "C" esp_status esp_local_part_static(const esp_box* box, int64_t N, doubl
   const double L = box->L[0];
   if (!(std::fabs(box->L[1] - L) <= 1e-12 * std::fabs(L) && std::fabs(box->L[2] - L) <= 1e-12 * std::fabs(L)))
     return sfail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
-  // the grid is not used here: keep the planner's spectral work minimal
+  // the grid is not used here: keep the planner's spectral work minimal;
+  // this entry runs the one-thread-per-atom local part, so plan for it
   if (o.n_f == 0) o.n_f = 4;
+  if (o.near_variant == 0 || o.near_variant >= 3) o.near_variant = 1;
   espe::HostPlan hp;
   std::string msg;
   esp_status s = espe::make_host_plan(L, N, tolerance, o, hp, msg);

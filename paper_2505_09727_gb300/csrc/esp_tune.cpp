@@ -43,24 +43,30 @@ esp_status tfail(esp_status s, const std::string& m) {
 // Median whole-compute time of `reps` computes with options o (ms), or a
 // negative value when the candidate cannot be planned or run.
 double time_candidate(const esp_box* box, int64_t N, double tol, const esp_plan_opts& o, const double* xyz,
-                      const double* q, int where, int reps, esp_plan_params* info) {
+                      const double* q, int where, int reps, esp_plan_params* info, std::string* why) {
   esp_plan_t p = nullptr;
-  if (esp_plan(box, N, tol, &o, &p) != ESP_OK) return -1.0;
+  if (esp_plan(box, N, tol, &o, &p) != ESP_OK) {
+    *why = esp_last_error();
+    return -1.0;
+  }
   double best = -1.0;
-  if (esp_plan_info(p, info) == ESP_OK && esp_set_charges(p, q, where) == ESP_OK &&
-      esp_set_positions(p, xyz, where) == ESP_OK && esp_compute(p, nullptr, nullptr, nullptr, ESP_HOST) == ESP_OK &&
-      esp_set_timing(p, 1) == ESP_OK) {
-    std::vector<double> t;
-    for (int r = 0; r < reps; ++r) {
-      float ms[9];
-      if (esp_compute(p, nullptr, nullptr, nullptr, ESP_HOST) != ESP_OK) break;
-      if (esp_phase_times(p, ms, 9) != ESP_OK) break;
-      t.push_back(ms[8]);
-    }
-    if ((int)t.size() == reps) {
-      std::sort(t.begin(), t.end());
-      best = t[t.size() / 2];
-    }
+  esp_status st = esp_plan_info(p, info);
+  if (st == ESP_OK) st = esp_set_charges(p, q, where);
+  if (st == ESP_OK) st = esp_set_positions(p, xyz, where);
+  if (st == ESP_OK) st = esp_compute(p, nullptr, nullptr, nullptr, ESP_HOST);
+  if (st == ESP_OK) st = esp_set_timing(p, 1);
+  std::vector<double> t;
+  for (int r = 0; st == ESP_OK && r < reps; ++r) {
+    float ms[9];
+    st = esp_compute(p, nullptr, nullptr, nullptr, ESP_HOST);
+    if (st == ESP_OK) st = esp_phase_times(p, ms, 9);
+    if (st == ESP_OK) t.push_back(ms[8]);
+  }
+  if (st == ESP_OK && (int)t.size() == reps) {
+    std::sort(t.begin(), t.end());
+    best = t[t.size() / 2];
+  } else {
+    *why = esp_last_error();
   }
   esp_destroy(p);
   return best;
@@ -104,6 +110,7 @@ extern "C" esp_status esp_autotune(const esp_box* box, int64_t N, double toleran
   else if (base.precision == ESP_FP32) variants = {3, 4};
   else variants = {1};
   TuneResult best{0, 0, 0, -1.0};
+  std::string why;
   for (int reach : reaches) {
     for (int var : variants) {
       esp_plan_opts o = base;
@@ -122,12 +129,13 @@ extern "C" esp_status esp_autotune(const esp_box* box, int64_t N, double toleran
       }
       for (int b : bricks) {
         o.brick_cells = b;
-        const double ms = time_candidate(box, N, tolerance, o, xyz, q, where, reps, &info);
+        const double ms = time_candidate(box, N, tolerance, o, xyz, q, where, reps, &info, &why);
         if (ms > 0 && (best.ms < 0 || ms < best.ms)) best = TuneResult{reach, var, b, ms};
       }
     }
   }
-  if (best.ms < 0) return tfail(ESP_ERR_INTERNAL, "no candidate configuration could be planned and run");
+  if (best.ms < 0)
+    return tfail(ESP_ERR_INTERNAL, "no candidate configuration could be planned and run (" + why + ")");
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;

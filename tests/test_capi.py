@@ -65,7 +65,10 @@ def test_planner_matches_oracle_reading(lib, L, N, eps, r_c):
     # cell list: edge >= r_c / reach, bricks divide the cell grid
     assert L / got["n_cells"] >= r_c / got["cell_reach"]
     assert got["n_cells"] % got["brick_cells"] == 0
-    assert got["si_fit_error"] < 1e-8 and got["near_fit_error"] < 1e-7
+    # local-part polynomials: the fewest terms whose fit error stays 100x
+    # below the tolerance (scaled by the correction's size, about 3)
+    assert got["si_fit_error"] < 1e-8 and got["near_fit_error"] <= 0.01 * eps * 3.1
+    assert got["near_terms"] in (8, 9, 10, 12)
 
 
 def test_planner_gaussian_split(lib):

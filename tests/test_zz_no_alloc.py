@@ -79,7 +79,10 @@ def test_energy_matches_plan_minus_spectral_part(lib, precision, bound):
 @pytest.mark.parametrize("precision,bound", [(1, 1e-10), (0, FP32_PARITY)])
 def test_matches_plan_when_spectral_part_vanishes(lib, precision, bound):
     s = inputs.electrolyte(5000, seed=32)
-    opts = dict(r_c=1.0, kernel=lib.ESP_KERNEL_GAUSS, alpha=1e-12, precision=precision)
+    # the same cell list on both sides (reach and one-cell bricks fixed), so
+    # both decide r < r_c from the same FP32 coordinates
+    opts = dict(r_c=1.0, kernel=lib.ESP_KERNEL_GAUSS, alpha=1e-12, precision=precision, cell_reach=3,
+                brick_cells=1)
     e_ref, f_ref, u_ref, e_fourier = plan_based(lib, s, 1e-4, **opts)
     assert e_fourier == 0.0
     results = [static_call(lib, s, 1e-4, **opts) for _ in range(2)]   # two calls in a row
