@@ -22,6 +22,10 @@ cudaError_t launch_scan(const uint32_t* count, uint32_t* start, uint32_t* tile_s
                         cudaStream_t st) {
   const int tiles = (int)((n + kScanTile - 1) / kScanTile);
   if (tiles == 0) return cudaMemsetAsync(start, 0, sizeof(uint32_t), st);
+  if (n <= kScanSmallMax) {
+    k_scan_small<<<1, kScanThreads, 0, st>>>(count, start, n);
+    return cudaGetLastError();
+  }
   k_scan_tiles<<<tiles, kScanThreads, 0, st>>>(count, start, tile_sum, n);
   k_scan_totals<<<1, kScanThreads, 0, st>>>(tile_sum, tiles, start, n);
   k_scan_add<<<tiles, kScanThreads, 0, st>>>(start, tile_sum, n);

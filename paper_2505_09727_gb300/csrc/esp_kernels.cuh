@@ -177,7 +177,16 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
   const uint32_t k = (uint32_t)(cell_key(S, c[0], c[1], c[2]) * kSub + slab);
   coord[i] = out;
   key[i] = k;
-  rank[i] = atomicAdd(&count[S.cell0 + k], 1u);
+  // warp-aggregated: lanes with the same slab key take consecutive ranks from
+  // one atomic (input order is often spatially coherent, so keys repeat)
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, k);
+  const int leader = __ffs(peers) - 1;
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&count[S.cell0 + k], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
 // A1a: exclusive scan of the pooled cell-list counts in three passes: each
@@ -247,6 +256,29 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_totals(
   for (int j = b; j < e; ++j) {
     const uint32_t t = tile_sum[j];
     tile_sum[j] = run;
+    run += t;
+  }
+  if (threadIdx.x == 0) start[n] = total;
+}
+
+// Whole scan in one CTA for short arrays (one launch instead of three): each
+// thread sums a contiguous run of entries, the CTA scans the run sums, and
+// each thread writes its run.
+constexpr long long kScanSmallMax = (long long)kScanThreads * 16;
+
+static __global__ void __launch_bounds__(kScanThreads) k_scan_small(
+    const uint32_t* __restrict__ count, uint32_t* __restrict__ start, long long n) {
+  __shared__ uint32_t wsum[33];
+  const long long per = (n + kScanThreads - 1) / kScanThreads;
+  const long long b = per * threadIdx.x;
+  const long long e = b + per < n ? b + per : n;
+  uint32_t s = 0;
+  for (long long j = b; j < e; ++j) s += count[j];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, wsum, &total);
+  for (long long j = b; j < e; ++j) {
+    const uint32_t t = count[j];
+    start[j] = run;
     run += t;
   }
   if (threadIdx.x == 0) start[n] = total;
