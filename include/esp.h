@@ -72,6 +72,7 @@ typedef enum {
 } esp_status;
 
 enum { ESP_KERNEL_PSWF = 0, ESP_KERNEL_GAUSS = 1 };
+enum { ESP_WINDOW_PSWF = 0, ESP_WINDOW_BSPLINE = 1 };
 enum { ESP_FP32 = 0, ESP_FP64 = 1 };
 enum { ESP_HOST = 0, ESP_DEVICE = 1 };
 
@@ -98,11 +99,18 @@ typedef struct {
   int brick_cells;     /* tuning: cells per spread/gather brick edge; 0 auto */
   double timeout_ms;   /* deadline of host waits; 0 = 60000                  */
   int cell_reach;      /* tuning: cell edge ~ r_c / cell_reach (2 or 3; 0 auto) */
+  int window;          /* SI kernel: ESP_WINDOW_PSWF (default, Eq. pswf) or
+                          ESP_WINDOW_BSPLINE (centred cardinal B-spline of
+                          order P, default P 4, n_f raised until the aliasing
+                          estimate is <= tolerance/10: the "Default" PME-style
+                          comparator of Table 1, meant with ESP_KERNEL_GAUSS) */
   int near_variant;    /* tuning: local-part kernel, 1 = one thread per atom,
                           pairs evaluated in the scan, 2 = the same with pairs
-                          queued per lane, 3 = one warp per cluster of 8 atoms
-                          (FP32 only); 0 = default (3 in FP32, 1 in FP64)     */
-  int reserved[6];
+                          queued per lane, 3 = one warp per cluster of 8 atoms,
+                          every pair from both sides, 4 = the same, every pair
+                          once (FP32 only for 3, 4); 0 = default (4 in FP32,
+                          1 in FP64)                                          */
+  int reserved[5];
 } esp_plan_opts;
 
 /* Parameters a plan chose (esp_plan_info). */
@@ -120,6 +128,8 @@ typedef struct {
   int tile;                /* shared-memory tile edge in grid points         */
   int si_degree, near_degree;
   size_t device_bytes;     /* device memory held by the plan                 */
+  int window;              /* ESP_WINDOW_PSWF or ESP_WINDOW_BSPLINE          */
+  int reserved[3];
 } esp_plan_params;
 
 /* Fill opts with defaults (all planner choices, FP32, PSWF, device 0). */

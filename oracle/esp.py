@@ -46,12 +46,20 @@ class ESPParams:
     c1: float | None = None       # SI kernel shape (default: C1_RATIO * c)
     kind: str = "pswf"            # "pswf" or "gauss"
     alpha: float | None = None    # Gaussian shape (default: ln(1/eps))
+    window: str = "pswf"          # SI window: "pswf" (psi_0^{c1}) or "bspline" (order P)
 
     def resolved(self) -> "ESPParams":
         c = self.c if self.c is not None else pswf.c_from_tolerance(self.eps)
         c1 = self.c1 if self.c1 is not None else prm.C1_RATIO * c
         alpha = self.alpha if self.alpha is not None else math.log(1.0 / self.eps)
-        return ESPParams(self.eps, self.r_c, self.P, self.n_f, c, c1, self.kind, alpha)
+        return ESPParams(self.eps, self.r_c, self.P, self.n_f, c, c1, self.kind, alpha, self.window)
+
+    def si_window(self):
+        p = self.resolved()
+        if p.window == "bspline":
+            from . import bspline
+            return bspline.BSplineWindow(p.P)
+        return pswf.PSWFWindow(p.c1, p.P)
 
     def split(self):
         p = self.resolved()
@@ -177,7 +185,7 @@ def esp(pos, q, L, p: ESPParams, targets=None):
     all_atoms = targets is None
     tgt = np.arange(n) if all_atoms else np.asarray(targets, dtype=np.int64)
     split = p.split()
-    window = pswf.PSWFWindow(p.c1, p.P)
+    window = p.si_window()
     u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt)
     u_l, f_l = near_field(pos, q, L, p.r_c, split, tgt)
     self_term = q[tgt] * split.chi0 / (4.0 * math.pi * p.r_c)

@@ -274,9 +274,37 @@ Window make_window(double c1, int P) {
   return w;
 }
 
-double Window::phi(double t) const { return psi.value(2.0 * t / P); }
+Window make_bspline_window(int P) {
+  Window w;
+  w.kind = 1;
+  w.P = P;
+  return w;
+}
+
+// Cardinal B-spline M_P(x) on [0, P] by the truncated-power sum.
+static double cardinal_bspline(int P, double x) {
+  if (!(x > 0.0 && x < P)) return 0.0;
+  double s = 0.0, binom = 1.0, fact = 1.0;
+  for (int k = 1; k < P; ++k) fact *= k;                  // (P-1)!
+  for (int k = 0; k <= P; ++k) {
+    const double d = x - k;
+    if (d > 0.0) s += ((k & 1) ? -binom : binom) * std::pow(d, P - 1);
+    binom = binom * (P - k) / (k + 1);
+  }
+  return s / fact;
+}
+
+double Window::phi(double t) const {
+  if (kind == 1) return cardinal_bspline(P, t + 0.5 * P);
+  return psi.value(2.0 * t / P);
+}
 
 double Window::Phi(double theta) const {
+  if (kind == 1) {
+    const double h = 0.5 * theta;
+    const double sinc = std::fabs(h) > 1e-12 ? std::sin(h) / h : 1.0;
+    return std::pow(sinc, P);
+  }
   // int_{-P/2}^{P/2} psi(2t/P) cos(theta t) dt = P int_0^1 psi(x) cos(theta P x / 2) dx
   double s = 0.0;
   for (size_t i = 0; i < gx.size(); ++i) s += gw[i] * psi_at[i] * std::cos(0.5 * theta * P * gx[i]);

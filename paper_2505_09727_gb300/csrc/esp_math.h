@@ -45,16 +45,20 @@ struct Split {
 Split make_pswf_split(double c);
 Split make_gauss_split(double alpha);
 
-// SI kernel phi(t) = psi_0^{c1}(2t/P), t in grid units, and its transform.
+// SI kernel phi(t) in grid units t and its transform.
+// kind 0: PSWF window psi_0^{c1}(2t/P); kind 1: centred cardinal B-spline of
+// order P (piecewise polynomial of degree P-1, transform (sin(x/2)/(x/2))^P).
 struct Window {
+  int kind = 0;
   double c1 = 0;
   int P = 0;
   Pswf psi;
   std::vector<double> gx, gw, psi_at;
-  double phi(double t) const;            // analytic (no support cut)
+  double phi(double t) const;            // analytic on the support (no support cut for kind 0)
   double Phi(double theta) const;        // int phi(t) cos(theta t) dt over |t|<=P/2
 };
 Window make_window(double c1, int P);
+Window make_bspline_window(int P);
 
 // Relative aliasing estimate (Eq. errorformula divided by the same sum
 // without the alias ratio).

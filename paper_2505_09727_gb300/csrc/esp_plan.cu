@@ -281,8 +281,11 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   if (kernel != ESP_KERNEL_PSWF && kernel != ESP_KERNEL_GAUSS) { msg = "unknown kernel"; return ESP_ERR_INVALID_ARG; }
   const int pmax = prec == ESP_FP32 ? 12 : 16;
 
+  if (o.window != ESP_WINDOW_PSWF && o.window != ESP_WINDOW_BSPLINE) { msg = "unknown SI window"; return ESP_ERR_INVALID_ARG; }
+  const bool bspline = o.window == ESP_WINDOW_BSPLINE;
   const double c = o.c > 0 ? o.c : cached_c(tol);
-  const int P = o.P > 0 ? o.P : espm::stencil_width(tol);
+  // the B-spline comparator defaults to the usual smooth-PME order 4
+  const int P = o.P > 0 ? o.P : (bspline ? 4 : espm::stencil_width(tol));
   if (P < espk::kMinP || P > pmax) {
     msg = "stencil width P=" + std::to_string(P) + " outside the compiled range [4, " + std::to_string(pmax) + "]";
     return ESP_ERR_UNSUPPORTED;
@@ -317,19 +320,45 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
   if (n_f > 1024) { msg = "grid too large (n_f > 1024): raise r_c or the tolerance"; return ESP_ERR_UNSUPPORTED; }
   double best_c1 = ratios[0] * c, best_alias = 1e300;
-  std::vector<espm::Window> windows;
-  for (double r : ratios) windows.push_back(cached_window(r * c, P));
-  for (int step = 0; step < 8; ++step) {
-    const std::vector<double> rows = alias_rows(split, n_f, L, r_c);
-    best_alias = 1e300;
-    for (size_t i = 0; i < ratios.size(); ++i) {
-      const double a = alias_from_rows(rows, windows[i], n_f);
-      if (a < best_alias) { best_alias = a; best_c1 = ratios[i] * c; }
+  espm::Window bwin;
+  if (bspline) {
+    // B-spline window: no shape to choose; the aliasing estimate is
+    // calibrated on the PSWF window, so the comparator accepts at 0.1 eps
+    // (measured errors against Ewald stay below eps); the smallest
+    // FFT-friendly n_f that meets it is found by bisection (the estimate
+    // falls with n_f)
+    bwin = espm::make_bspline_window(P);
+    best_c1 = 0.0;
+    auto alias_at = [&](int n) { return alias_from_rows(alias_rows(split, n, L, r_c), bwin, n); };
+    if (o.n_f > 0) {
+      best_alias = alias_at(n_f);
+    } else {
+      std::vector<int> ladder;
+      for (int n = n_f; n <= 1024; n = espm::round_grid(n + 1)) ladder.push_back(n);
+      int lo = 0, hi = (int)ladder.size() - 1;
+      if (alias_at(ladder[hi]) > 0.1 * tol) lo = hi;          // even the largest grid does not meet it
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (alias_at(ladder[mid]) <= 0.1 * tol) hi = mid; else lo = mid + 1;
+      }
+      n_f = ladder[lo];
+      best_alias = alias_at(n_f);
     }
-    if (o.n_f > 0 || best_alias <= 0.5 * tol || n_f >= 1024) break;
-    n_f = espm::round_grid(n_f + 1);
+  } else {
+    std::vector<espm::Window> windows;
+    for (double r : ratios) windows.push_back(cached_window(r * c, P));
+    for (int step = 0; step < 8; ++step) {
+      const std::vector<double> rows = alias_rows(split, n_f, L, r_c);
+      best_alias = 1e300;
+      for (size_t i = 0; i < ratios.size(); ++i) {
+        const double a = alias_from_rows(rows, windows[i], n_f);
+        if (a < best_alias) { best_alias = a; best_c1 = ratios[i] * c; }
+      }
+      if (o.n_f > 0 || best_alias <= 0.5 * tol || n_f >= 1024) break;
+      n_f = espm::round_grid(n_f + 1);
+    }
   }
-  const espm::Window win = cached_window(best_c1, P);
+  const espm::Window win = bspline ? bwin : cached_window(best_c1, P);
 
   // cell list and bricks: cell edge w >= r_c / reach. For the one-thread-per-
   // atom local part a reach of 3 (smaller cells) reads fewer non-neighbours;
@@ -444,6 +473,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   info.n_cells = n_c; info.brick_cells = bc; info.tile = T;
   info.cell_reach = reach; info.near_terms = hp.near_nc;
   info.si_degree = (prec == ESP_FP32 ? espk::Deg<float>::si : espk::Deg<double>::si) - 1;
+  info.window = o.window;
   info.near_degree = (prec == ESP_FP32 ? espk::Deg<float>::nr : espk::Deg<double>::nr) - 1;
   return ESP_OK;
 }

@@ -14,6 +14,7 @@ import numpy as np
 
 ESP_OK = 0
 ESP_KERNEL_PSWF, ESP_KERNEL_GAUSS = 0, 1
+ESP_WINDOW_PSWF, ESP_WINDOW_BSPLINE = 0, 1
 ESP_FP32, ESP_FP64 = 0, 1
 ESP_HOST, ESP_DEVICE = 0, 1
 
@@ -44,7 +45,8 @@ class esp_plan_opts(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("prefactor", ctypes.c_double),
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("allow_background", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("timeout_ms", ctypes.c_double),
-        ("cell_reach", ctypes.c_int), ("near_variant", ctypes.c_int), ("reserved", ctypes.c_int * 6),
+        ("cell_reach", ctypes.c_int), ("window", ctypes.c_int), ("near_variant", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -58,7 +60,8 @@ class esp_plan_params(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("n_cells", ctypes.c_int),
         ("cell_reach", ctypes.c_int), ("near_terms", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("tile", ctypes.c_int), ("si_degree", ctypes.c_int),
-        ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
+        ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("window", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
     def as_dict(self) -> dict:

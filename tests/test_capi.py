@@ -77,6 +77,22 @@ def test_planner_gaussian_split(lib):
     assert got["n_f"] == want["n_f"] and abs(got["alpha"] - math.log(1e4)) < 1e-12
 
 
+@pytest.mark.parametrize("L,N,eps,r_c", [
+    (14.4129, 300_000, 1e-4, 1.0),      # water 1e5 molecules
+    (5.0, 300, 1e-3, 1.2),
+    (10.0, 100_000, 1e-5, 1.0),
+])
+def test_planner_bspline_window_matches_oracle(lib, L, N, eps, r_c):
+    got = lib.esp_plan_query(L, N, eps, r_c=r_c, kernel=lib.ESP_KERNEL_GAUSS, window=lib.ESP_WINDOW_BSPLINE)
+    want = oparams.plan_bspline(eps, L, r_c)
+    assert got["window"] == lib.ESP_WINDOW_BSPLINE
+    assert got["P"] == want["P"] == 4 and got["n_f"] == want["n_f"]
+    assert abs(got["alias_estimate"] - want["alias"]) < 1e-6 * want["alias"]
+    assert got["alias_estimate"] <= 0.1 * eps
+    # the B-spline comparator needs a finer grid than the PSWF window
+    assert got["n_f"] > lib.esp_plan_query(L, N, eps, r_c=r_c)["n_f"]
+
+
 def test_planner_fp64_fits_to_rounding(lib):
     got = lib.esp_plan_query(20.0, 1000, 1e-10, r_c=5.0, precision=lib.ESP_FP64)
     # (the near-field correction K reaches ~35 at this shape: 1e-12 is ~3e-14 relative)

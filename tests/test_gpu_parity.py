@@ -45,8 +45,9 @@ def gpu_solve(esp, s, eps, **opts):
 
 def oracle_same(s, eps, info, targets=None, pos=None):
     kind = "pswf" if info["kernel"] == 0 else "gauss"
+    window = "bspline" if info["window"] == 1 else "pswf"
     p = oesp.ESPParams(eps, info["r_c"], info["P"], info["n_f"], c=info["c"], c1=info["c1"],
-                       kind=kind, alpha=info["alpha"] if kind == "gauss" else None)
+                       kind=kind, alpha=info["alpha"] if kind == "gauss" else None, window=window)
     return oesp.esp(s.pos if pos is None else pos, s.q, s.L, p, targets)
 
 
@@ -144,6 +145,31 @@ def test_gaussian_split_variant(esp):
         assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= bound
     ew = ewald.ewald(s.pos, s.q, s.L, acc=1e-14)
     assert metrics.relative_rms_force_error(g["forces"], ew["forces"]) <= 1e-4
+
+
+@pytest.mark.parametrize("P", [4, 5])
+def test_bspline_window_matches_oracle(esp, P):
+    """Gaussian split with the cardinal B-spline window (the comparator's
+    spreading kernel): FP64 and FP32 against the oracle at the same
+    parameters; odd P puts the stencil's knots on half-integers."""
+    s = inputs.spce_water(1000, seed=11)
+    for prec, bound in ((esp.ESP_FP64, 1e-9), (esp.ESP_FP32, FP32_PARITY)):
+        g = gpu_solve(esp, s, 1e-4, r_c=1.0, kernel=esp.ESP_KERNEL_GAUSS, window=esp.ESP_WINDOW_BSPLINE,
+                      P=P, precision=prec)
+        assert g["info"]["window"] == esp.ESP_WINDOW_BSPLINE and g["info"]["P"] == P
+        assert g["info"]["si_fit_error"] < (1e-6 if prec == esp.ESP_FP32 else 1e-12)
+        ref = oracle_same(s, 1e-4, g["info"])
+        assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= bound
+        assert abs(g["energy"] - ref["energy"]) <= 10 * bound * abs(ref["energy"])
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-5])
+def test_bspline_window_within_tolerance_of_ewald(esp, eps):
+    s = inputs.spce_water(1000, seed=11)
+    g = gpu_solve(esp, s, eps, r_c=1.0, kernel=esp.ESP_KERNEL_GAUSS, window=esp.ESP_WINDOW_BSPLINE)
+    ref = ewald.ewald(s.pos, s.q, s.L, acc=1e-14)
+    assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= eps
+    assert abs(g["energy"] - ref["energy"]) <= eps * abs(ref["energy"])
 
 
 def test_empty_system(esp):
