@@ -11,13 +11,15 @@
 //     the cutoff around the box is cut at brick boundaries into contiguous
 //     slab ranges, appended to a per-warp list of ranges (first atom, prefix
 //     count, image offsets);
-//  3. walks the listed candidates with all 32 lanes, kWalk consecutive
-//     candidates per lane and step (a lane finds its range by a binary search
-//     over the prefix counts), moves each into the cluster frame and keeps
-//     those within r_c of the box in a per-warp queue, and
+//  3. walks the listed candidates with all 32 lanes, 32 * kWalk per step,
+//     lane k taking candidates k, k + 32, ... (coalesced loads; each lane
+//     advances a range cursor shared through the warp), moves each into the
+//     cluster frame and keeps those within r_c of the box in a per-warp
+//     queue, and
 //  4. whenever 32 are queued, lane k takes queued candidate k and evaluates it
-//     against every atom of the cluster (masked by 0 < r < r_c); at the end the
-//     per-lane sums are summed over the warp.
+//     against every atom of the cluster; pairs outside 0 < r < r_c are
+//     evaluated at r = r_c with zero charge, so no lane branches. At the end
+//     the per-lane sums are summed over the warp.
 #pragma once
 #include "esp_kernels.cuh"
 
@@ -25,7 +27,7 @@ namespace espk {
 
 constexpr int kClusterAtoms = kClusterAtomsHost;
 constexpr int kClusterWarps = 8;                 // warps per block
-constexpr int kWalk = 4;                         // consecutive candidates per lane and step
+constexpr int kWalk = 4;                         // candidates per lane and step
 constexpr int kClusterQueue = 32 + 32 * kWalk;   // queued candidates per warp
 constexpr int kSegCap = 96;                      // listed ranges per warp
 
@@ -101,6 +103,14 @@ __device__ __forceinline__ float horner_f(const float* c, float y) {
 #pragma unroll
   for (int k = NC - 2; k >= 0; --k) v = fmaf(v, y, c[k]);
   return v;
+}
+
+// 1/sqrt(r2) by the PTX approximate instruction (relative error below
+// 2^-22), subnormal inputs flushed: no slow path for them.
+__device__ __forceinline__ float rsqrt_approx(float r2) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
+  return r;
 }
 
 // Per-warp shared state of the cluster kernel.
@@ -207,21 +217,25 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
         // HALF never queues a cluster atom against itself, so 0 < r2 holds
         // for distinct positions; the full form meets the cluster's own atoms
         const bool in = HALF ? r2 < rc2 : (r2 < rc2 && r2 > 0.f);
-        // masked pairs may give inf or NaN here; the selects below drop them
-        const float rinv = rsqrtf(r2);
-        const float y = fmaf(r2, inv_rc2x2, -1.f);
+        const float r2m = in ? r2 : rc2;
+        const float qj = in ? jd.w : 0.f;
+        // masked pairs (outside r_c, or the far-away padding) are evaluated
+        // at r = r_c with zero charge: every lane runs the same instructions
+        const float rinv = rsqrt_approx(r2m);
+        const float y = fmaf(r2m, inv_rc2x2, -1.f);
         const float h = horner_f<NC>(nc.h, y);
         const float kk = horner_f<NC>(nc.k, y);
-        const float t1 = in ? fmaf(-h, inv_rc, rinv) : 0.f;
-        const float t2 = in ? fmaf(kk, inv_rc3, rinv * rinv * rinv) : 0.f;
-        pu[t] = fmaf(jd.w, t1, pu[t]);
-        const float fs = jd.w * t2;
+        const float t1 = fmaf(-h, inv_rc, rinv);
+        const float t2 = fmaf(kk, inv_rc3, rinv * rinv * rinv);
+        pu[t] = fmaf(qj, t1, pu[t]);
+        const float fs = qj * t2;
         px[t] = fmaf(fs, dx, px[t]);
         py[t] = fmaf(fs, dy, py[t]);
         pz[t] = fmaf(fs, dz, pz[t]);
         if constexpr (HALF) {
-          uj = fmaf(ci.w, t1, uj);
-          const float fsj = ci.w * t2;
+          const float qi = in ? ci.w : 0.f;
+          uj = fmaf(qi, t1, uj);
+          const float fsj = qi * t2;
           fjx = fmaf(fsj, dx, fjx);
           fjy = fmaf(fsj, dy, fjy);
           fjz = fmaf(fsj, dz, fjz);
@@ -358,6 +372,7 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
       // chargeless candidates)
       __syncwarp();
       int base = 0;
+      int scur = 0;
       for (;;) {
         if (qn >= 32 || (last_walk && qn > 0 && base >= total)) {
           const bool has = lane < qn;
@@ -372,24 +387,14 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
           continue;
         }
         if (base >= total) break;
-        const int f0 = base + lane * kWalk;
-        base += 32 * kWalk;
         float4 v[kWalk];
         int jv[kWalk];
-        int s = 0;
-        if (f0 < total) {
-          int lo = 0, hi = nseg - 1;               // last range whose prefix is <= f0
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (W.seg_pre[mid] <= f0) lo = mid; else hi = mid - 1;
-          }
-          s = lo;
-        }
 #pragma unroll
         for (int u = 0; u < kWalk; ++u) {
-          const int f = f0 + u;
+          const int f = base + u * 32 + lane;
           jv[u] = -1;
           v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          int s = scur;
           if (f < total) {
             while (W.seg_pre[s + 1] <= f) ++s;
             const int j = (int)W.seg_pos[s] + (f - W.seg_pre[s]);
@@ -400,7 +405,9 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
             v[u].z += o.z;
             jv[u] = j;
           }
+          scur = __shfl_sync(full, s, 31);
         }
+        base += 32 * kWalk;
 #pragma unroll
         for (int u = 0; u < kWalk; ++u) {
           const float ex = fmax3(0.f, bx_lo - v[u].x, v[u].x - bx_hi);
@@ -451,7 +458,7 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
           const bool in = t != lane && r2 < rc2 && r2 > 0.f;
           const float r2m = in ? r2 : rc2;
           const float qe = in ? ci.w : 0.f;
-          const float rinv = rsqrtf(r2m);
+          const float rinv = rsqrt_approx(r2m);
           const float y = fmaf(r2m, inv_rc2x2, -1.f);
           const float h = horner_f<NC>(nc.h, y);
           const float kk = horner_f<NC>(nc.k, y);
