@@ -429,49 +429,73 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
       if (last_walk) break;
     }
 
-    // ---- 4. warp sums, output
+    // ---- 4. warp sums, output. The 32 per-lane sums (4 quantities x 8
+    // atoms) are reduced over the warp by halving exchanges: at offset o a
+    // lane keeps one half of its values, sends the other to lane ^ o and adds
+    // what it receives; afterwards lane k holds the warp sum of value k =
+    // 8 * quantity + atom.
     __syncwarp();
-    float ou = 0.f, ofx = 0.f, ofy = 0.f, ofz = 0.f;
+    float v[4 * kClusterAtoms];
 #pragma unroll
     for (int t = 0; t < kClusterAtoms; ++t) {
-      if (t < m) {
-        float a = pu[t], b = px[t], c = py[t], d = pz[t];
+      v[t] = pu[t];
+      v[kClusterAtoms + t] = px[t];
+      v[2 * kClusterAtoms + t] = py[t];
+      v[3 * kClusterAtoms + t] = pz[t];
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(full, a, o);
-          b += __shfl_xor_sync(full, b, o);
-          c += __shfl_xor_sync(full, c, o);
-          d += __shfl_xor_sync(full, d, o);
-        }
-        if (lane == t) { ou = a; ofx = b; ofy = c; ofz = d; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < o; ++k) {
+        const float send = up ? v[k] : v[k + o];
+        const float keep = up ? v[k + o] : v[k];
+        v[k] = keep + __shfl_xor_sync(full, send, o);
       }
     }
     if constexpr (HALF) {
-      // pairs inside the cluster (same image): each lane sums its own atom's
-      // pairs with the others
-      if (mine) {
+      // pairs inside the cluster (same image), every ordered pair (a, b):
+      // lane k takes atom a = k % 8 against b = k / 8 and k / 8 + 4
+      const int a_at = lane & (kClusterAtoms - 1);
+      const float4 ra = W.idata[a_at];
+      float su = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
-        for (int t = 0; t < kClusterAtoms; ++t) {
-          const float4 ci = W.idata[t];
-          const float dx = ri.x - ci.x, dy = ri.y - ci.y, dz = ri.z - ci.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const bool in = t != lane && r2 < rc2 && r2 > 0.f;
-          const float r2m = in ? r2 : rc2;
-          const float qe = in ? ci.w : 0.f;
-          const float rinv = rsqrt_approx(r2m);
-          const float y = fmaf(r2m, inv_rc2x2, -1.f);
-          const float h = horner_f<NC>(nc.h, y);
-          const float kk = horner_f<NC>(nc.k, y);
-          ou = fmaf(qe, fmaf(-h, inv_rc, rinv), ou);
-          const float fs = qe * fmaf(kk, inv_rc3, rinv * rinv * rinv);
-          ofx = fmaf(fs, dx, ofx);
-          ofy = fmaf(fs, dy, ofy);
-          ofz = fmaf(fs, dz, ofz);
-        }
-        atomicAdd(nearres + my_idx, make_float4(ou * k4, ri.w * ofx * k4, ri.w * ofy * k4, ri.w * ofz * k4));
+      for (int hb = 0; hb < 2; ++hb) {
+        const int b_at = (lane >> 3) + 4 * hb;
+        const float4 rb = W.idata[b_at];
+        const float dx = ra.x - rb.x, dy = ra.y - rb.y, dz = ra.z - rb.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool in = a_at != b_at && r2 < rc2 && r2 > 0.f;
+        const float r2m = in ? r2 : rc2;
+        const float qe = in ? rb.w : 0.f;
+        const float rinv = rsqrt_approx(r2m);
+        const float y = fmaf(r2m, inv_rc2x2, -1.f);
+        const float h = horner_f<NC>(nc.h, y);
+        const float kk = horner_f<NC>(nc.k, y);
+        su = fmaf(qe, fmaf(-h, inv_rc, rinv), su);
+        const float fs = qe * fmaf(kk, inv_rc3, rinv * rinv * rinv);
+        sx = fmaf(fs, dx, sx);
+        sy = fmaf(fs, dy, sy);
+        sz = fmaf(fs, dz, sz);
       }
-    } else if (mine) {
-      nearres[my_idx] = make_float4(ou * k4, ri.w * ofx * k4, ri.w * ofy * k4, ri.w * ofz * k4);
+#pragma unroll
+      for (int o = 8; o < 32; o <<= 1) {
+        su += __shfl_xor_sync(full, su, o);
+        sx += __shfl_xor_sync(full, sx, o);
+        sy += __shfl_xor_sync(full, sy, o);
+        sz += __shfl_xor_sync(full, sz, o);
+      }
+      v[0] += lane < kClusterAtoms ? su : (lane < 2 * kClusterAtoms ? sx : (lane < 3 * kClusterAtoms ? sy : sz));
+    }
+    // lane t < 8 gathers atom t's four sums from lanes t, t + 8, t + 16, t + 24
+    const float ou = v[0];
+    const float ofx = __shfl_sync(full, v[0], (lane + kClusterAtoms) & 31);
+    const float ofy = __shfl_sync(full, v[0], (lane + 2 * kClusterAtoms) & 31);
+    const float ofz = __shfl_sync(full, v[0], (lane + 3 * kClusterAtoms) & 31);
+    if (mine) {
+      const float4 out = make_float4(ou * k4, ri.w * ofx * k4, ri.w * ofy * k4, ri.w * ofz * k4);
+      if constexpr (HALF) atomicAdd(nearres + my_idx, out);
+      else nearres[my_idx] = out;
     }
     __syncwarp();
   }
