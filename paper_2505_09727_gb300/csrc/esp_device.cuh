@@ -75,11 +75,15 @@ struct SysDesc {
   double r_c, rc2, inv_rc, inv_rc2, inv_rc3;
   double w;          // cell edge L / n_c
   double fix_scale;  // L / 2^32
+  double to_fixed;   // 2^32 / L
+  double w32;        // w / 2^32
   double self_coef;  // chi(0) / (4 pi r_c)
   double bg_shift;   // -(Q/V) (r_c^2/2) int_0^1 x^2 chi
   double prefactor;
   // FP32 copies for the FP32 local part
   float wf, r_cf, rc2f, inv_rcf, inv_rc2x2f, inv_rc3f, inv_bcf;
+  float w32f;                       // wf / 2^32 (exact)
+  float self_coef_f, bg_shift_f, prefactor_f;
 };
 
 // ------------------------------------------------------------ coordinates

@@ -137,7 +137,7 @@ struct esp_plan_s {
   int2* d_catoms = nullptr;
 
   cudaStream_t st = nullptr, st2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_scat = nullptr;
   cudaEvent_t tev[14] = {};
   float phase_ms[kPhases] = {};
   bool timed_valid = false;      // events of the last compute were recorded
@@ -189,6 +189,7 @@ void release(esp_plan_s* p) {
   }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_scat) cudaEventDestroy(p->ev_scat);
   for (auto& e : p->tev) if (e) cudaEventDestroy(e);
   if (p->st2) cudaStreamDestroy(p->st2);
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
@@ -427,6 +428,7 @@ esp_status do_set_charges(esp_plan_s* p, const void* q, bool is_double, int wher
     double bg_shift;
     espe::charge_constants(p->hps[s], Qs[s], Q2s[s], &consts[2 * s], &consts[2 * s + 1], &bg_shift);
     p->descs[s].bg_shift = bg_shift;
+    p->descs[s].bg_shift_f = (float)bg_shift;
   }
   ESP_CU(cudaMemcpyAsync(p->d_qstage, hq.data(), N * sizeof(double), cudaMemcpyHostToDevice, p->st));
   ESP_CU((cudaError_t)L::convert_charges(p->d_qstage, true, (real*)p->d_q, N, p->st));
@@ -479,12 +481,10 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   cudaStream_t st = p->st, st2 = p->st2;
 
   rec(p, 2, st);
-  // A1b: scatter into cell order
-  ESP_CU(L::scatter(p->d_desc, p->d_chunks, p->n_chunks, p->d_coord, p->d_key, p->d_rank, p->d_start,
-                    (const real*)p->d_q, p->d_atoms, p->d_rel, p->d_perm, st));
-  rec(p, 12, st);
   // fork: local part on the second stream (on the main stream when timing
-  // mode 2 serialises the phases so each kernel is timed alone)
+  // mode 2 serialises the phases so each kernel is timed alone). Its cluster
+  // lists need only the cell offsets of the sort, so they are built while the
+  // main stream scatters the atoms; the pair kernel waits for the scatter.
   const bool serial = p->timing_mode == 2;
   if (serial) st2 = st;
   else {
@@ -496,12 +496,22 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   const espk::SICoef<real>& si = *reinterpret_cast<const espk::SICoef<real>*>(
       sizeof(real) == 4 ? (const void*)&hp.si32 : (const void*)&hp.si64);
   if (hp.near_clusters) {
-    // cluster lists (timed with the bin sort), then the pair kernel alone
-    // between the local-part events
+    // cluster lists (timed with the bin sort)
     rec(p, 13, st2);
     ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
                             p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
                             hp.near_half, p->N, 2, p->d_err, st2));
+  }
+  // A1b: scatter into cell order
+  ESP_CU(L::scatter(p->d_desc, p->d_chunks, p->n_chunks, p->d_coord, p->d_key, p->d_rank, p->d_start,
+                    (const real*)p->d_q, p->d_atoms, p->d_rel, p->d_perm, st));
+  rec(p, 12, st);
+  if (!serial) {
+    ESP_CU(cudaEventRecord(p->ev_scat, st));
+    ESP_CU(cudaStreamWaitEvent(st2, p->ev_scat, 0));
+  }
+  if (hp.near_clusters) {
+    // the pair kernel alone between the local-part events
     rec(p, 9, st2);
     ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
                             p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
@@ -598,7 +608,8 @@ esp_status create_streams(esp_plan_s* p, const esp_plan_opts& o) {
   }
   if (cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_scat, cudaEventDisableTiming) != cudaSuccess)
     return fail(ESP_ERR_CUDA, "stream/event creation failed");
   for (auto& e : p->tev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(ESP_ERR_CUDA, "event creation failed");
@@ -790,8 +801,8 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
     }
     return t;
   };
-  p->phase_ms[0] = el(0, 1) + el(2, 12);  // ingest + scan, scatter
-  if (p->hps[0].near_clusters) p->phase_ms[0] += el(13, 9);   // cluster lists
+  // ingest + scan, then scatter and (concurrently) the cluster lists
+  p->phase_ms[0] = el(0, 1) + (p->hps[0].near_clusters ? el(2, 9) : el(2, 12));
   p->phase_ms[1] = el(3, 4);              // spread (with grid clear)
   p->phase_ms[2] = el(4, 5);              // R2C FFT
   p->phase_ms[3] = el(5, 6);              // scale + energy

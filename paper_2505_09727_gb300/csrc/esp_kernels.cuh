@@ -146,12 +146,19 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
     uint32_t u[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double f = p[a] / S.L;
-      if (!(f >= 0.0 && f < 1.0)) {
+      // u = floor(x 2^32 / L) mod 2^32: one FP64 product rounded down to a
+      // 64-bit integer whose low word is the periodic wrap (FP64 division
+      // and floor are slow on this GPU); only |x| beyond 2^30 L wraps in FP64
+      const double t = p[a] * S.to_fixed;
+      long long v;
+      if (fabs(t) < 4.0e18) {
+        v = __double2ll_rd(t);
+      } else {
+        double f = p[a] * S.inv_L;
         f -= floor(f);
-        if (!(f < 1.0) || f < 0.0) f = 0.0;
+        v = (long long)(f * 4294967296.0);
       }
-      u[a] = (uint32_t)(f * 4294967296.0);
+      u[a] = (uint32_t)(unsigned long long)v;
       c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
     }
     // slab: fractional position inside the z cell, in kSub parts
@@ -298,13 +305,15 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_add(
 // of its brick (z: the cells of a brick column share one z frame).
 __device__ inline float cell_relative(const SysDesc& S, uint32_t u) {
   const uint32_t frac = (uint32_t)((uint64_t)u * (uint64_t)S.n_c);   // fraction of the cell
-  return (float)((double)frac * 2.3283064365386962890625e-10 * S.w);
+  return (float)frac * S.w32f;                                        // < w: two FP32 roundings
 }
 __device__ inline float brick_relative(const SysDesc& S, uint32_t u) {
   const uint64_t t = (uint64_t)u * (uint64_t)S.n_c;                   // 32.32 cell coordinate
-  const int c = (int)(t >> 32);
-  const double in_brick = (double)(c % S.bc) + (double)(uint32_t)t * 2.3283064365386962890625e-10;
-  return (float)(in_brick * S.w);
+  const uint32_t c = (uint32_t)(t >> 32);
+  // position in the brick as an exact 35-bit fixed-point integer, one FP64
+  // product and one rounding to FP32 (z spans several cells)
+  const uint64_t in_brick = ((uint64_t)(c % (uint32_t)S.bc) << 32) | (uint32_t)t;
+  return (float)((double)in_brick * S.w32);
 }
 __device__ inline double brick_relative(const SysDesc&, double x) { return x; }
 // FP64 mode keeps absolute wrapped coordinates in the pair records, so pair
@@ -857,6 +866,16 @@ __global__ void __launch_bounds__(kChunk) k_near(
 
 // A8: per-atom totals in the caller's order and energy partials.
 // partials layout: [near chunk partials][gather chunk partials].
+// (hi, lo) += (bh, bl) with the rounding error of hi + bh kept in lo
+// (Knuth's TwoSum; exact for FP32 round-to-nearest without reassociation).
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (bh - bp);
+  hi = s;
+  lo = lo + bl + err;
+}
+
 template <typename real, typename Out>
 __global__ void __launch_bounds__(kChunk) k_finalize(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
@@ -867,6 +886,50 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
   const int2 ch = chunks[blockIdx.x];
   const SysDesc& S = sys[ch.x];
   const int local = ch.y + threadIdx.x;
+  if constexpr (sizeof(real) == 4) {
+    // FP32 mode: the far and near parts are FP32 sums, so their combination
+    // stays in FP32 (FP64 arithmetic is scarce on this GPU); the energy
+    // terms are summed without loss over the warp as FP32 (hi, lo) pairs
+    // and over the block in FP64
+    float en_hi = 0.f, en_lo = 0.f, eg_hi = 0.f, eg_lo = 0.f;
+    if (local < S.n_atoms) {
+      const long long i = S.atom0 + local;
+      const float q = atom_q(atoms[i]);
+      const typename Types<real>::res f = far[i];
+      const typename Types<real>::res nr = nearres[i];
+      const uint32_t o = perm[i];
+      const float pre = S.prefactor_f;
+      if (forces) {
+        forces[3ll * o + 0] = (Out)(pre * fmaf(-q, f.y, nr.y));
+        forces[3ll * o + 1] = (Out)(pre * fmaf(-q, f.z, nr.z));
+        forces[3ll * o + 2] = (Out)(pre * fmaf(-q, f.w, nr.w));
+      }
+      if (pot) pot[o] = (Out)(pre * (fmaf(-q, S.self_coef_f, f.x + nr.x) + S.bg_shift_f));
+      en_hi = 0.5f * q * nr.x;
+      eg_hi = 0.5f * q * f.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      two_sum_add(en_hi, en_lo, __shfl_xor_sync(0xffffffffu, en_hi, o), __shfl_xor_sync(0xffffffffu, en_lo, o));
+      two_sum_add(eg_hi, eg_lo, __shfl_xor_sync(0xffffffffu, eg_hi, o), __shfl_xor_sync(0xffffffffu, eg_lo, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+      red[wid] = (double)en_hi + (double)en_lo;
+      red[16 + wid] = (double)eg_hi + (double)eg_lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        a += red[w];
+        b += red[16 + w];
+      }
+      partials[blockIdx.x] = a;
+      partials[n_chunks + blockIdx.x] = b;
+    }
+    return;
+  }
   double en = 0.0, eg = 0.0;
   if (local < S.n_atoms) {
     const long long i = S.atom0 + local;

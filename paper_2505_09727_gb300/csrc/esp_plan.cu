@@ -416,7 +416,10 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.inv_rc2 = d.inv_rc * d.inv_rc; d.inv_rc3 = d.inv_rc2 * d.inv_rc;
   d.w = L / n_c;
   d.fix_scale = L / 4294967296.0;
+  d.to_fixed = 4294967296.0 / L;
+  d.w32 = d.w / 4294967296.0;
   d.wf = (float)d.w;
+  d.w32f = d.wf * 2.3283064365386962890625e-10f;
   d.r_cf = (float)r_c;
   d.rc2f = (float)d.rc2;
   d.inv_rcf = (float)d.inv_rc;
@@ -428,6 +431,9 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.self_coef = hp.self_unit;
   d.bg_shift = 0.0;
   d.prefactor = o.prefactor > 0 ? o.prefactor : 1.0;
+  d.self_coef_f = (float)d.self_coef;
+  d.bg_shift_f = 0.0f;
+  d.prefactor_f = (float)d.prefactor;
 
   // polynomial tables
   const SiTables& sit = si_tables(win, P);

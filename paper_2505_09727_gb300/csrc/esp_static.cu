@@ -100,6 +100,7 @@ esp_status run_local(const espe::HostPlan& hp, unsigned char* scratch, const dou
   double consts[2], bg_shift;
   espe::charge_constants(hp, Q, Q2, &consts[0], &consts[1], &bg_shift);
   d.bg_shift = bg_shift;
+  d.bg_shift_f = (float)bg_shift;
   std::vector<int2> chunks(n_chunks);
   for (int k = 0; k < n_chunks; ++k) chunks[k] = make_int2(0, k * espk::kChunk);
   int chunk_first[2] = {0, n_chunks};
