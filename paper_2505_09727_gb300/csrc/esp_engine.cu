@@ -147,6 +147,13 @@ struct esp_plan_s {
   int direct_runs = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+
+  // single plans: the compute captured as a CUDA graph for its output
+  // pointers (re-captured when they change; given up after kMaxRecaptures)
+  int c_direct_runs = 0, c_captures = 0;
+  cudaGraph_t cgraph = nullptr;
+  cudaGraphExec_t cgexec = nullptr;
+  const void* ckey[4] = {};
 };
 
 struct esp_batch_s {
@@ -181,6 +188,8 @@ void release(esp_plan_s* p) {
   if (p->st2) cudaStreamSynchronize(p->st2);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cgexec) cudaGraphExecDestroy(p->cgexec);
+  if (p->cgraph) cudaGraphDestroy(p->cgraph);
   for (void* a : p->allocs) cudaFree(a);
   p->allocs.clear();
   for (Bucket& b : p->buckets) {
@@ -579,6 +588,47 @@ esp_status finish_host(esp_plan_s* p, double* energy, void* forces, void* potent
   return check_err_flag(p);
 }
 
+constexpr int kMaxRecaptures = 4;
+
+// One compute on the plan's streams: directly while timing (the phase events
+// are recorded then), for the first run, inside a caller's own capture, or
+// once the output pointers have changed too often; otherwise as a replay of
+// the captured graph for these output pointers (no launch gaps between the
+// dependent kernels).
+template <typename real>
+esp_status compute_enqueue(esp_plan_s* p, void* outF, void* outU, bool out_double, double* outE) {
+  const void* key[4] = {outF, outU, out_double ? (const void*)1 : nullptr, outE};
+  const bool same = std::equal(key, key + 4, p->ckey);
+  if (p->cgexec && same && !p->timing) {
+    ESP_CU(cudaGraphLaunch(p->cgexec, p->st));
+    return ESP_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ESP_CU(cudaStreamIsCapturing(p->st, &cs));
+  if (p->timing || p->c_direct_runs == 0 || cs != cudaStreamCaptureStatusNone || p->c_captures >= kMaxRecaptures) {
+    ++p->c_direct_runs;
+    return launch_compute<real>(p, outF, outU, out_double, outE);
+  }
+  cudaGraph_t graph = nullptr;
+  ESP_CU(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+  const esp_status s = launch_compute<real>(p, outF, outU, out_double, outE);
+  const cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+  if (s != ESP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(ESP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (p->cgexec) cudaGraphExecDestroy(p->cgexec);
+  if (p->cgraph) cudaGraphDestroy(p->cgraph);
+  p->cgexec = nullptr;
+  p->cgraph = graph;
+  ++p->c_captures;
+  ESP_CU(cudaGraphInstantiate(&p->cgexec, graph, 0));
+  std::copy(key, key + 4, p->ckey);
+  ESP_CU(cudaGraphLaunch(p->cgexec, p->st));
+  return ESP_OK;
+}
+
 template <typename real>
 esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potential, bool out_double,
                       int where) {
@@ -592,7 +642,7 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
     outU = potential ? p->d_outU : nullptr;
     outE = nullptr;
   }
-  ESP_TRY(launch_compute<real>(p, outF, outU, out_double, outE));
+  ESP_TRY(compute_enqueue<real>(p, outF, outU, out_double, outE));
   if (where == ESP_HOST) ESP_TRY(finish_host(p, energy, forces, potential, out_double));
   p->timed_valid = p->timing;
   return ESP_OK;
@@ -845,7 +895,7 @@ esp_status enqueue_step(esp_plan_s* p, const double* xyz, double* forces, double
   ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, N * 3 * sizeof(double), cudaMemcpyHostToDevice, p->st));
   ESP_TRY(launch_sort<real>(p, p->d_pos, true));
   p->have_pos = true;
-  ESP_TRY(launch_compute<real>(p, p->d_outF, p->d_outU, true, nullptr));
+  ESP_TRY(compute_enqueue<real>(p, p->d_outF, p->d_outU, true, nullptr));
   ESP_CU(cudaMemcpyAsync(forces, p->d_outF, N * 3 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
   ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * sizeof(double), cudaMemcpyDeviceToHost, p->st));
   ESP_CU(cudaMemcpyAsync(energy, p->d_eout, sizeof(double), cudaMemcpyDeviceToHost, p->st));

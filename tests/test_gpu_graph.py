@@ -1,0 +1,73 @@
+"""Graph replay of a single plan's compute.
+
+After its first direct run, a plan replays its compute as a captured CUDA
+graph for the same output pointers and re-captures when they change. Every
+replayed result must equal a fresh plan's direct result for the same
+positions (up to the FP32 atomic summation order), with new positions each
+step, host outputs, and device outputs alternating between two buffers.
+"""
+import numpy as np
+import pytest
+
+from paper_2505_09727_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP32_PARITY = 5e-6
+
+
+@pytest.fixture(scope="module")
+def esp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2505_09727_gb300 import _build, esp as binding
+    _build.build()
+    return binding
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+def fresh(esp, s, pos):
+    with esp.Plan(s.L, s.n, 1e-4, r_c=1.0) as p:
+        p.set_charges(s.q)
+        p.set_positions(pos)
+        return p.compute()
+
+
+def test_host_outputs_replayed(esp):
+    s = inputs.spce_water(2000, seed=41)
+    with esp.Plan(s.L, s.n, 1e-4, r_c=1.0) as p:
+        p.set_charges(s.q)
+        for k in range(5):                       # direct, capture, replays
+            pos = inputs.perturb(s, 0.02, seed=400 + k).pos
+            p.set_positions(pos)
+            e, f, u = p.compute()
+            e0, f0, u0 = fresh(esp, s, pos)
+            assert rel_rms(f, f0) <= FP32_PARITY
+            assert rel_rms(u, u0) <= FP32_PARITY
+            assert abs(e - e0) <= FP32_PARITY * abs(e0)
+
+
+def test_device_outputs_alternating_buffers(esp):
+    import torch
+    dev = torch.device("cuda:0")
+    s = inputs.electrolyte(6000, seed=42)
+    h = esp.esp_plan(s.L, s.n, 1e-4, r_c=1.0)
+    try:
+        esp.esp_set_charges(h, torch.tensor(s.q, device=dev))
+        bufs = [(torch.zeros(1, dtype=torch.float64, device=dev), torch.zeros((s.n, 3), dtype=torch.float64, device=dev),
+                 torch.zeros(s.n, dtype=torch.float64, device=dev)) for _ in range(2)]
+        for k in range(7):                       # keys change every step: re-captures, then direct runs
+            pos = inputs.perturb(s, 0.02, seed=500 + k).pos
+            e, f, u = bufs[k % 2]
+            esp.esp_set_positions(h, torch.tensor(pos, device=dev))
+            esp.esp_compute(h, e, f, u)
+            torch.cuda.synchronize()
+            e0, f0, u0 = fresh(esp, s, pos)
+            assert rel_rms(f.cpu().numpy(), f0) <= FP32_PARITY
+            assert rel_rms(u.cpu().numpy(), u0) <= FP32_PARITY
+            assert abs(float(e.cpu()[0]) - e0) <= FP32_PARITY * abs(e0)
+    finally:
+        esp.esp_destroy(h)
