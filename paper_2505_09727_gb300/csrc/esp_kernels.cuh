@@ -2,6 +2,8 @@
 // Instantiated for FP32 (production) in esp_kern_f32.cu and FP64 (plain mode)
 // in esp_kern_f64.cu.
 #pragma once
+#include <climits>
+
 #include "esp_device.cuh"
 
 namespace espk {
@@ -133,7 +135,8 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     p[a] = (double)xyz[3 * i + a];
-    finite &= isfinite(p[a]);
+    // finite = exponent field not all ones (integer test, no FP64 compare)
+    finite &= ((__double_as_longlong(p[a]) >> 52) & 0x7ff) != 0x7ff;
   }
   if (!finite) {
     atomicOr(err, 1);
@@ -148,12 +151,9 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
     for (int a = 0; a < 3; ++a) {
       // u = floor(x 2^32 / L) mod 2^32: one FP64 product rounded down to a
       // 64-bit integer whose low word is the periodic wrap (FP64 division
-      // and floor are slow on this GPU); only |x| beyond 2^30 L wraps in FP64
-      const double t = p[a] * S.to_fixed;
-      long long v;
-      if (fabs(t) < 4.0e18) {
-        v = __double2ll_rd(t);
-      } else {
+      // and floor are slow on this GPU); only |x| beyond 2^31 L wraps in FP64
+      long long v = __double2ll_rd(p[a] * S.to_fixed);
+      if (v == LLONG_MAX || v == LLONG_MIN) {   // saturated: |x| beyond 2^31 L
         double f = p[a] * S.inv_L;
         f -= floor(f);
         v = (long long)(f * 4294967296.0);
@@ -965,22 +965,26 @@ __device__ inline void neumaier_add(double& s, double& c, double v) {
 }
 
 // Per-system energy: E = prefactor (E_fourier + E_near + E_self + E_bg).
-// One block per system. out[3 s + 0] = E, [1] = E_fourier, [2] = E_gather.
-static __global__ void __launch_bounds__(256) k_energy(
+// One block of 1024 threads per system. out[3 s + 0] = E, [1] = E_fourier, [2] = E_gather.
+static __global__ void __launch_bounds__(1024) k_energy(
     const SysDesc* __restrict__ sys, const double* __restrict__ fourier, int n_fourier_blocks,
     const double* __restrict__ partials, int n_chunks, const int* __restrict__ chunk_first,
     const double* __restrict__ consts, double* __restrict__ out, double* __restrict__ user_energy) {
   __shared__ double red[32];
   const int s = blockIdx.x;
-  double vs[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+  // a few plain FP64 additions per thread, then a pairwise tree over the
+  // block: the rounding error stays near log2(terms) ulp, and the FP64 work
+  // of this single block is kept small (FP64 is scarce on this GPU);
+  // the four parts are combined with compensation below
+  double vs[3] = {0, 0, 0};
   for (int j = threadIdx.x; j < n_fourier_blocks; j += blockDim.x)
-    neumaier_add(vs[0], vc[0], fourier[(long long)s * n_fourier_blocks + j]);
+    vs[0] += fourier[(long long)s * n_fourier_blocks + j];
   for (int j = chunk_first[s] + threadIdx.x; j < chunk_first[s + 1]; j += blockDim.x) {
-    neumaier_add(vs[1], vc[1], partials[j]);
-    neumaier_add(vs[2], vc[2], partials[n_chunks + j]);
+    vs[1] += partials[j];
+    vs[2] += partials[n_chunks + j];
   }
   double tot[3];
-  for (int a = 0; a < 3; ++a) tot[a] = block_sum(vs[a] + vc[a], red);
+  for (int a = 0; a < 3; ++a) tot[a] = block_sum(vs[a], red);
   if (threadIdx.x == 0) {
     const double pre = sys[s].prefactor;
     // consts[2 s] = E_self, consts[2 s + 1] = E_bg (host FP64)

@@ -21,79 +21,14 @@
 //     evaluated at r = r_c with zero charge, so no lane branches. At the end
 //     the per-lane sums are summed over the warp.
 #pragma once
-#include "esp_kernels.cuh"
+#include "esp_cluster_list.cuh"
 
 namespace espk {
 
-constexpr int kClusterAtoms = kClusterAtomsHost;
 constexpr int kClusterWarps = 8;                 // warps per block
 constexpr int kWalk = 4;                         // candidates per lane and step
 constexpr int kClusterQueue = 32 + 32 * kWalk;   // queued candidates per warp
 constexpr int kSegCap = 96;                      // listed ranges per warp
-
-__device__ __forceinline__ int system_of_column(const SysDesc* __restrict__ sys, int nsys, long long g) {
-  int lo = 0, hi = nsys - 1;                      // last system with col0 <= g
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (sys[mid].col0 <= g) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// One warp per pooled column (lanes over the column's bricks).
-// Cluster count per column: ceil(atoms in the column / kClusterAtoms).
-static __global__ void __launch_bounds__(256) k_col_clusters(
-    const SysDesc* __restrict__ sys, int nsys, long long n_cols, const uint32_t* __restrict__ start,
-    uint32_t* __restrict__ ccount) {
-  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (g >= n_cols) return;
-  const SysDesc& S = sys[system_of_column(sys, nsys, g)];
-  const int c = (int)(g - S.col0);
-  const int cx = c / S.n_c, cy = c - cx * S.n_c;
-  const uint32_t* st = start + S.cell0;
-  uint32_t total = 0;
-  for (int bz = lane; bz < S.nb; bz += 32) {
-    const long long k0 = cell_key(S, cx, cy, bz * S.bc);
-    total += st[(k0 + S.bc) * kSub] - st[k0 * kSub];
-  }
-  total = __reduce_add_sync(0xffffffffu, total);
-  if (lane == 0) ccount[g] = (total + kClusterAtoms - 1) / kClusterAtoms;
-}
-
-// Cluster list: cmap[q] = (system, column) and catoms[q][t] = (atom index,
-// brick z index) of the t-th atom of cluster q = cstart[column] + k
-// (index -1 in the empty slots of a column's last cluster).
-static __global__ void __launch_bounds__(256) k_cluster_expand(
-    const SysDesc* __restrict__ sys, int nsys, long long n_cols, const uint32_t* __restrict__ ccount,
-    const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ start, int2* __restrict__ cmap,
-    int2* __restrict__ catoms, long long capacity, int* __restrict__ err) {
-  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (g >= n_cols) return;
-  const int s = system_of_column(sys, nsys, g);
-  const SysDesc& S = sys[s];
-  const int c = (int)(g - S.col0);
-  const int cx = c / S.n_c, cy = c - cx * S.n_c;
-  const uint32_t n = ccount[g], b = cstart[g];
-  if ((long long)b + n > capacity) {
-    if (lane == 0) atomicOr(err, 4);
-    return;
-  }
-  for (uint32_t k = lane; k < n; k += 32) cmap[b + k] = make_int2(s, c);
-  const uint32_t* st = start + S.cell0;
-  const long long slots = (long long)n * kClusterAtoms;
-  int2* out = catoms + (long long)b * kClusterAtoms;
-  long long p = 0;                                  // position of the brick's first atom
-  for (int bz = 0; bz < S.nb; ++bz) {
-    const long long k0 = cell_key(S, cx, cy, bz * S.bc);
-    const uint32_t j0 = st[k0 * kSub], j1 = st[(k0 + S.bc) * kSub];
-    for (uint32_t j = j0 + lane; j < j1; j += 32)
-      if (p + (j - j0) < slots) out[p + (j - j0)] = make_int2((int)j, bz);
-    p += j1 - j0;
-  }
-  for (long long q = p + lane; q < slots; q += 32) out[q] = make_int2(-1, 0);
-}
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) { return fmaxf(fmaxf(a, b), c); }
 
