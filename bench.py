@@ -189,6 +189,51 @@ def roofline(phases: dict, info: dict, n_atoms: int, L: float, clocks, n_steps: 
             "algorithmic_per_launch": work, "avg_launch_ms": phases[kernel]}
 
 
+def phase_rooflines(phases: dict, info: dict, n_atoms: int, L: float, clocks) -> dict:
+    """Every phase (serialised CUDA-event time) against each resource: its
+    algorithmic DRAM bytes over the measured HBM copy bandwidth and, for the
+    arithmetic phases, its FP32 flops over the derived FP32 peak.
+
+    Bytes per step: sort 24 B/atom FP64 positions in + 36 B/atom sorted
+    records, pair records and permutation out; spread 16 B/atom + 4 B per
+    grid point; R2C and C2R 4 B per grid point + 8 B per mode; scale 16 B per
+    mode; gather 32 B/atom + 4 B per grid point; local part 32 B/atom;
+    finalize 52 B/atom in + 32 B/atom out. Flops per atom: spread 2 P^3
+    (weighted adds) + 6 P (SI_DEGREE + 1) (1-D weights); gather 8 P^3 + 12 P
+    (SI_DEGREE + 1) (potential, three derivatives); local part as in
+    roofline()."""
+    rho = n_atoms / L ** 3
+    pairs = 0.5 * n_atoms * 4.0 / 3.0 * math.pi * info["r_c"] ** 3 * rho
+    n_f, P, deg = info["n_f"], info["P"], info.get("si_degree", 9)
+    grid = n_f ** 3
+    modes = n_f * n_f * (n_f // 2 + 1)
+    peaks, source = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1492.0)
+    fp32 = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    work = {
+        "ingest_sort": (60.0 * n_atoms, 0.0),
+        "spread": (16.0 * n_atoms + 4.0 * grid, n_atoms * (2.0 * P ** 3 + 6.0 * P * (deg + 1))),
+        "fft_r2c": (4.0 * grid + 8.0 * modes, 0.0),
+        "scale": (16.0 * modes, 0.0),
+        "fft_c2r": (4.0 * grid + 8.0 * modes, 0.0),
+        "gather": (32.0 * n_atoms + 4.0 * grid, n_atoms * (8.0 * P ** 3 + 12.0 * P * (deg + 1))),
+        "near": (32.0 * n_atoms, pairs * NEAR_FLOPS_PER_PAIR),
+        "finalize": (84.0 * n_atoms, 0.0),
+    }
+    out = {"hbm_peak_gbs": hbm, "hbm_peak_source": source, "fp32_peak_tflops": fp32}
+    for k, (b, f) in work.items():
+        t = phases.get(k, 0.0) * 1e-3
+        if t <= 0:
+            continue
+        row = {"ms": round(phases[k], 5), "hbm_gbs": round(b / t / 1e9, 2), "hbm_frac": round(b / t / 1e9 / hbm, 5)}
+        if f:
+            row["fp32_tflops"] = round(f / t / 1e12, 3)
+            row["fp32_frac"] = round(f / t / 1e12 / fp32, 5)
+        out[k] = row
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, world, rank, local):
     import torch
@@ -585,6 +630,7 @@ def main():
         d["grid_points_ratio"] = (d["n_f"] / r["info"]["n_f"]) ** 3
         d["esp_speedup"] = value / world / d["value"]
     line["roofline"] = roofline(r["phases"], r["info"], N, r["L"], r["clocks"], args.steps)
+    line["phase_roofline"] = phase_rooflines(r["phases"], r["info"], N, r["L"], r["clocks"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.molecules)
         line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -61,6 +61,7 @@ struct SysDesc {
   int bc;         // cells per brick edge (n_c % bc == 0)
   int nb;         // bricks per axis (n_c / bc)
   int T;          // shared tile edge in grid points
+  int tpy, tpz;   // tile row and plane pitch in elements (tile_pitches)
   int n_atoms;
   int gsize;      // entries of the radial table G (3 (n_f/2)^2 + 1)
   int reach;      // neighbour cells per side in the local part (edge w >= r_c / reach)
@@ -85,6 +86,18 @@ struct SysDesc {
   float w32f;                       // wf / 2^32 (exact)
   float self_coef_f, bg_shift_f, prefactor_f;
 };
+
+// Padded pitches of a spread/gather tile of edge T (elements): rows of odd
+// length, and a plane pitch equal to P rows modulo 32, so that the P x P rows
+// of one stencil (lane r = P z + y) start on banks r * py mod 32, all
+// distinct. Unpadded, a tile of edge 16 put every row of a stencil on two
+// banks.
+__host__ __device__ inline void tile_pitches(int T, int P, int& py, int& pz) {
+  py = T | 1;
+  pz = py * T;
+  const int want = (P * py) & 31;
+  while ((pz & 31) != want) ++pz;
+}
 
 // ------------------------------------------------------------ coordinates
 // FP32 mode stores coordinates as 32-bit fixed-point fractions of L: the grid

@@ -290,7 +290,7 @@ void layout(esp_plan_s* p, std::vector<int2>& chunks, std::vector<int>& chunk_fi
     cell0 += hp.n_keys;
     tab0 += (long long)(hp.G.size() + hp.W.size());
     col0 += (long long)d.n_c * d.n_c;
-    p->smem = std::max(p->smem, (size_t)d.T * d.T * d.T * rb);
+    p->smem = std::max(p->smem, (size_t)d.tpz * d.T * rb);
     max_spec = std::max(max_spec, hp.spec_elems);
   }
   chunk_first[n] = (int)chunks.size();

@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(256) k_spread(
   const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
   const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
             oz = tile_origin(S, bz, P, real());
-  const int T3 = T * T * T;
-  for (int j = threadIdx.x; j < T3; j += blockDim.x) tile[j] = real(0);
+  const int T3 = T * T * T, PY = S.tpy, PZ = S.tpz;
+  for (int j = threadIdx.x; j < PZ * T; j += blockDim.x) tile[j] = real(0);
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
   const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(256) k_spread(
 #pragma unroll
       for (int bb = 0; bb < P; ++bb) {
         const real qzy = qz * wy[bb];
-        real* row = tile + ((lz + c) * T + (ly + bb)) * T + lx;
+        real* row = tile + (lz + c) * PZ + (ly + bb) * PY + lx;
 #pragma unroll
         for (int a = 0; a < P; ++a) atomicAdd(row + a, qzy * wx[a]);
       }
@@ -397,9 +397,9 @@ __global__ void __launch_bounds__(256) k_spread(
   __syncthreads();
   real* grid = grids + S.grid0;
   for (int j = threadIdx.x; j < T3; j += blockDim.x) {
-    const real v = tile[j];
+    const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
+    const real v = tile[jz * PZ + jy * PY + jx];
     if (v != real(0)) {
-      const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
       const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f),
                 gz = wrap_index(oz + jz, n_f);
       atomicAdd(grid + ((long long)gz * n_f + gy) * n_f + gx, v);
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_spread_warps(
   const int b = wk.y;
   const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
   const int ox = tile_origin(S, bx, P, 0.f), oy = tile_origin(S, by, P, 0.f), oz = tile_origin(S, bz, P, 0.f);
-  const int T2 = T * T, T3 = T2 * T;
+  const int T2 = T * T, T3 = T2 * T, PY = S.tpy, PZ = S.tpz;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < P * NC; j += blockDim.x) coef[j] = si.c[j / NC][j % NC];
   for (int j = threadIdx.x; j < nwarps * tile_stride; j += blockDim.x) tiles[j] = 0.f;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256) k_spread_warps(
 #pragma unroll
     for (int k = 0; k < kPass; ++k) {
       const int r = min(lane + 32 * k, kRows - 1);
-      row_off[k] = (r / P) * T2 + (r % P) * T;
+      row_off[k] = (r / P) * PZ + (r % P) * PY;
     }
     // chunks of 32 consecutive atoms: one coalesced load, stencil origins and
     // fractions computed lane-parallel, then the atoms one after another
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(256) k_spread_warps(
         const int lz = stencil(S, at.z, P, syz) - oz;
         sok = !(lx < 0 || ly < 0 || lz < 0 || lx > T - P || ly > T - P || lz > T - P);
         if (!sok) atomicOr(err, 2);
-        sl = lz * T2 + ly * T + lx;
+        sl = lz * PZ + ly * PY + lx;
         sq = __uint_as_float(at.w);
       }
       const unsigned okmask = __ballot_sync(0xffffffffu, sok);
@@ -507,10 +507,11 @@ __global__ void __launch_bounds__(256) k_spread_warps(
   __syncthreads();
   float* grid = grids + S.grid0;
   for (int j = threadIdx.x; j < T3; j += blockDim.x) {
+    const int jx = j % T, jy = (j / T) % T, jz = j / T2;
+    const int jt = jz * PZ + jy * PY + jx;
     float v = 0.f;
-    for (int k = 0; k < nwarps; ++k) v += tiles[(size_t)k * tile_stride + j];
+    for (int k = 0; k < nwarps; ++k) v += tiles[(size_t)k * tile_stride + jt];
     if (v != 0.f) {
-      const int jx = j % T, jy = (j / T) % T, jz = j / T2;
       const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f), gz = wrap_index(oz + jz, n_f);
       atomicAdd(grid + ((long long)gz * n_f + gy) * n_f + gx, v);
     }
@@ -568,13 +569,13 @@ __global__ void __launch_bounds__(256) k_gather(
   const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
   const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
             oz = tile_origin(S, bz, P, real());
-  const int T3 = T * T * T;
+  const int T3 = T * T * T, PY = S.tpy, PZ = S.tpz;
   const real* grid = grids + S.grid0;
   for (int j = threadIdx.x; j < T3; j += blockDim.x) {
     const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
     const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f),
               gz = wrap_index(oz + jz, n_f);
-    tile[j] = __ldg(grid + ((long long)gz * n_f + gy) * n_f + gx);
+    tile[jz * PZ + jy * PY + jx] = __ldg(grid + ((long long)gz * n_f + gy) * n_f + gx);
   }
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(256) k_gather(
       real uc = 0, gxc = 0, gyc = 0;
 #pragma unroll
       for (int bb = 0; bb < P; ++bb) {
-        const real* row = tile + ((lz + c) * T + (ly + bb)) * T + lx;
+        const real* row = tile + (lz + c) * PZ + (ly + bb) * PY + lx;
         real s0 = 0, s1 = 0;
 #pragma unroll
         for (int a = 0; a < P; ++a) {

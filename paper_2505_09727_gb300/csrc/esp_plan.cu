@@ -390,7 +390,9 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     d.n_f = n_f; d.n_c = nc; d.bc = b; d.nb = nc / b;
     d.L = L; d.inv_h = n_f / L;
     const int t = tile_edge(d, P, prec);
-    if ((size_t)t * t * t * rb > 200 * 1024) continue;
+    int tpy = 0, tpz = 0;
+    espk::tile_pitches(t, P, tpy, tpz);
+    if ((size_t)tpz * t * rb > 200 * 1024) continue;
     const double edge = (double)b * n_f / nc;            // brick edge in grid points
     const double keep = (double)nc / nc_max;
     double score = -std::fabs(std::log(edge / 6.5));
@@ -408,6 +410,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   espk::SysDesc& d = hp.desc;
   d = espk::SysDesc{};
   d.n_f = n_f; d.n_c = n_c; d.bc = bc; d.nb = n_c / bc; d.T = T;
+  espk::tile_pitches(T, P, d.tpy, d.tpz);
   d.reach = reach;
   d.n_atoms = (int)N;
   d.gsize = 3 * (n_f / 2) * (n_f / 2) + 1;
