@@ -76,10 +76,11 @@ static cudaError_t spread_p(const SysDesc* sys, const int2* work, int n_work, si
     // private tile per warp while up to 8 tiles fit in ~110 KB (two CTAs per
     // SM); otherwise one shared tile with shared-memory atomics
     const size_t stride = (smem / sizeof(float) + 31) & ~size_t(31);   // floats, bank-aligned
-    const int nwarps = (int)std::min<size_t>(8, (110u * 1024u) / (stride * sizeof(float)));
+    const size_t per_warp = (stride + SpreadScratch<P>::kFloats) * sizeof(float);
+    const int nwarps = (int)std::min<size_t>(8, (110u * 1024u) / per_warp);
     if (nwarps >= 2) {
       auto kw = k_spread_warps<P>;
-      const size_t bytes = (size_t)((P * Deg<float>::si + 3) & ~3) * sizeof(float) + nwarps * stride * sizeof(float);
+      const size_t bytes = nwarps * per_warp;
       cudaError_t e = detail::allow_smem(kw, bytes);
       if (e != cudaSuccess) return e;
       const int splits = detail::brick_splits(n_work);

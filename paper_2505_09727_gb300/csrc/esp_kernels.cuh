@@ -408,22 +408,29 @@ __global__ void __launch_bounds__(256) k_spread(
 }
 
 // A2 (FP32): spread with one private tile per warp and no atomics inside the
-// block. The warps of a CTA take the brick's atoms in turn; for each atom,
-// lanes 0 ... 3P-1 evaluate the 3P one-dimensional weights (coefficients in
-// shared memory), every lane takes whole stencil rows (b, c) of the atom, and
-// the row points of one atom are distinct, so plain read-add-write needs no
-// atomics; atoms of one warp follow each other after a warp barrier. The
-// private tiles are summed point by point and flushed to the grid with
-// global atomics (bricks overlap by P - 1 points).
+// block. The warps of a CTA take the brick's atoms in chunks of 32: lane l
+// evaluates the 3P one-dimensional weights of the chunk's atom l (charge
+// folded into the z weights) and its tile offset into the warp's scratch;
+// then the chunk's atoms follow each other, every lane taking whole stencil
+// rows (b, c) of the atom. The row points of one atom are distinct, so plain
+// read-add-write needs no atomics, and the padded tile pitches put the rows
+// of one atom on distinct banks. The private tiles are summed point by point
+// and flushed to the grid with global atomics (bricks overlap by P - 1
+// points).
+template <int P>
+struct SpreadScratch {
+  static constexpr int kW = 3 * P | 1;            // weights per atom; odd: lane stores hit distinct banks
+  static constexpr int kFloats = 32 * kW + 32;    // weights of 32 atoms + their tile offsets
+};
+
 template <int P>
 __global__ void __launch_bounds__(256) k_spread_warps(
     const SysDesc* __restrict__ sys, const int2* __restrict__ work, const uint4* __restrict__ atoms,
     const uint32_t* __restrict__ start, float* __restrict__ grids, const SICoef<float> si, int nwarps,
     int tile_stride, int splits, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int NC = Deg<float>::si;
-  float* coef = reinterpret_cast<float*>(smem_raw);                  // [P][NC]
-  float* tiles = coef + ((P * NC + 3) & ~3);                        // [nwarps][tile_stride]
+  constexpr int kW = SpreadScratch<P>::kW;
+  float* tiles = reinterpret_cast<float*>(smem_raw);                 // [nwarps][tile_stride]
   const int2 wk = work[blockIdx.x / splits];
   const int split = blockIdx.x % splits;
   const SysDesc& S = sys[wk.x];
@@ -433,68 +440,62 @@ __global__ void __launch_bounds__(256) k_spread_warps(
   const int ox = tile_origin(S, bx, P, 0.f), oy = tile_origin(S, by, P, 0.f), oz = tile_origin(S, bz, P, 0.f);
   const int T2 = T * T, T3 = T2 * T, PY = S.tpy, PZ = S.tpz;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < P * NC; j += blockDim.x) coef[j] = si.c[j / NC][j % NC];
   for (int j = threadIdx.x; j < nwarps * tile_stride; j += blockDim.x) tiles[j] = 0.f;
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
   const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
   if (wid < nwarps) {
     float* tile = tiles + (size_t)wid * tile_stride;
-    // this lane's weight: axis lane / P, point lane % P (coefficients kept in
-    // registers for the whole kernel)
-    const int w_axis = lane / P, w_point = lane - (lane / P) * P;
-    float wc[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) wc[k] = coef[w_point * NC + k];
+    float* wts = tiles + (size_t)nwarps * tile_stride + (size_t)wid * SpreadScratch<P>::kFloats;
+    int* offs = reinterpret_cast<int*>(wts + 32 * kW);
     constexpr int kRows = P * P;
     constexpr int kPass = (kRows + 31) / 32;
-    int row_off[kPass];
+    int row_off[kPass], wy_at[kPass], wz_at[kPass];
 #pragma unroll
     for (int k = 0; k < kPass; ++k) {
       const int r = min(lane + 32 * k, kRows - 1);
       row_off[k] = (r / P) * PZ + (r % P) * PY;
+      wy_at[k] = P + r % P;
+      wz_at[k] = 2 * P + r / P;
     }
-    // chunks of 32 consecutive atoms: one coalesced load, stencil origins and
-    // fractions computed lane-parallel, then the atoms one after another
     const int n_here = (int)(a_end - a_begin);
     const int n_chunks = (n_here + 31) / 32;
     for (int ch = split * nwarps + wid; ch < n_chunks; ch += nwarps * splits) {
       const int a0 = ch * 32;
       const int cnt = min(32, n_here - a0);
-      int sl = 0;                                  // packed tile offset of this lane's atom
-      float syx = 0.f, syy = 0.f, syz = 0.f, sq = 0.f;
       bool sok = false;
       if (lane < cnt) {
         const uint4 at = atoms[a_begin + a0 + lane];
-        const int lx = stencil(S, at.x, P, syx) - ox;
-        const int ly = stencil(S, at.y, P, syy) - oy;
-        const int lz = stencil(S, at.z, P, syz) - oz;
+        float yx, yy, yz;
+        const int lx = stencil(S, at.x, P, yx) - ox;
+        const int ly = stencil(S, at.y, P, yy) - oy;
+        const int lz = stencil(S, at.z, P, yz) - oz;
         sok = !(lx < 0 || ly < 0 || lz < 0 || lx > T - P || ly > T - P || lz > T - P);
         if (!sok) atomicOr(err, 2);
-        sl = lz * PZ + ly * PY + lx;
-        sq = __uint_as_float(at.w);
-      }
-      const unsigned okmask = __ballot_sync(0xffffffffu, sok);
-      for (int t = 0; t < cnt; ++t) {
-        if (!((okmask >> t) & 1u)) continue;
-        const int off = __shfl_sync(0xffffffffu, sl, t);
-        const float yx = __shfl_sync(0xffffffffu, syx, t);
-        const float yy = __shfl_sync(0xffffffffu, syy, t);
-        const float yz = __shfl_sync(0xffffffffu, syz, t);
-        const float q = __shfl_sync(0xffffffffu, sq, t);
-        const float y = w_axis == 0 ? yx : (w_axis == 1 ? yy : yz);
-        float wv = wc[NC - 1];
+        float w[3 * P];
+        si_weights<float, P, false>(si, yx, w, nullptr);
+        si_weights<float, P, false>(si, yy, w + P, nullptr);
+        si_weights<float, P, false>(si, yz, w + 2 * P, nullptr);
+        const float q = __uint_as_float(at.w);
+        float* mine = wts + lane * kW;
 #pragma unroll
-        for (int k = NC - 2; k >= 0; --k) wv = fmaf(wv, y, wc[k]);
-        if (lane >= 3 * P) wv = 0.f;
+        for (int k = 0; k < 2 * P; ++k) mine[k] = w[k];
+#pragma unroll
+        for (int k = 2 * P; k < 3 * P; ++k) mine[k] = q * w[k];
+        offs[lane] = sok ? lz * PZ + ly * PY + lx : -1;
+      }
+      __syncwarp();
+      for (int t = 0; t < cnt; ++t) {
+        const int off = offs[t];
+        if (off < 0) continue;                   // warp-uniform
+        const float* wt = wts + t * kW;
         float wx[P];
 #pragma unroll
-        for (int a = 0; a < P; ++a) wx[a] = __shfl_sync(0xffffffffu, wv, a);
+        for (int a = 0; a < P; ++a) wx[a] = wt[a];
 #pragma unroll
         for (int k = 0; k < kPass; ++k) {
-          const int r = min(lane + 32 * k, kRows - 1);
-          const float wyz = q * __shfl_sync(0xffffffffu, wv, P + r % P) * __shfl_sync(0xffffffffu, wv, 2 * P + r / P);
           if (lane + 32 * k < kRows) {
+            const float wyz = wt[wy_at[k]] * wt[wz_at[k]];
             float* row = tile + off + row_off[k];
 #pragma unroll
             for (int a = 0; a < P; ++a) row[a] = fmaf(wyz, wx[a], row[a]);
