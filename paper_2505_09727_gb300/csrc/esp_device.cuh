@@ -145,6 +145,13 @@ __host__ __device__ inline int wrap_index(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
+// The same for indices within a few periods of [0, n) (tile points around a
+// brick): additions instead of an integer division.
+__host__ __device__ inline int wrap_near(int v, int n) {
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
+}
 
 // --------------------------------------------------------------- reductions
 __device__ inline double warp_sum(double v) {

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256) k_spread(
   const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
   const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
             oz = tile_origin(S, bz, P, real());
-  const int T3 = T * T * T, PY = S.tpy, PZ = S.tpz;
+  const int PY = S.tpy, PZ = S.tpz;
   for (int j = threadIdx.x; j < PZ * T; j += blockDim.x) tile[j] = real(0);
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
@@ -396,13 +396,12 @@ __global__ void __launch_bounds__(256) k_spread(
   }
   __syncthreads();
   real* grid = grids + S.grid0;
-  for (int j = threadIdx.x; j < T3; j += blockDim.x) {
-    const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
-    const real v = tile[jz * PZ + jy * PY + jx];
-    if (v != real(0)) {
-      const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f),
-                gz = wrap_index(oz + jz, n_f);
-      atomicAdd(grid + ((long long)gz * n_f + gy) * n_f + gx, v);
+  for (int jyx = threadIdx.x; jyx < T * T; jyx += blockDim.x) {
+    const int jy = jyx / T, jx = jyx - jy * T;
+    const long long gyx = (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f);
+    for (int jz = 0; jz < T; ++jz) {
+      const real v = tile[jz * PZ + jy * PY + jx];
+      if (v != real(0)) atomicAdd(grid + (long long)wrap_near(oz + jz, n_f) * n_f * n_f + gyx, v);
     }
   }
 }
@@ -438,7 +437,7 @@ __global__ void __launch_bounds__(256) k_spread_warps(
   const int b = wk.y;
   const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
   const int ox = tile_origin(S, bx, P, 0.f), oy = tile_origin(S, by, P, 0.f), oz = tile_origin(S, bz, P, 0.f);
-  const int T2 = T * T, T3 = T2 * T, PY = S.tpy, PZ = S.tpz;
+  const int T2 = T * T, PY = S.tpy, PZ = S.tpz;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < nwarps * tile_stride; j += blockDim.x) tiles[j] = 0.f;
   __syncthreads();
@@ -506,15 +505,16 @@ __global__ void __launch_bounds__(256) k_spread_warps(
     }
   }
   __syncthreads();
+  // flush: a thread keeps one (y, x) column of the tile and walks it in z
   float* grid = grids + S.grid0;
-  for (int j = threadIdx.x; j < T3; j += blockDim.x) {
-    const int jx = j % T, jy = (j / T) % T, jz = j / T2;
-    const int jt = jz * PZ + jy * PY + jx;
-    float v = 0.f;
-    for (int k = 0; k < nwarps; ++k) v += tiles[(size_t)k * tile_stride + jt];
-    if (v != 0.f) {
-      const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f), gz = wrap_index(oz + jz, n_f);
-      atomicAdd(grid + ((long long)gz * n_f + gy) * n_f + gx, v);
+  for (int jyx = threadIdx.x; jyx < T2; jyx += blockDim.x) {
+    const int jy = jyx / T, jx = jyx - jy * T;
+    const long long gyx = (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f);
+    int jt = jy * PY + jx;
+    for (int jz = 0; jz < T; ++jz, jt += PZ) {
+      float v = 0.f;
+      for (int k = 0; k < nwarps; ++k) v += tiles[(size_t)k * tile_stride + jt];
+      if (v != 0.f) atomicAdd(grid + (long long)wrap_near(oz + jz, n_f) * n_f * n_f + gyx, v);
     }
   }
 }
@@ -570,13 +570,13 @@ __global__ void __launch_bounds__(256) k_gather(
   const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
   const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
             oz = tile_origin(S, bz, P, real());
-  const int T3 = T * T * T, PY = S.tpy, PZ = S.tpz;
+  const int PY = S.tpy, PZ = S.tpz;
   const real* grid = grids + S.grid0;
-  for (int j = threadIdx.x; j < T3; j += blockDim.x) {
-    const int jx = j % T, jy = (j / T) % T, jz = j / (T * T);
-    const int gx = wrap_index(ox + jx, n_f), gy = wrap_index(oy + jy, n_f),
-              gz = wrap_index(oz + jz, n_f);
-    tile[jz * PZ + jy * PY + jx] = __ldg(grid + ((long long)gz * n_f + gy) * n_f + gx);
+  for (int jyx = threadIdx.x; jyx < T * T; jyx += blockDim.x) {
+    const int jy = jyx / T, jx = jyx - jy * T;
+    const long long gyx = (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f);
+    for (int jz = 0; jz < T; ++jz)
+      tile[jz * PZ + jy * PY + jx] = __ldg(grid + (long long)wrap_near(oz + jz, n_f) * n_f * n_f + gyx);
   }
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
