@@ -9,7 +9,9 @@ Spectral (far-field) part, the five-step procedure (Eqs. spread ... interp):
                   th = 2 pi k / n_f), p_0 = 0
   4. IFFT         c_l  = sum_k exp(-2 pi i k.l / n_f) ch_k
   5. interpolate  u~_i = sum_l phi~(r_i - h l) c_l, and grad u~_i by exact
-                  derivatives of phi (the "AD" force method)
+                  derivatives of phi (the "AD" force method), or (the "ik"
+                  method, Methods) by interpolating with phi~ the three grids
+                  IFFT(-2 pi i k_a / L ch_k), a = x, y, z
 Local (near-field) part (Eq. localpart): u^l_i = sum' q_j L(|r_i - r_j - nL|) over
 pairs closer than r_c, L(r) = (1 - g(r/r_c)) / (4 pi r).
 Self term: the spectral sum keeps j = i, n = 0 (spectralpart discussion), whose
@@ -47,12 +49,13 @@ class ESPParams:
     kind: str = "pswf"            # "pswf" or "gauss"
     alpha: float | None = None    # Gaussian shape (default: ln(1/eps))
     window: str = "pswf"          # SI window: "pswf" (psi_0^{c1}) or "bspline" (order P)
+    diff: str = "ad"              # spectral forces: "ad" (derivatives of phi) or "ik"
 
     def resolved(self) -> "ESPParams":
         c = self.c if self.c is not None else pswf.c_from_tolerance(self.eps)
         c1 = self.c1 if self.c1 is not None else prm.C1_RATIO * c
         alpha = self.alpha if self.alpha is not None else math.log(1.0 / self.eps)
-        return ESPParams(self.eps, self.r_c, self.P, self.n_f, c, c1, self.kind, alpha, self.window)
+        return ESPParams(self.eps, self.r_c, self.P, self.n_f, c, c1, self.kind, alpha, self.window, self.diff)
 
     def si_window(self):
         p = self.resolved()
@@ -121,7 +124,26 @@ def influence(L, n_f, r_c, split, window):
     return shat / den
 
 
-def far_field(pos, q, L, n_f, r_c, split, window, targets):
+def ik_gradient(ch, L):
+    """The three grids of the ik method: c^a_l = sum_k exp(-2 pi i k.l/n_f)
+    (-2 pi i k_a / L) ch_k, the exact derivatives along a of the
+    trigonometric interpolant of c_l (ch in numpy's FFT order). The Nyquist
+    component k_a = -n_f/2 of the differentiated axis is set to zero: its
+    derivative is not a real grid function (reading of the ik method for
+    even n_f)."""
+    n_f = ch.shape[0]
+    k = np.fft.fftfreq(n_f, d=1.0 / n_f)
+    k = np.where(k == -(n_f // 2), 0.0, k) if n_f % 2 == 0 else k
+    out = []
+    for a in range(3):
+        shape = [1, 1, 1]
+        shape[a] = n_f
+        mult = (-2j * math.pi / L) * k.reshape(shape)
+        out.append(np.fft.fftn(ch * mult).real)
+    return out
+
+
+def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad"):
     """Steps 1-5: (u~ at targets, grad u~ at targets, 1/2 sum_k p_k |bh_k|^2)."""
     b = spread(pos, q, L, n_f, window)
     bh = np.fft.ifftn(b) * n_f ** 3                           # exp(+2 pi i k.l/n_f)
@@ -133,6 +155,18 @@ def far_field(pos, q, L, n_f, r_c, split, window, targets):
     P = window.P
     u = np.zeros(len(targets))
     grad = np.zeros((len(targets), 3))
+    if diff == "ik":
+        gx, gy, gz = ik_gradient(ch, L)
+        for a, bb, cc in itertools.product(range(P), repeat=3):
+            ii = (idx[:, 0, a], idx[:, 1, bb], idx[:, 2, cc])
+            www = w[:, 0, a] * w[:, 1, bb] * w[:, 2, cc]
+            u += www * cgrid[ii]
+            grad[:, 0] += www * gx[ii]
+            grad[:, 1] += www * gy[ii]
+            grad[:, 2] += www * gz[ii]
+        return u, grad, fourier_energy
+    if diff != "ad":
+        raise ValueError("diff must be 'ad' or 'ik'")
     for a, bb, cc in itertools.product(range(P), repeat=3):
         val = cgrid[idx[:, 0, a], idx[:, 1, bb], idx[:, 2, cc]]
         u += w[:, 0, a] * w[:, 1, bb] * w[:, 2, cc] * val
@@ -186,7 +220,7 @@ def esp(pos, q, L, p: ESPParams, targets=None):
     tgt = np.arange(n) if all_atoms else np.asarray(targets, dtype=np.int64)
     split = p.split()
     window = p.si_window()
-    u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt)
+    u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt, p.diff)
     u_l, f_l = near_field(pos, q, L, p.r_c, split, tgt)
     self_term = q[tgt] * split.chi0 / (4.0 * math.pi * p.r_c)
     Q = float(np.sum(q))
