@@ -324,6 +324,8 @@ def run_gpu(args, world, rank, local):
     if not args.no_extras and world == 1:
         extras["plain_fp64"] = single_variant(args, local, stream, flush, s, precision=esp.ESP_FP64)
         extras["gaussian"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS)
+        # the ik force method (Methods, step 5): three more inverse FFTs
+        extras["ik"] = single_variant(args, local, stream, flush, s, diff=esp.ESP_DIFF_IK)
         # the "Default" comparator of Table 1: Gaussian split, cardinal B-spline window
         extras["default_bspline"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS,
                                                    window=esp.ESP_WINDOW_BSPLINE)
@@ -375,7 +377,8 @@ def single_variant(args, local, stream, flush, s, tolerance=None, **opts):
     esp.esp_destroy(h)
     t = statistics.median(ms)
     return {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
-            "window": ("pswf", "bspline")[info["window"]], "tolerance": tol, "steps": len(ms)}
+            "window": ("pswf", "bspline")[info["window"]], "diff": ("ad", "ik")[info["diff"]],
+            "tolerance": tol, "steps": len(ms)}
 
 
 LARGE = dict(workload="spce_water_1e6_molecules", molecules=1_000_000, atoms=3_000_000, density_per_nm3=33.4,

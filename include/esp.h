@@ -73,6 +73,7 @@ typedef enum {
 
 enum { ESP_KERNEL_PSWF = 0, ESP_KERNEL_GAUSS = 1 };
 enum { ESP_WINDOW_PSWF = 0, ESP_WINDOW_BSPLINE = 1 };
+enum { ESP_DIFF_AD = 0, ESP_DIFF_IK = 1 };
 enum { ESP_FP32 = 0, ESP_FP64 = 1 };
 enum { ESP_HOST = 0, ESP_DEVICE = 1 };
 
@@ -110,7 +111,14 @@ typedef struct {
                           every pair from both sides, 4 = the same, every pair
                           once (FP32 only for 3, 4); 0 = default (4 in FP32,
                           1 in FP64)                                          */
-  int reserved[5];
+  int diff;            /* spectral forces (Methods, step 5): ESP_DIFF_AD
+                          (default: analytic derivatives of the SI kernel's
+                          polynomials) or ESP_DIFF_IK (the scaled spectrum
+                          times 2 pi i k_a / L, three more inverse FFTs, the
+                          gradients interpolated with the SI weights; the
+                          Nyquist component of the differentiated axis is
+                          zero). Potentials and energies are the same.      */
+  int reserved[4];
 } esp_plan_opts;
 
 /* Parameters a plan chose (esp_plan_info). */
@@ -129,7 +137,8 @@ typedef struct {
   int si_degree, near_degree;
   size_t device_bytes;     /* device memory held by the plan                 */
   int window;              /* ESP_WINDOW_PSWF or ESP_WINDOW_BSPLINE          */
-  int reserved[3];
+  int diff;                /* ESP_DIFF_AD or ESP_DIFF_IK                     */
+  int reserved[2];
 } esp_plan_params;
 
 /* Fill opts with defaults (all planner choices, FP32, PSWF, device 0). */

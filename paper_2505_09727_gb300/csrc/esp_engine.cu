@@ -119,6 +119,9 @@ struct esp_plan_s {
   void* d_qstage = nullptr;      // staging for charges (FP64)
   void* d_grid = nullptr;
   void* d_spec = nullptr;
+  void* d_grid_ik = nullptr;     // ik method: three gradient grids, component-major
+  void* d_spec_ik = nullptr;     // ... and their three half spectra
+  bool ik = false;
   void* d_tabs = nullptr;
   void* d_far = nullptr;
   void* d_near = nullptr;
@@ -333,6 +336,11 @@ esp_status build_buffers(esp_plan_s* p) {
   ESP_TRY(dev_alloc(p, &p->d_qstage, (size_t)N * sizeof(double)));
   ESP_TRY(dev_alloc(p, &p->d_grid, (size_t)p->grid_total * rb));
   ESP_TRY(dev_alloc(p, &p->d_spec, (size_t)p->spec_total * 2 * rb));
+  p->ik = p->hps[0].info.diff == ESP_DIFF_IK;
+  if (p->ik) {
+    ESP_TRY(dev_alloc(p, &p->d_grid_ik, (size_t)p->grid_total * 3 * rb));
+    ESP_TRY(dev_alloc(p, &p->d_spec_ik, (size_t)p->spec_total * 3 * 2 * rb));
+  }
   ESP_TRY(dev_alloc(p, &p->d_tabs, (size_t)p->tab_total * rb));
   ESP_TRY(dev_alloc(p, &p->d_far, (size_t)N * L::res_bytes()));
   ESP_TRY(dev_alloc(p, &p->d_near, (size_t)N * L::res_bytes()));
@@ -547,7 +555,8 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
                            (cufftDoubleComplex*)p->d_spec + b.spec0));
   }
   rec(p, 5, st);
-  ESP_CU(L::scale(p->d_desc, p->nsys, p->F, p->d_spec, (const real*)p->d_tabs, p->d_fourier, st));
+  ESP_CU(L::scale(p->d_desc, p->nsys, p->F, p->d_spec, (const real*)p->d_tabs, p->d_fourier, p->d_spec_ik,
+                  p->spec_total, st));
   rec(p, 6, st);
   for (Bucket& b : p->buckets) {
     if (sizeof(real) == 4)
@@ -556,9 +565,21 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
       ESP_FFT(cufftExecZ2D(b.inv, (cufftDoubleComplex*)p->d_spec + b.spec0,
                            (cufftDoubleReal*)p->d_grid + b.grid0));
   }
+  if (p->ik) {
+    // ik method: the three gradient spectra back to the grid
+    for (int a = 0; a < 3; ++a) {
+      for (Bucket& b : p->buckets) {
+        const long long so = a * p->spec_total + b.spec0, go = a * p->grid_total + b.grid0;
+        if (sizeof(real) == 4)
+          ESP_FFT(cufftExecC2R(b.inv, (cufftComplex*)p->d_spec_ik + so, (cufftReal*)p->d_grid_ik + go));
+        else
+          ESP_FFT(cufftExecZ2D(b.inv, (cufftDoubleComplex*)p->d_spec_ik + so, (cufftDoubleReal*)p->d_grid_ik + go));
+      }
+    }
+  }
   rec(p, 7, st);
   ESP_CU(L::gather(p->P, p->d_desc, p->d_work, p->n_work, p->smem, p->d_atoms, p->d_start,
-                   (const real*)p->d_grid, p->d_far, si, p->d_err, st));
+                   (const real*)p->d_grid, (const real*)p->d_grid_ik, p->grid_total, p->d_far, si, p->d_err, st));
   rec(p, 8, st);
   // join and finish
   if (!serial) ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
@@ -756,6 +777,7 @@ esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const
   size_t bytes = (size_t)N * (24 + 2 * ab + 4 * 3 + rb + 8 + 2 * ab + 32) +
                  (size_t)hp.n_keys * 8 + (size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb +
                  (hp.G.size() + hp.W.size()) * rb;
+  if (o.diff == ESP_DIFF_IK) bytes += 3 * ((size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb);
   if (hp.near_clusters) {
     // cluster counts, offsets and lists of the local part
     const size_t n_cols = (size_t)hp.desc.n_c * hp.desc.n_c;

@@ -99,9 +99,20 @@ static cudaError_t spread_p(const SysDesc* sys, const int2* work, int n_work, si
 template <int P>
 static cudaError_t gather_p(const SysDesc* sys, const int2* work, int n_work, size_t smem,
                             const void* atoms, const uint32_t* start, const ESP_REAL* grids,
+                            const ESP_REAL* grids_ik, long long grid_total,
                             void* far, const SICoef<ESP_REAL>& si, int* err, cudaStream_t st) {
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
+  if (grids_ik) {
+    // ik method: potential and three gradient tiles
+    auto ki = k_gather_ik<ESP_REAL, P>;
+    cudaError_t e = detail::allow_smem(ki, 4 * smem);
+    if (e != cudaSuccess) return e;
+    const int splits = detail::brick_splits(n_work);
+    ki<<<n_work * splits, 256, 4 * smem, st>>>(sys, work, (const A*)atoms, start, grids, grids_ik, grid_total,
+                                               (R*)far, si, splits, err);
+    return cudaGetLastError();
+  }
   auto kern = k_gather<ESP_REAL, P>;
   cudaError_t e = detail::allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -128,11 +139,11 @@ cudaError_t Launch<ESP_REAL>::spread(int P, const SysDesc* sys, const int2* work
 template <>
 cudaError_t Launch<ESP_REAL>::gather(int P, const SysDesc* sys, const int2* work, int n_work,
                                      size_t smem, const void* atoms, const uint32_t* start,
-                                     const ESP_REAL* grids, void* far, const SICoef<ESP_REAL>& si,
-                                     int* err, cudaStream_t st) {
+                                     const ESP_REAL* grids, const ESP_REAL* grids_ik, long long grid_total,
+                                     void* far, const SICoef<ESP_REAL>& si, int* err, cudaStream_t st) {
   if (n_work == 0) return cudaSuccess;
   switch (P) {
-    ESP_P_CASES(gather_p, sys, work, n_work, smem, atoms, start, grids, far, si, err, st)
+    ESP_P_CASES(gather_p, sys, work, n_work, smem, atoms, start, grids, grids_ik, grid_total, far, si, err, st)
     default: return cudaErrorInvalidValue;
   }
 }
@@ -142,10 +153,11 @@ bool Launch<ESP_REAL>::supports_P(int P) { return P >= ESP_P_MIN && P <= ESP_P_M
 
 template <>
 cudaError_t Launch<ESP_REAL>::scale(const SysDesc* sys, int nsys, int nblk, void* spec,
-                                    const ESP_REAL* tabs, double* partials, cudaStream_t st) {
+                                    const ESP_REAL* tabs, double* partials, void* spec_ik,
+                                    long long spec_total, cudaStream_t st) {
   using C = typename Types<ESP_REAL>::cplx;
   dim3 grid(nblk, nsys);
-  k_scale<ESP_REAL><<<grid, 256, 0, st>>>(sys, (C*)spec, tabs, partials);
+  k_scale<ESP_REAL><<<grid, 256, 0, st>>>(sys, (C*)spec, tabs, partials, (C*)spec_ik, spec_total);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 namespace espk {
 
 constexpr double kFourPi = 12.566370614359172953850573533118;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 // 32-byte aligned FP64 quadruple (one 256-bit access per atom / result).
 struct __align__(32) dquad { double x, y, z, w; };
@@ -27,6 +28,13 @@ template <> struct Types<double> {
   using res = dquad;
   using cplx = double2;
 };
+
+template <typename real> __device__ inline typename Types<real>::cplx make_cplx(real re, real im) {
+  typename Types<real>::cplx c;
+  c.x = re;
+  c.y = im;
+  return c;
+}
 
 __device__ inline float atom_q(const uint4& a) { return __uint_as_float(a.w); }
 __device__ inline double atom_q(const dquad& a) { return a.w; }
@@ -524,7 +532,8 @@ __global__ void __launch_bounds__(256) k_spread_warps(
 template <typename real>
 __global__ void __launch_bounds__(256) k_scale(
     const SysDesc* __restrict__ sys, typename Types<real>::cplx* __restrict__ spec,
-    const real* __restrict__ tabs, double* __restrict__ partials) {
+    const real* __restrict__ tabs, double* __restrict__ partials,
+    typename Types<real>::cplx* __restrict__ spec_ik, long long spec_total) {
   __shared__ double red[32];
   const SysDesc& S = sys[blockIdx.y];
   const int n = S.n_f, nh = n / 2 + 1, half = n / 2;
@@ -548,9 +557,100 @@ __global__ void __launch_bounds__(256) k_scale(
     v.x *= p;
     v.y *= p;
     sp[idx] = v;
+    if (spec_ik) {
+      // ik method: the inverse transform is sum_k c_k exp(+2 pi i k.l/n_f),
+      // so d/dx_a multiplies c_k by +2 pi i k_a / L; the Nyquist component
+      // of the differentiated axis is zero (no real grid function)
+      const real s = real(kTwoPi / S.L);
+      const real sx = kx == half ? real(0) : s * kx;
+      const real sy = kyi == half ? real(0) : s * ky;
+      const real sz = kzi == half ? real(0) : s * kz;
+      typename Types<real>::cplx* o = spec_ik + S.spec0 + idx;
+      o[0] = make_cplx<real>(-v.y * sx, v.x * sx);
+      o[spec_total] = make_cplx<real>(-v.y * sy, v.x * sy);
+      o[2 * spec_total] = make_cplx<real>(-v.y * sz, v.x * sz);
+    }
   }
   e = block_sum(e, red);
   if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * e;
+}
+
+// A6 (ik method): gather the potential and the three gradient grids with the
+// SI weights alone; the gradients are already derivatives in physical units.
+template <typename real, int P>
+__global__ void __launch_bounds__(256) k_gather_ik(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ work,
+    const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ start,
+    const real* __restrict__ grids, const real* __restrict__ grids_ik, long long grid_total,
+    typename Types<real>::res* __restrict__ far, const SICoef<real> si, int splits, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 wk = work[blockIdx.x / splits];
+  const int split = blockIdx.x % splits;
+  const SysDesc& S = sys[wk.x];
+  const int nb = S.nb, T = S.T, n_f = S.n_f, bc = S.bc;
+  const int b = wk.y;
+  const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+  const int ox = tile_origin(S, bx, P, real()), oy = tile_origin(S, by, P, real()),
+            oz = tile_origin(S, bz, P, real());
+  const int PY = S.tpy, PZ = S.tpz;
+  const int tsz = PZ * T;                                   // elements of one tile
+  real* tile = reinterpret_cast<real*>(smem_raw);           // [4][tsz]: u, du/dx, du/dy, du/dz
+  for (int g = 0; g < 4; ++g) {
+    const real* grid = (g == 0 ? grids : grids_ik + (g - 1) * grid_total) + S.grid0;
+    real* t = tile + g * tsz;
+    for (int jyx = threadIdx.x; jyx < T * T; jyx += blockDim.x) {
+      const int jy = jyx / T, jx = jyx - jy * T;
+      const long long gyx = (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f);
+      for (int jz = 0; jz < T; ++jz)
+        t[jz * PZ + jy * PY + jx] = __ldg(grid + (long long)wrap_near(oz + jz, n_f) * n_f * n_f + gyx);
+    }
+  }
+  __syncthreads();
+  const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
+  const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];
+  for (uint32_t i = a_begin + split * blockDim.x + threadIdx.x; i < a_end; i += blockDim.x * splits) {
+    const typename Types<real>::atom at = atoms[i];
+    real yx, yy, yz;
+    const int lx = stencil(S, at.x, P, yx) - ox;
+    const int ly = stencil(S, at.y, P, yy) - oy;
+    const int lz = stencil(S, at.z, P, yz) - oz;
+    typename Types<real>::res out;
+    if (lx < 0 || ly < 0 || lz < 0 || lx > T - P || ly > T - P || lz > T - P) {
+      atomicOr(err, 2);
+      out.x = out.y = out.z = out.w = real(0);
+      far[i] = out;
+      continue;
+    }
+    real wx[P], wy[P];
+    si_weights<real, P, false>(si, yx, wx, nullptr);
+    si_weights<real, P, false>(si, yy, wy, nullptr);
+    real acc[4] = {0, 0, 0, 0};
+#pragma unroll (Unroll<P>::outer)
+    for (int c = 0; c < P; ++c) {
+      real wzc, unused;
+      si_weight_one<real, false>(si, c, yz, wzc, unused);
+      real accc[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int bb = 0; bb < P; ++bb) {
+        const int row = (lz + c) * PZ + (ly + bb) * PY + lx;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const real* r = tile + g * tsz + row;
+          real sx = 0;
+#pragma unroll
+          for (int a = 0; a < P; ++a) sx += wx[a] * r[a];
+          accc[g] += wy[bb] * sx;
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) acc[g] += wzc * accc[g];
+    }
+    out.x = acc[0];
+    out.y = acc[1];
+    out.z = acc[2];
+    out.w = acc[3];
+    far[i] = out;
+  }
 }
 
 // A6: gather (Eq. interp) with analytic-derivative forces.

@@ -18,10 +18,16 @@ struct Launch {
   static cudaError_t spread(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem,
                             const void* atoms, const uint32_t* start, real* grids,
                             const SICoef<real>& si, int* err, cudaStream_t st);
+  // spec_ik (nullable): the ik method's three gradient spectra, component
+  // a at spec_ik + a * spec_total (the pool's half-spectrum length)
   static cudaError_t scale(const SysDesc* sys, int nsys, int nblk, void* spec, const real* tabs,
-                           double* partials, cudaStream_t st);
+                           double* partials, void* spec_ik, long long spec_total, cudaStream_t st);
+  // grids_ik (nullable): the ik method's gradient grids, component a at
+  // grids_ik + a * grid_total; then the forces come from them, not from
+  // derivatives of the SI kernel
   static cudaError_t gather(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem,
-                            const void* atoms, const uint32_t* start, const real* grids, void* far,
+                            const void* atoms, const uint32_t* start, const real* grids,
+                            const real* grids_ik, long long grid_total, void* far,
                             const SICoef<real>& si, int* err, cudaStream_t st);
   static cudaError_t near(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                           const void* rel, const uint32_t* start, void* nearres,

@@ -282,6 +282,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   const int pmax = prec == ESP_FP32 ? 12 : 16;
 
   if (o.window != ESP_WINDOW_PSWF && o.window != ESP_WINDOW_BSPLINE) { msg = "unknown SI window"; return ESP_ERR_INVALID_ARG; }
+  if (o.diff != ESP_DIFF_AD && o.diff != ESP_DIFF_IK) { msg = "diff must be ESP_DIFF_AD or ESP_DIFF_IK"; return ESP_ERR_INVALID_ARG; }
   const bool bspline = o.window == ESP_WINDOW_BSPLINE;
   const double c = o.c > 0 ? o.c : cached_c(tol);
   // the B-spline comparator defaults to the usual smooth-PME order 4
@@ -392,7 +393,8 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     const int t = tile_edge(d, P, prec);
     int tpy = 0, tpz = 0;
     espk::tile_pitches(t, P, tpy, tpz);
-    if ((size_t)tpz * t * rb > 200 * 1024) continue;
+    const size_t tiles = o.diff == ESP_DIFF_IK ? 4 : 1;      // the ik gather holds four tiles
+    if ((size_t)tpz * t * rb * tiles > 200 * 1024) continue;
     const double edge = (double)b * n_f / nc;            // brick edge in grid points
     const double keep = (double)nc / nc_max;
     double score = -std::fabs(std::log(edge / 6.5));
@@ -483,6 +485,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   info.cell_reach = reach; info.near_terms = hp.near_nc;
   info.si_degree = (prec == ESP_FP32 ? espk::Deg<float>::si : espk::Deg<double>::si) - 1;
   info.window = o.window;
+  info.diff = o.diff;
   info.near_degree = (prec == ESP_FP32 ? espk::Deg<float>::nr : espk::Deg<double>::nr) - 1;
   return ESP_OK;
 }

@@ -15,6 +15,7 @@ import numpy as np
 ESP_OK = 0
 ESP_KERNEL_PSWF, ESP_KERNEL_GAUSS = 0, 1
 ESP_WINDOW_PSWF, ESP_WINDOW_BSPLINE = 0, 1
+ESP_DIFF_AD, ESP_DIFF_IK = 0, 1
 ESP_FP32, ESP_FP64 = 0, 1
 ESP_HOST, ESP_DEVICE = 0, 1
 
@@ -46,7 +47,7 @@ class esp_plan_opts(ctypes.Structure):
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("allow_background", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("timeout_ms", ctypes.c_double),
         ("cell_reach", ctypes.c_int), ("window", ctypes.c_int), ("near_variant", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("diff", ctypes.c_int), ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -61,7 +62,7 @@ class esp_plan_params(ctypes.Structure):
         ("cell_reach", ctypes.c_int), ("near_terms", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("tile", ctypes.c_int), ("si_degree", ctypes.c_int),
         ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("window", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("diff", ctypes.c_int), ("reserved", ctypes.c_int * 2),
     ]
 
     def as_dict(self) -> dict:

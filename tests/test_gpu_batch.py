@@ -84,6 +84,26 @@ def test_batch_fp64_matches_oracle(esp):
             assert abs(e[i] - ref["energy"]) <= 1e-10 * abs(ref["energy"])
 
 
+def test_batch_ik_fp64_matches_oracle(esp):
+    """The ik force method on a batch: two grid-size buckets, FP64 against
+    the oracle at each system's parameters."""
+    systems = inputs.electrolyte_batch([3000, 9000], seed=55)
+    eps = 1e-4
+    with esp.Batch([s.L for s in systems], [s.n for s in systems], eps, r_c=1.0,
+                   precision=esp.ESP_FP64, diff=esp.ESP_DIFF_IK) as b:
+        pos, q = inputs.concat(systems)
+        b.set_charges(q)
+        for _ in range(2):               # direct run, then the captured graph
+            e, f, u = b.compute(pos)
+        for i, s in enumerate(systems):
+            info = b.info(i)
+            assert info["diff"] == esp.ESP_DIFF_IK
+            p = oesp.ESPParams(eps, info["r_c"], info["P"], info["n_f"], c=info["c"], c1=info["c1"], diff="ik")
+            ref = oesp.esp(s.pos, s.q, s.L, p)
+            assert metrics.relative_rms_force_error(split(f, b.offsets, i), ref["forces"]) <= 1e-9
+            assert rel_rms(split(u, b.offsets, i), ref["potential"]) <= 1e-9
+
+
 def test_batch_fp32_within_tolerance_of_ewald(esp):
     systems = inputs.electrolyte_batch([3000, 4000, 3200], seed=60)
     refs = [ewald.ewald(s.pos, s.q, s.L, acc=1e-14) for s in systems]

@@ -47,7 +47,8 @@ def oracle_same(s, eps, info, targets=None, pos=None):
     kind = "pswf" if info["kernel"] == 0 else "gauss"
     window = "bspline" if info["window"] == 1 else "pswf"
     p = oesp.ESPParams(eps, info["r_c"], info["P"], info["n_f"], c=info["c"], c1=info["c1"],
-                       kind=kind, alpha=info["alpha"] if kind == "gauss" else None, window=window)
+                       kind=kind, alpha=info["alpha"] if kind == "gauss" else None, window=window,
+                       diff="ik" if info["diff"] == 1 else "ad")
     return oesp.esp(s.pos if pos is None else pos, s.q, s.L, p, targets)
 
 
@@ -170,6 +171,32 @@ def test_bspline_window_within_tolerance_of_ewald(esp, eps):
     ref = ewald.ewald(s.pos, s.q, s.L, acc=1e-14)
     assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= eps
     assert abs(g["energy"] - ref["energy"]) <= eps * abs(ref["energy"])
+
+
+@pytest.mark.parametrize("name", ["water500", "ions300_eps1e-5", "ragged258_P7"])
+def test_ik_matches_oracle(esp, name):
+    """ik force differentiation (three gradient grids) against the oracle at
+    the same parameters, FP64 and FP32."""
+    make, eps, r_c = CASES[name]
+    s = make()
+    for prec, bound in ((esp.ESP_FP64, 1e-9), (esp.ESP_FP32, FP32_PARITY)):
+        g = gpu_solve(esp, s, eps, r_c=r_c, precision=prec, diff=esp.ESP_DIFF_IK)
+        assert g["info"]["diff"] == esp.ESP_DIFF_IK
+        ref = oracle_same(s, eps, g["info"])
+        assert force_error(s, g["forces"], ref["forces"]) <= bound
+        assert rel_rms(g["potential"], ref["potential"]) <= bound
+        e_self = 0.5 * float(np.sum(s.q * ref["self_term"]))
+        assert abs(g["energy"] - ref["energy"]) <= bound * max(abs(ref["energy"]), abs(e_self))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-5])
+def test_ik_within_tolerance_of_ewald(esp, eps):
+    s = inputs.spce_water(1000, seed=11)
+    g = gpu_solve(esp, s, eps, r_c=1.0, diff=esp.ESP_DIFF_IK)
+    ref = ewald.ewald(s.pos, s.q, s.L, acc=1e-14)
+    assert metrics.relative_rms_force_error(g["forces"], ref["forces"]) <= eps
+    ad = gpu_solve(esp, s, eps, r_c=1.0)
+    assert rel_rms(g["potential"], ad["potential"]) <= FP32_PARITY
 
 
 def test_empty_system(esp):
