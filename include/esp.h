@@ -170,7 +170,9 @@ esp_status esp_set_positions_f32(esp_plan_t plan, const float* xyz, int where);
 
 /* Spread, R2C FFT, fused influence scale + spectral energy, C2R FFT, gather,
  * local part, corrections and compensated FP64 energy. Any of energy,
- * forces, potential may be NULL. */
+ * forces, potential may be NULL; with forces and potential both NULL only
+ * the energy is computed (the C2R FFT and the gather are skipped, and the
+ * gathered spectral energy of esp_last_spectral_energy reads 0). */
 esp_status esp_compute(esp_plan_t plan, double* energy, double* forces,
                        double* potential, int where);
 esp_status esp_compute_f32(esp_plan_t plan, double* energy, float* forces,

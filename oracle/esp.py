@@ -17,6 +17,12 @@ pairs closer than r_c, L(r) = (1 - g(r/r_c)) / (4 pi r).
 Self term: the spectral sum keeps j = i, n = 0 (spectralpart discussion), whose
 value q_i S(0) = q_i chi(0) / (4 pi r_c) is subtracted from u_i.
 Totals: u_i = u~_i + u^l_i - self; E = 1/2 sum q_i u_i; F_i = -q_i grad u~_i + F^l_i.
+Virial W_ab = -dE/d eps_ab under the homogeneous deformation r -> (1 + eps) r
+of atoms and box (the grid deforms with the box, so b_l and the grid-unit
+Phi are unchanged): spectral part sum_k 1/2 |bh_k|^2 [p_k delta_ab +
+p'_k k_a k_b / |k|^2], p'_k = (r_c xi chihat'(r_c xi) - 2 chihat(r_c xi)) /
+(xi^2 L^3 Phi^2 Phi^2 Phi^2); local part 1/2 sum_i sum_j F_ij,a d_ij,b over the
+pairs of Eq. localpart; background E_bg delta_ab (E_bg ~ 1/V); self term 0.
 Non-neutral systems get the neutralising-background shift
 -(Q/V) (r_c^2/2) int_0^1 x^2 chi(x) dx on every u_i.
 
@@ -143,12 +149,46 @@ def ik_gradient(ch, L):
     return out
 
 
-def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad"):
-    """Steps 1-5: (u~ at targets, grad u~ at targets, 1/2 sum_k p_k |bh_k|^2)."""
+def influence_virial(L, n_f, r_c, split, window):
+    """p'_k of the spectral virial (FFT order, p'_0 = 0): the derivative of
+    Shat(xi) = chihat(r_c xi)/xi^2 with respect to ln xi, over L^3 Phi^2 Phi^2
+    Phi^2, i.e. (r_c xi chihat'(r_c xi) - 2 chihat(r_c xi)) / xi^2 / den."""
+    k = np.fft.fftfreq(n_f, d=1.0 / n_f)
+    Phi = window.Phi(2.0 * math.pi * k / n_f)
+    k2 = (k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2).astype(np.int64)
+    uniq, inv = np.unique(k2, return_inverse=True)
+    xi = 2.0 * math.pi * np.sqrt(uniq.astype(np.float64)) / L
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(uniq > 0, (r_c * xi * split.dchihat(r_c * xi) - 2.0 * split.chihat(r_c * xi)) / xi ** 2, 0.0)
+    d = d[inv.reshape(k2.shape)]
+    den = L ** 3 * (Phi[:, None, None] * Phi[None, :, None] * Phi[None, None, :]) ** 2
+    return d / den
+
+
+def spectral_virial(bh, p, pv, n_f):
+    """sum_k 1/2 |bh_k|^2 [p_k delta + p'_k k k^T / |k|^2] (3 x 3)."""
+    k = np.fft.fftfreq(n_f, d=1.0 / n_f)
+    K = np.stack(np.meshgrid(k, k, k, indexing="ij"))         # (3, n, n, n)
+    k2 = np.sum(K * K, axis=0)
+    a = 0.5 * np.abs(bh) ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(k2 > 0, a * pv / k2, 0.0)
+    W = np.eye(3) * float(np.sum(a * p))
+    for i in range(3):
+        for j in range(3):
+            W[i, j] += float(np.sum(t * K[i] * K[j]))
+    return W
+
+
+def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad", virial=None):
+    """Steps 1-5: (u~ at targets, grad u~ at targets, 1/2 sum_k p_k |bh_k|^2).
+    With a dict `virial`, its key "spectral" receives the spectral virial."""
     b = spread(pos, q, L, n_f, window)
     bh = np.fft.ifftn(b) * n_f ** 3                           # exp(+2 pi i k.l/n_f)
     p = influence(L, n_f, r_c, split, window)
     fourier_energy = 0.5 * float(np.sum(p * np.abs(bh) ** 2))
+    if virial is not None:
+        virial["spectral"] = spectral_virial(bh, p, influence_virial(L, n_f, r_c, split, window), n_f)
     ch = p * bh
     cgrid = np.fft.fftn(ch).real                              # exp(-2 pi i k.l/n_f)
     idx, w, dw = stencil(pos[targets], L, n_f, window)
@@ -176,12 +216,14 @@ def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad"):
     return u, grad, fourier_energy
 
 
-def near_field(pos, q, L, r_c, split, targets):
+def near_field(pos, q, L, r_c, split, targets, virial=None):
     """Local part (Eq. localpart) and its forces at the targets.
 
     Pairs closer than r_c (strictly) under the minimum image, r_c < L/2.
     u^l_i += q_j (1 - g(x)) / (4 pi r),  x = r / r_c
     F^l_i += q_i q_j [(1 - g(x))/r^2 + chi(x)/(r_c r)] / (4 pi) * (r_i - r_j)/r
+    With a dict `virial`, its key "local" receives 1/2 sum over the targets'
+    pairs of F_ij d_ij^T (the local virial when every atom is a target).
     """
     if not r_c < 0.5 * L:
         raise ValueError("r_c must be smaller than L/2")
@@ -190,6 +232,7 @@ def near_field(pos, q, L, r_c, split, targets):
     tree = cKDTree(pos, boxsize=L)
     u = np.zeros(len(targets))
     f = np.zeros((len(targets), 3))
+    W = np.zeros((3, 3))
     for t_i, i in enumerate(targets):
         js = np.asarray(tree.query_ball_point(pos[i], r_c), dtype=np.int64)
         js = js[js != i]
@@ -203,6 +246,10 @@ def near_field(pos, q, L, r_c, split, targets):
         u[t_i] = np.sum(q[js] * omg / (4.0 * math.pi * r))
         mag = (omg / r ** 2 + split.chi(x) / (r_c * r)) / (4.0 * math.pi)
         f[t_i] = q[i] * np.sum((q[js] * mag / r)[:, None] * d, axis=0)
+        if virial is not None:
+            W += 0.5 * q[i] * (d.T * (q[js] * mag / r)) @ d
+    if virial is not None:
+        virial["local"] = W
     return u, f
 
 
@@ -220,15 +267,20 @@ def esp(pos, q, L, p: ESPParams, targets=None):
     tgt = np.arange(n) if all_atoms else np.asarray(targets, dtype=np.int64)
     split = p.split()
     window = p.si_window()
-    u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt, p.diff)
-    u_l, f_l = near_field(pos, q, L, p.r_c, split, tgt)
+    parts = {} if all_atoms else None
+    u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt, p.diff, parts)
+    u_l, f_l = near_field(pos, q, L, p.r_c, split, tgt, parts)
     self_term = q[tgt] * split.chi0 / (4.0 * math.pi * p.r_c)
     Q = float(np.sum(q))
     background = -(Q / L ** 3) * 0.5 * p.r_c ** 2 * split.second_moment()
     u = u_s + u_l - self_term + background
     f = -q[tgt, None] * grad_s + f_l
     energy = 0.5 * float(np.dot(q, u)) if all_atoms else None
-    return dict(energy=energy, potential=u, forces=f, fourier_energy=e_fourier,
+    virial = None
+    if all_atoms:
+        e_bg = 0.5 * Q * background
+        virial = parts["spectral"] + parts["local"] + e_bg * np.eye(3)
+    return dict(energy=energy, potential=u, forces=f, fourier_energy=e_fourier, virial=virial,
                 spectral_potential=u_s, spectral_forces=-q[tgt, None] * grad_s,
                 local_potential=u_l, local_forces=f_l, self_term=self_term,
                 indices=tgt, params=p)

@@ -16,6 +16,9 @@ erfc(g r_cut) <= acc); the k-space sum runs over the cube |k_a| <= K with K
 chosen so exp(-xi^2/(4g^2)) <= acc at the cube face. erfc comes from SciPy.
 Structure factors are assembled with matrix products over per-axis phase
 tables (a library matmul used as a step; no reordering of the sum itself).
+The virial W_ab = -dE/d eps_ab (homogeneous deformation of atoms and box)
+uses the textbook forms: real-space pair terms, reciprocal
+E_k [delta_ab - 2 (1 + xi^2/(4 g^2)) xi_a xi_b / xi^2], background E_bg delta_ab.
 """
 from __future__ import annotations
 
@@ -35,10 +38,12 @@ def ewald_parameters(L: float, acc: float = 1e-16) -> tuple[float, float, int]:
 
 
 def _real_space(pos, q, L, g, r_cut, targets, chunk=256):
-    """Minimum-image erfc sum for the target atoms (all j != i)."""
+    """Minimum-image erfc sum for the target atoms (all j != i); also
+    1/2 sum_i sum_j F_ij d_ij^T over the targets' pairs (virial)."""
     n_t = len(targets)
     u = np.zeros(n_t)
     f = np.zeros((n_t, 3))
+    W = np.zeros((3, 3))
     for s in range(0, n_t, chunk):
         idx = targets[s:s + chunk]
         d = pos[idx, None, :] - pos[None, :, :]            # r_i - r_j
@@ -54,7 +59,8 @@ def _real_space(pos, q, L, g, r_cut, targets, chunk=256):
         dl = (ec / r + 2.0 * g / math.sqrt(math.pi) * np.exp(-(g * r) ** 2)) / (4.0 * math.pi * r * r)
         coef = np.where(keep, dl, 0.0) * q[None, :]
         f[s:s + chunk] = q[idx, None] * np.einsum("ij,ijk->ik", coef, d)
-    return u, f
+        W += 0.5 * np.einsum("i,ij,ija,ijb->ab", q[idx], coef, d, d)
+    return u, f, W
 
 
 def _k_space(pos, q, L, g, K, targets, want_energy):
@@ -72,6 +78,7 @@ def _k_space(pos, q, L, g, K, targets, want_energy):
     u = np.zeros(n_t)
     f = np.zeros((n_t, 3))
     energy = 0.0
+    W = np.zeros((3, 3))
     for kx in range(0, K + 1):
         k2 = kx * kx + ky * ky + kz * kz
         xi2 = (tw ** 2) * k2
@@ -83,7 +90,16 @@ def _k_space(pos, q, L, g, K, targets, want_energy):
         exy = ex[:, kx, None] * ey                           # (N, 2K+1)
         S = (exy * q[:, None]).T @ ez                        # S[ky, kz]
         if want_energy:
-            energy += wgt * 0.5 / V * float(np.sum(amp * np.abs(S) ** 2))
+            ek = wgt * 0.5 / V * amp * np.abs(S) ** 2
+            energy += float(np.sum(ek))
+            # textbook reciprocal virial: E_k [delta - 2 (1 + xi^2/(4 g^2)) xi xi^T / xi^2]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                fk = np.where(k2 > 0, ek * 2.0 * (1.0 + xi2 / (4.0 * g * g)) / k2, 0.0)
+            kv = (kx * np.ones_like(ky), ky, kz)
+            W += np.eye(3) * float(np.sum(ek))
+            for a in range(3):
+                for b in range(3):
+                    W[a, b] -= float(np.sum(fk * kv[a] * kv[b]))
         # e^{-i xi.r_i} S summed against amp for the targets
         A = amp * S                                          # (2K+1, 2K+1)
         et = np.conj(exy[targets])                           # (n_t, 2K+1)
@@ -100,7 +116,7 @@ def _k_space(pos, q, L, g, K, targets, want_energy):
         f[:, 1] += -wgt / V * tw * valy.imag
         f[:, 2] += -wgt / V * tw * valz.imag
     f *= q[targets, None]
-    return u, f, energy
+    return u, f, energy, W
 
 
 def ewald(pos, q, L, acc: float = 1e-16, targets=None, g: float | None = None):
@@ -121,12 +137,15 @@ def ewald(pos, q, L, acc: float = 1e-16, targets=None, g: float | None = None):
         K = int(math.ceil(2.0 * g0 * math.sqrt(-math.log(acc)) * L / (2.0 * math.pi)))
     all_atoms = targets is None
     tgt = np.arange(n) if all_atoms else np.asarray(targets, dtype=np.int64)
-    u_r, f_r = _real_space(pos, q, L, g0, r_cut, tgt)
-    u_k, f_k, e_k = _k_space(pos, q, L, g0, K, tgt, all_atoms)
+    u_r, f_r, w_r = _real_space(pos, q, L, g0, r_cut, tgt)
+    u_k, f_k, e_k, w_k = _k_space(pos, q, L, g0, K, tgt, all_atoms)
     Q = float(np.sum(q))
     V = L ** 3
     u = u_r + u_k - q[tgt] * g0 / (2.0 * math.pi ** 1.5) - Q / (4.0 * V * g0 * g0)
     f = f_r + f_k
     energy = 0.5 * float(np.dot(q, u)) if all_atoms else None
+    # virial W_ab = -dE/d eps_ab: real-space pairs, reciprocal modes, and the
+    # background energy -Q^2/(8 V g^2) (proportional to 1/V); self term 0
+    virial = w_r + w_k - Q * Q / (8.0 * V * g0 * g0) * np.eye(3) if all_atoms else None
     return dict(energy=energy, potential=u, forces=f, g=g0, r_cut=r_cut, K=K,
-                indices=tgt, k_energy=e_k if all_atoms else None)
+                indices=tgt, k_energy=e_k if all_atoms else None, virial=virial)

@@ -147,6 +147,14 @@ class PSWFSplit:
         out = np.cos(np.outer(flat, _GL01_X)) @ (_GL01_W * vals)
         return out.reshape(kappa.shape)
 
+    def dchihat(self, kappa):
+        """d chihat / d kappa = -int_0^1 x chi(x) sin(kappa x) dx (same rule)."""
+        kappa = np.asarray(kappa, dtype=np.float64)
+        vals = self.chi(_GL01_X)
+        flat = kappa.reshape(-1)
+        out = -np.sin(np.outer(flat, _GL01_X)) @ (_GL01_W * _GL01_X * vals)
+        return out.reshape(kappa.shape)
+
     def second_moment(self) -> float:
         """int_0^1 x^2 chi(x) dx (enters the neutralising-background energy)."""
         return float(np.sum(_GL01_W * _GL01_X ** 2 * self.chi(_GL01_X)))
@@ -184,6 +192,10 @@ class GaussianSplit:
     def chihat(self, kappa):
         kappa = np.asarray(kappa, dtype=np.float64)
         return np.exp(-kappa * kappa / (4.0 * self.alpha))
+
+    def dchihat(self, kappa):
+        kappa = np.asarray(kappa, dtype=np.float64)
+        return -kappa / (2.0 * self.alpha) * np.exp(-kappa * kappa / (4.0 * self.alpha))
 
     def second_moment(self) -> float:
         return 1.0 / (2.0 * self.alpha)          # int_0^inf x^2 chi

@@ -558,14 +558,18 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   ESP_CU(L::scale(p->d_desc, p->nsys, p->F, p->d_spec, (const real*)p->d_tabs, p->d_fourier, p->d_spec_ik,
                   p->spec_total, st));
   rec(p, 6, st);
+  // energy only (no forces, no potentials): E needs the spectral sum of the
+  // scale kernel and the local part, not the inverse FFT and the gather
+  const bool atom_outputs = outF != nullptr || outU != nullptr;
   for (Bucket& b : p->buckets) {
+    if (!atom_outputs) break;
     if (sizeof(real) == 4)
       ESP_FFT(cufftExecC2R(b.inv, (cufftComplex*)p->d_spec + b.spec0, (cufftReal*)p->d_grid + b.grid0));
     else
       ESP_FFT(cufftExecZ2D(b.inv, (cufftDoubleComplex*)p->d_spec + b.spec0,
                            (cufftDoubleReal*)p->d_grid + b.grid0));
   }
-  if (p->ik) {
+  if (p->ik && atom_outputs) {
     // ik method: the three gradient spectra back to the grid
     for (int a = 0; a < 3; ++a) {
       for (Bucket& b : p->buckets) {
@@ -578,12 +582,14 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
     }
   }
   rec(p, 7, st);
-  ESP_CU(L::gather(p->P, p->d_desc, p->d_work, p->n_work, p->smem, p->d_atoms, p->d_start,
-                   (const real*)p->d_grid, (const real*)p->d_grid_ik, p->grid_total, p->d_far, si, p->d_err, st));
+  if (atom_outputs)
+    ESP_CU(L::gather(p->P, p->d_desc, p->d_work, p->n_work, p->smem, p->d_atoms, p->d_start,
+                     (const real*)p->d_grid, (const real*)p->d_grid_ik, p->grid_total, p->d_far, si, p->d_err, st));
   rec(p, 8, st);
   // join and finish
   if (!serial) ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
-  ESP_CU(L::finalize(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_perm, p->d_far, p->d_near,
+  ESP_CU(L::finalize(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_perm,
+                     atom_outputs ? p->d_far : nullptr, p->d_near,
                      outF, outU, out_double, p->d_partials, st));
   ESP_CU(espk::launch_energy(p->d_desc, p->nsys, p->d_fourier, p->F, p->d_partials, p->n_chunks,
                              p->d_chunk_first, p->d_consts, p->d_eout, outE, st));

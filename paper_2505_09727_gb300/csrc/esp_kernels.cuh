@@ -997,7 +997,7 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
     if (local < S.n_atoms) {
       const long long i = S.atom0 + local;
       const float q = atom_q(atoms[i]);
-      const typename Types<real>::res f = far[i];
+      const typename Types<real>::res f = far ? far[i] : typename Types<real>::res{};
       const typename Types<real>::res nr = nearres[i];
       const uint32_t o = perm[i];
       const float pre = S.prefactor_f;
@@ -1037,7 +1037,7 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
     const long long i = S.atom0 + local;
     const typename Types<real>::atom at = atoms[i];
     const double q = (double)atom_q(at);
-    const typename Types<real>::res f = far[i];
+    const typename Types<real>::res f = far ? far[i] : typename Types<real>::res{};
     const typename Types<real>::res nr = nearres[i];
     const uint32_t o = perm[i];
     const double u = (double)f.x + (double)nr.x - q * S.self_coef + S.bg_shift;

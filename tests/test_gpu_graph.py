@@ -71,3 +71,28 @@ def test_device_outputs_alternating_buffers(esp):
             assert abs(float(e.cpu()[0]) - e0) <= FP32_PARITY * abs(e0)
     finally:
         esp.esp_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_energy_only_matches_full_compute(esp, prec):
+    """Forces and potential NULL: the energy alone, from the spectral sum of
+    the scale kernel and the local part (no inverse FFT, no gather)."""
+    import torch
+    dev = torch.device("cuda:0")
+    precision = esp.ESP_FP32 if prec == "fp32" else esp.ESP_FP64
+    s = inputs.spce_water(1500, seed=43)
+    h = esp.esp_plan(s.L, s.n, 1e-4, r_c=1.0, precision=precision)
+    try:
+        esp.esp_set_charges(h, torch.tensor(s.q, device=dev))
+        esp.esp_set_positions(h, torch.tensor(s.pos, device=dev))
+        e_full = torch.zeros(1, dtype=torch.float64, device=dev)
+        f = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
+        esp.esp_compute(h, e_full, f, None)
+        for _ in range(3):                       # direct, captured, replayed
+            e = torch.zeros(1, dtype=torch.float64, device=dev)
+            esp.esp_compute(h, e, None, None)
+            torch.cuda.synchronize()
+            bound = 1e-6 if prec == "fp32" else 1e-13
+            assert abs(float(e.cpu()[0]) - float(e_full.cpu()[0])) <= bound * abs(float(e_full.cpu()[0]))
+    finally:
+        esp.esp_destroy(h)
