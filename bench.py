@@ -326,6 +326,8 @@ def run_gpu(args, world, rank, local):
         extras["gaussian"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS)
         # the ik force method (Methods, step 5): three more inverse FFTs
         extras["ik"] = single_variant(args, local, stream, flush, s, diff=esp.ESP_DIFF_IK)
+        # the same compute with the virial (local pair terms and spectral modes)
+        extras["virial"] = single_variant(args, local, stream, flush, s, virial=1)
         # the "Default" comparator of Table 1: Gaussian split, cardinal B-spline window
         extras["default_bspline"] = single_variant(args, local, stream, flush, s, kernel=esp.ESP_KERNEL_GAUSS,
                                                    window=esp.ESP_WINDOW_BSPLINE)

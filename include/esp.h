@@ -118,7 +118,11 @@ typedef struct {
                           gradients interpolated with the SI weights; the
                           Nyquist component of the differentiated axis is
                           zero). Potentials and energies are the same.      */
-  int reserved[4];
+  int virial;          /* 1: every compute also forms the virial W_ab =
+                          -dE/d eps_ab (esp_last_virial); needs the default
+                          local-part kernel (near_variant 0 or 4 in FP32, 0
+                          or 1 in FP64)                                       */
+  int reserved[3];
 } esp_plan_opts;
 
 /* Parameters a plan chose (esp_plan_info). */
@@ -138,7 +142,8 @@ typedef struct {
   size_t device_bytes;     /* device memory held by the plan                 */
   int window;              /* ESP_WINDOW_PSWF or ESP_WINDOW_BSPLINE          */
   int diff;                /* ESP_DIFF_AD or ESP_DIFF_IK                     */
-  int reserved[2];
+  int virial;              /* 1 when computes form the virial                */
+  int reserved[1];
 } esp_plan_params;
 
 /* Fill opts with defaults (all planner choices, FP32, PSWF, device 0). */
@@ -196,6 +201,18 @@ esp_status esp_phase_times(esp_plan_t plan, float* ms, int n);
 
 /* Spectral energy 1/2 sum_k p_k |bh_k|^2 of the last compute (host double). */
 esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* e_gather);
+
+/* Virial of the last compute of a plan made with opts.virial = 1: W_ab =
+ * -dE/d eps_ab under the homogeneous deformation r -> (1 + eps) r of atoms
+ * and box (the grid deforms with the box), in energy units (times the
+ * prefactor); pressure = (kinetic term + trace W) / (3 V). Spectral part
+ * sum_k 1/2 |bh_k|^2 [p_k delta_ab + p'_k k_a k_b / |k|^2] with p'_k the
+ * derivative of Eq. pk's Shat with respect to ln|k|, local part the pair
+ * terms of Eq. localpart, and the neutralising background's energy on the
+ * diagonal. virial[6] receives (xx, yy, zz, xy, xz, yz) on the host; the
+ * call waits (bounded) for the compute. ESP_ERR_NOT_READY without
+ * opts.virial or before the first compute. */
+esp_status esp_last_virial(esp_plan_t plan, double* virial);
 
 esp_status esp_destroy(esp_plan_t plan);
 
@@ -260,6 +277,9 @@ esp_status esp_batch_synchronize(esp_batch_t batch);
  * step runs as direct launches instead of the graph. */
 esp_status esp_batch_set_timing(esp_batch_t batch, int enable);
 esp_status esp_batch_phase_times(esp_batch_t batch, float* ms, int n);
+/* Virials of the last batch compute (opts.virial = 1): virial[6 * s + c],
+ * c = xx, yy, zz, xy, xz, yz, for every system s (as esp_last_virial). */
+esp_status esp_batch_last_virial(esp_batch_t batch, double* virial);
 esp_status esp_batch_destroy(esp_batch_t batch);
 
 /* ------------------------------------------------------------------ server

@@ -166,9 +166,15 @@ def influence_virial(L, n_f, r_c, split, window):
 
 
 def spectral_virial(bh, p, pv, n_f):
-    """sum_k 1/2 |bh_k|^2 [p_k delta + p'_k k k^T / |k|^2] (3 x 3)."""
+    """sum_k 1/2 |bh_k|^2 [p_k delta + p'_k k k^T / |k|^2] (3 x 3).
+
+    A Nyquist index k_a = -n_f/2 stands for both aliases +-n_f/2; the
+    off-diagonal products k_a k_b (a != b) take their average, zero
+    (reading for even n_f; the diagonal k_a^2 is the same for both)."""
     k = np.fft.fftfreq(n_f, d=1.0 / n_f)
     K = np.stack(np.meshgrid(k, k, k, indexing="ij"))         # (3, n, n, n)
+    ks = np.where(k == -(n_f // 2), 0.0, k) if n_f % 2 == 0 else k
+    Ks = np.stack(np.meshgrid(ks, ks, ks, indexing="ij"))
     k2 = np.sum(K * K, axis=0)
     a = 0.5 * np.abs(bh) ** 2
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -176,7 +182,7 @@ def spectral_virial(bh, p, pv, n_f):
     W = np.eye(3) * float(np.sum(a * p))
     for i in range(3):
         for j in range(3):
-            W[i, j] += float(np.sum(t * K[i] * K[j]))
+            W[i, j] += float(np.sum(t * K[i] * K[j])) if i == j else float(np.sum(t * Ks[i] * Ks[j]))
     return W
 
 

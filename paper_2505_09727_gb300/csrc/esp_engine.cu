@@ -129,6 +129,11 @@ struct esp_plan_s {
   double* d_partials = nullptr;
   double* d_consts = nullptr;
   double* d_eout = nullptr;      // per system: E, E_fourier, E_gather
+  double* d_vpart = nullptr;     // virial: spectral partials [nsys][F][6]
+  double* d_vloc = nullptr;      // virial: local part [nsys][6] (atomics)
+  double* d_vout = nullptr;      // virial: totals [nsys][6]
+  bool virial = false;
+  bool computed = false;         // a compute has been enqueued
   double* d_energy = nullptr;    // per system: E (batch output)
   void* d_outF = nullptr;        // staging for outputs (FP64)
   void* d_outU = nullptr;
@@ -291,7 +296,7 @@ void layout(esp_plan_s* p, std::vector<int2>& chunks, std::vector<int>& chunk_fi
     for (int b = 0; b < hp.n_bricks; ++b) work.push_back(make_int2(s, b));
     atom0 += d.n_atoms;
     cell0 += hp.n_keys;
-    tab0 += (long long)(hp.G.size() + hp.W.size());
+    tab0 += (long long)(hp.G.size() + hp.W.size() + hp.H.size());
     col0 += (long long)d.n_c * d.n_c;
     p->smem = std::max(p->smem, (size_t)d.tpz * d.T * rb);
     max_spec = std::max(max_spec, hp.spec_elems);
@@ -348,6 +353,12 @@ esp_status build_buffers(esp_plan_s* p) {
   ESP_TRY(dev_alloc_t(p, &p->d_partials, 2 * std::max(1, p->n_chunks)));
   ESP_TRY(dev_alloc_t(p, &p->d_consts, 2 * n));
   ESP_TRY(dev_alloc_t(p, &p->d_eout, 3 * n));
+  p->virial = p->hps[0].info.virial != 0;
+  if (p->virial) {
+    ESP_TRY(dev_alloc_t(p, &p->d_vpart, (size_t)n * p->F * 6));
+    ESP_TRY(dev_alloc_t(p, &p->d_vloc, (size_t)n * 6));
+    ESP_TRY(dev_alloc_t(p, &p->d_vout, (size_t)n * 6));
+  }
   ESP_TRY(dev_alloc_t(p, &p->d_energy, n));
   ESP_TRY(dev_alloc(p, &p->d_outF, (size_t)N * 3 * sizeof(double)));
   ESP_TRY(dev_alloc(p, &p->d_outU, (size_t)N * sizeof(double)));
@@ -366,6 +377,7 @@ esp_status build_buffers(esp_plan_s* p) {
     const long long t0 = p->descs[s].tab0;
     for (size_t i = 0; i < hp.G.size(); ++i) tabs[t0 + i] = (real)hp.G[i];
     for (size_t i = 0; i < hp.W.size(); ++i) tabs[t0 + hp.G.size() + i] = (real)hp.W[i];
+    for (size_t i = 0; i < hp.H.size(); ++i) tabs[t0 + hp.G.size() + hp.W.size() + i] = (real)hp.H[i];
   }
   ESP_CU(cudaMemcpyAsync(p->d_desc, p->descs.data(), n * sizeof(espk::SysDesc), cudaMemcpyHostToDevice, p->st));
   if (p->n_chunks)
@@ -527,16 +539,17 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
     ESP_CU(cudaEventRecord(p->ev_scat, st));
     ESP_CU(cudaStreamWaitEvent(st2, p->ev_scat, 0));
   }
+  if (p->virial) ESP_CU(cudaMemsetAsync(p->d_vloc, 0, (size_t)p->nsys * 6 * sizeof(double), st2));
   if (hp.near_clusters) {
     // the pair kernel alone between the local-part events
     rec(p, 9, st2);
     ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
                             p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
-                            hp.near_half, p->N, 1, p->d_err, st2));
+                            hp.near_half, p->N, 1, p->d_err, st2, p->d_vloc));
   } else {
     rec(p, 9, st2);
     ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
-                   hp.near_nc, hp.near_queued, st2));
+                   hp.near_nc, hp.near_queued, st2, p->d_vloc));
   }
   rec(p, 10, st2);
   if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
@@ -556,7 +569,7 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   }
   rec(p, 5, st);
   ESP_CU(L::scale(p->d_desc, p->nsys, p->F, p->d_spec, (const real*)p->d_tabs, p->d_fourier, p->d_spec_ik,
-                  p->spec_total, st));
+                  p->spec_total, p->d_vpart, st));
   rec(p, 6, st);
   // energy only (no forces, no potentials): E needs the spectral sum of the
   // scale kernel and the local part, not the inverse FFT and the gather
@@ -592,7 +605,9 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
                      atom_outputs ? p->d_far : nullptr, p->d_near,
                      outF, outU, out_double, p->d_partials, st));
   ESP_CU(espk::launch_energy(p->d_desc, p->nsys, p->d_fourier, p->F, p->d_partials, p->n_chunks,
-                             p->d_chunk_first, p->d_consts, p->d_eout, outE, st));
+                             p->d_chunk_first, p->d_consts, p->d_eout, outE, st, p->d_vpart, p->d_vloc,
+                             p->d_vout));
+  p->computed = true;
   rec(p, 11, st);
   return ESP_OK;
 }
@@ -782,7 +797,7 @@ esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const
   const size_t ab = o.precision == ESP_FP32 ? 16 : 32;
   size_t bytes = (size_t)N * (24 + 2 * ab + 4 * 3 + rb + 8 + 2 * ab + 32) +
                  (size_t)hp.n_keys * 8 + (size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb +
-                 (hp.G.size() + hp.W.size()) * rb;
+                 (hp.G.size() + hp.W.size() + hp.H.size()) * rb;
   if (o.diff == ESP_DIFF_IK) bytes += 3 * ((size_t)hp.grid_elems * rb + (size_t)hp.spec_elems * 2 * rb);
   if (hp.near_clusters) {
     // cluster counts, offsets and lists of the local part
@@ -891,6 +906,15 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
   p->phase_ms[8] = el(2, 11);             // whole compute
   for (int i = 0; i < n && i < kPhases; ++i) ms[i] = p->phase_ms[i];
   return ESP_OK;
+}
+
+esp_status esp_last_virial(esp_plan_t p, double* virial) {
+  if (!p || !virial) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  if (!p->virial) return fail(ESP_ERR_NOT_READY, "the plan was made without opts.virial");
+  if (!p->computed) return fail(ESP_ERR_NOT_READY, "no compute yet");
+  DeviceGuard g(p->device);
+  ESP_CU(cudaMemcpyAsync(virial, p->d_vout, 6 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  return wait_stream(p, p->st);
 }
 
 esp_status esp_last_spectral_energy(esp_plan_t p, double* e_fourier, double* e_gather) {
@@ -1154,6 +1178,16 @@ esp_status esp_batch_phase_times(esp_batch_t b, float* ms, int n) {
   esp_plan_s* p = pool_of(b);
   if (!p) return fail(ESP_ERR_INVALID_ARG, "NULL batch");
   return esp_phase_times(p, ms, n);
+}
+
+esp_status esp_batch_last_virial(esp_batch_t b, double* virial) {
+  esp_plan_s* p = pool_of(b);
+  if (!p || !virial) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  if (!p->virial) return fail(ESP_ERR_NOT_READY, "the batch was made without opts.virial");
+  if (!p->computed) return fail(ESP_ERR_NOT_READY, "no compute yet");
+  DeviceGuard g(p->device);
+  ESP_CU(cudaMemcpyAsync(virial, p->d_vout, (size_t)p->nsys * 6 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  return wait_stream(p, p->st);
 }
 
 esp_status esp_batch_destroy(esp_batch_t b) {

@@ -34,9 +34,10 @@ cudaError_t launch_scan(const uint32_t* count, uint32_t* start, uint32_t* tile_s
 
 cudaError_t launch_energy(const SysDesc* sys, int nsys, const double* fourier, int n_fourier_blocks,
                           const double* partials, int n_chunks, const int* chunk_first,
-                          const double* consts, double* out, double* user_energy, cudaStream_t st) {
+                          const double* consts, double* out, double* user_energy, cudaStream_t st,
+                          const double* vpart, const double* vloc, double* vout) {
   k_energy<<<nsys, 1024, 0, st>>>(sys, fourier, n_fourier_blocks, partials, n_chunks, chunk_first,
-                                 consts, out, user_energy);
+                                 consts, out, user_energy, vpart, vloc, vout);
   return cudaGetLastError();
 }
 

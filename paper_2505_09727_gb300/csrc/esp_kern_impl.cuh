@@ -154,10 +154,10 @@ bool Launch<ESP_REAL>::supports_P(int P) { return P >= ESP_P_MIN && P <= ESP_P_M
 template <>
 cudaError_t Launch<ESP_REAL>::scale(const SysDesc* sys, int nsys, int nblk, void* spec,
                                     const ESP_REAL* tabs, double* partials, void* spec_ik,
-                                    long long spec_total, cudaStream_t st) {
+                                    long long spec_total, double* vpart, cudaStream_t st) {
   using C = typename Types<ESP_REAL>::cplx;
   dim3 grid(nblk, nsys);
-  k_scale<ESP_REAL><<<grid, 256, 0, st>>>(sys, (C*)spec, tabs, partials, (C*)spec_ik, spec_total);
+  k_scale<ESP_REAL><<<grid, 256, 0, st>>>(sys, (C*)spec, tabs, partials, (C*)spec_ik, spec_total, vpart);
   return cudaGetLastError();
 }
 
@@ -165,21 +165,24 @@ template <>
 cudaError_t Launch<ESP_REAL>::near(const SysDesc* sys, const int2* chunks, int n_chunks,
                                    const void* atoms, const void* rel, const uint32_t* start,
                                    void* nearres, const NearCoef<ESP_REAL>& nc, int terms,
-                                   bool queued, cudaStream_t st) {
+                                   bool queued, cudaStream_t st, double* vloc) {
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
+  if (vloc && queued) return cudaErrorNotSupported;     // the virial is formed in the inline form
   decltype(&k_near<ESP_REAL, ESP_NEAR_SHORT, true>) kern = nullptr;
   // fewer terms run on the shorter instance: the unused coefficients are zero
   if (terms <= ESP_NEAR_SHORT)
-    kern = queued ? k_near<ESP_REAL, ESP_NEAR_SHORT, true> : k_near<ESP_REAL, ESP_NEAR_SHORT, false>;
+    kern = vloc ? k_near<ESP_REAL, ESP_NEAR_SHORT, false, true>
+                : queued ? k_near<ESP_REAL, ESP_NEAR_SHORT, true> : k_near<ESP_REAL, ESP_NEAR_SHORT, false>;
   else if (terms == Deg<ESP_REAL>::nr)
-    kern = queued ? k_near<ESP_REAL, Deg<ESP_REAL>::nr, true> : k_near<ESP_REAL, Deg<ESP_REAL>::nr, false>;
+    kern = vloc ? k_near<ESP_REAL, Deg<ESP_REAL>::nr, false, true>
+                : queued ? k_near<ESP_REAL, Deg<ESP_REAL>::nr, true> : k_near<ESP_REAL, Deg<ESP_REAL>::nr, false>;
   if (!kern) return cudaErrorInvalidValue;
   const size_t smem = queued ? kNearQueueBytes : 0;
   cudaError_t e = detail::allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_chunks, kChunk, smem, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc);
+  kern<<<n_chunks, kChunk, smem, st>>>(sys, chunks, (const A*)atoms, (const R*)rel, start, (R*)nearres, nc, vloc);
   return cudaGetLastError();
 }
 

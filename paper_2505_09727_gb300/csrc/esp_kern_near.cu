@@ -13,7 +13,7 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
                                          const NearCoef<float>& nc, int terms, uint32_t* ccount,
                                          uint32_t* cstart, uint32_t* ctiles, int2* cmap, int2* catoms,
                                          long long cmap_cap, bool half, long long n_atoms, int stage,
-                                         int* err, cudaStream_t st) {
+                                         int* err, cudaStream_t st, double* vloc) {
   if (n_cols == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   if (!(stage & 1)) {
@@ -25,12 +25,13 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
     k_cluster_expand<<<cb, 256, 0, st>>>(sys, nsys, n_cols, ccount, cstart, start, cmap, catoms, cmap_cap, err);
     if (stage == 2) return cudaGetLastError();
   }
+  if (vloc && !half) return cudaErrorNotSupported;         // the virial is formed in the half form
   decltype(&k_near_cluster<10, false>) kern = nullptr;
   switch (terms) {
-    case 8: kern = half ? k_near_cluster<8, true> : k_near_cluster<8, false>; break;
-    case 9: kern = half ? k_near_cluster<9, true> : k_near_cluster<9, false>; break;
-    case 10: kern = half ? k_near_cluster<10, true> : k_near_cluster<10, false>; break;
-    case 12: kern = half ? k_near_cluster<12, true> : k_near_cluster<12, false>; break;
+    case 8: kern = vloc ? k_near_cluster<8, true, true> : half ? k_near_cluster<8, true> : k_near_cluster<8, false>; break;
+    case 9: kern = vloc ? k_near_cluster<9, true, true> : half ? k_near_cluster<9, true> : k_near_cluster<9, false>; break;
+    case 10: kern = vloc ? k_near_cluster<10, true, true> : half ? k_near_cluster<10, true> : k_near_cluster<10, false>; break;
+    case 12: kern = vloc ? k_near_cluster<12, true, true> : half ? k_near_cluster<12, true> : k_near_cluster<12, false>; break;
     default: return cudaErrorInvalidValue;
   }
   if (half) {
@@ -40,8 +41,8 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
   }
   // persistent grid: as many blocks as fit on the device at once, each block
   // taking a contiguous run of clusters
-  static int blocks_full = 0, blocks_half = 0;
-  int& blocks = half ? blocks_half : blocks_full;
+  static int blocks_full = 0, blocks_half = 0, blocks_vir = 0;
+  int& blocks = vloc ? blocks_vir : half ? blocks_half : blocks_full;
   if (blocks == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -52,7 +53,7 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
   const long long need = (cmap_cap + kClusterWarps - 1) / kClusterWarps;
   const int grid = (int)std::min<long long>(blocks, std::max<long long>(1, need));
   kern<<<grid, kClusterWarps * 32, 0, st>>>(sys, cmap, catoms, cstart + n_cols, (const float4*)rel, start,
-                                           (float4*)nearres, nc, err);
+                                           (float4*)nearres, nc, err, vloc);
   return cudaGetLastError();
 }
 

@@ -533,7 +533,7 @@ template <typename real>
 __global__ void __launch_bounds__(256) k_scale(
     const SysDesc* __restrict__ sys, typename Types<real>::cplx* __restrict__ spec,
     const real* __restrict__ tabs, double* __restrict__ partials,
-    typename Types<real>::cplx* __restrict__ spec_ik, long long spec_total) {
+    typename Types<real>::cplx* __restrict__ spec_ik, long long spec_total, double* __restrict__ vpart) {
   __shared__ double red[32];
   const SysDesc& S = sys[blockIdx.y];
   const int n = S.n_f, nh = n / 2 + 1, half = n / 2;
@@ -541,7 +541,9 @@ __global__ void __launch_bounds__(256) k_scale(
   typename Types<real>::cplx* sp = spec + S.spec0;
   const real* G = tabs + S.tab0;
   const real* W = G + S.gsize;
+  const real* H = W + (half + 1);                 // virial table (R27)
   double e = 0.0;
+  double vir[6] = {0, 0, 0, 0, 0, 0};             // xx, yy, zz, xy, xz, yz
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int kx = (int)(idx % nh);
@@ -554,6 +556,21 @@ __global__ void __launch_bounds__(256) k_scale(
     typename Types<real>::cplx v = sp[idx];
     const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
     e += wgt * (double)p * ((double)v.x * v.x + (double)v.y * v.y);
+    if (vpart && m > 0) {
+      // virial of the mode: 1/2 |bh|^2 W W W [G delta + H k k^T / |k|^2]
+      const double a = 0.5 * wgt * (double)(__ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz))) *
+                       ((double)v.x * v.x + (double)v.y * v.y);
+      const double g = a * (double)__ldg(G + m), hm = a * (double)__ldg(H + m) / m;
+      // a Nyquist index stands for both aliases +-n_f/2: zero in the
+      // off-diagonal products (their average)
+      const int sx = kx == half ? 0 : kx, sy = kyi == half ? 0 : ky, sz = kzi == half ? 0 : kz;
+      vir[0] += g + hm * kx * kx;
+      vir[1] += g + hm * ky * ky;
+      vir[2] += g + hm * kz * kz;
+      vir[3] += hm * sx * sy;
+      vir[4] += hm * sx * sz;
+      vir[5] += hm * sy * sz;
+    }
     v.x *= p;
     v.y *= p;
     sp[idx] = v;
@@ -573,6 +590,12 @@ __global__ void __launch_bounds__(256) k_scale(
   }
   e = block_sum(e, red);
   if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * e;
+  if (vpart) {
+    for (int c = 0; c < 6; ++c) {
+      const double t = block_sum(vir[c], red);
+      if (threadIdx.x == 0) vpart[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 6 + c] = t;
+    }
+  }
 }
 
 // A6 (ik method): gather the potential and the three gradient grids with the
@@ -819,12 +842,17 @@ __device__ __forceinline__ void near_flush(const SysDesc& S, const typename Type
   }
 }
 
-template <typename real, int NC, bool QUEUE>
+// VIR (inline form only): also the local virial, per atom 1/2 q_i sum_j
+// fs_ij d d^T (every pair is met from both sides), summed over the warp and
+// added to vloc[6 * system + c] with FP64 atomics.
+template <typename real, int NC, bool QUEUE, bool VIR = false>
 __global__ void __launch_bounds__(kChunk) k_near(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
     const typename Types<real>::atom* __restrict__ atoms,
     const typename Types<real>::res* __restrict__ rel, const uint32_t* __restrict__ start,
-    typename Types<real>::res* __restrict__ nearres, const NearCoef<real> nc) {
+    typename Types<real>::res* __restrict__ nearres, const NearCoef<real> nc,
+    double* __restrict__ vloc = nullptr) {
+  static_assert(!(QUEUE && VIR), "the virial is formed in the inline form");
   __shared__ NearTabs tabs;
   extern __shared__ __align__(16) uint32_t queue_mem[];   // [warp][kQueueCap][32]
   const int2 ch = chunks[blockIdx.x];
@@ -873,6 +901,7 @@ __global__ void __launch_bounds__(kChunk) k_near(
   const int slab_min = -R * kSub, slab_max = (R + 1) * kSub - 1;
   const uint32_t* st = start + S.cell0;
   real pot = 0, fx = 0, fy = 0, fz = 0;
+  real vir[6] = {0, 0, 0, 0, 0, 0};
   int cnt = 0;
   for (int oy = -R; oy <= R; ++oy) {
     const int uy = cy + oy + kTabPad;
@@ -924,6 +953,14 @@ __global__ void __launch_bounds__(kChunk) k_near(
                 fx += fs * dx;
                 fy += fs * dy;
                 fz += fs * dz;
+                if constexpr (VIR) {
+                  vir[0] += fs * dx * dx;
+                  vir[1] += fs * dy * dy;
+                  vir[2] += fs * dz * dz;
+                  vir[3] += fs * dx * dy;
+                  vir[4] += fs * dx * dz;
+                  vir[5] += fs * dy * dz;
+                }
               } else if (cnt < kQueueCap) {
                 q[cnt * 32] = j;
                 ++cnt;
@@ -955,6 +992,16 @@ __global__ void __launch_bounds__(kChunk) k_near(
   }
   if (QUEUE)
     near_flush<real, NC>(S, ai, atoms, q, cnt, nc, rc2, inv_rc, inv_rc2x2, inv_rc3, pot, fx, fy, fz);
+  if constexpr (VIR) {
+    const double w = valid ? 0.5 * (double)ra.w / kFourPi : 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double t = w * (double)vir[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) atomicAdd(vloc + 6 * ch.x + c, t);
+    }
+  }
   if (!valid) return;
   const real qi = ra.w;
   const real k4 = real(1.0 / kFourPi);
@@ -1071,7 +1118,8 @@ __device__ inline void neumaier_add(double& s, double& c, double v) {
 static __global__ void __launch_bounds__(1024) k_energy(
     const SysDesc* __restrict__ sys, const double* __restrict__ fourier, int n_fourier_blocks,
     const double* __restrict__ partials, int n_chunks, const int* __restrict__ chunk_first,
-    const double* __restrict__ consts, double* __restrict__ out, double* __restrict__ user_energy) {
+    const double* __restrict__ consts, double* __restrict__ out, double* __restrict__ user_energy,
+    const double* __restrict__ vpart, const double* __restrict__ vloc, double* __restrict__ vout) {
   __shared__ double red[32];
   const int s = blockIdx.x;
   // a few plain FP64 additions per thread, then a pairwise tree over the
@@ -1100,6 +1148,17 @@ static __global__ void __launch_bounds__(1024) k_energy(
     out[3 * s + 1] = pre * tot[0];
     out[3 * s + 2] = pre * tot[2];
     if (user_energy) user_energy[s] = e;
+  }
+  if (vout) {
+    // virial: spectral partials, local sums, background energy on the diagonal
+    for (int c = 0; c < 6; ++c) {
+      double v = 0.0;
+      for (int j = threadIdx.x; j < n_fourier_blocks; j += blockDim.x)
+        v += vpart[((long long)s * n_fourier_blocks + j) * 6 + c];
+      v = block_sum(v, red);
+      if (threadIdx.x == 0)
+        vout[6 * s + c] = sys[s].prefactor * (v + vloc[6 * s + c] + (c < 3 ? consts[2 * s + 1] : 0.0));
+    }
   }
 }
 

@@ -20,8 +20,10 @@ struct Launch {
                             const SICoef<real>& si, int* err, cudaStream_t st);
   // spec_ik (nullable): the ik method's three gradient spectra, component
   // a at spec_ik + a * spec_total (the pool's half-spectrum length)
+  // vpart (nullable): spectral virial partials [nsys][nblk][6]
   static cudaError_t scale(const SysDesc* sys, int nsys, int nblk, void* spec, const real* tabs,
-                           double* partials, void* spec_ik, long long spec_total, cudaStream_t st);
+                           double* partials, void* spec_ik, long long spec_total, double* vpart,
+                           cudaStream_t st);
   // grids_ik (nullable): the ik method's gradient grids, component a at
   // grids_ik + a * grid_total; then the forces come from them, not from
   // derivatives of the SI kernel
@@ -31,7 +33,8 @@ struct Launch {
                             const SICoef<real>& si, int* err, cudaStream_t st);
   static cudaError_t near(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                           const void* rel, const uint32_t* start, void* nearres,
-                          const NearCoef<real>& nc, int terms, bool queued, cudaStream_t st);
+                          const NearCoef<real>& nc, int terms, bool queued, cudaStream_t st,
+                          double* vloc = nullptr);
   // Local part with one warp per i-cluster (FP32 only): per-column cluster
   // counts into ccount[n_cols], their scan into cstart[n_cols + 1] (ctiles:
   // scan_tiles(n_cols) entries), the cluster list into cmap[cmap_cap] and
@@ -42,7 +45,7 @@ struct Launch {
                                    const void* rel, void* nearres, const NearCoef<real>& nc, int terms,
                                    uint32_t* ccount, uint32_t* cstart, uint32_t* ctiles, int2* cmap,
                                    int2* catoms, long long cmap_cap, bool half, long long n_atoms, int stage,
-                                   int* err, cudaStream_t st);
+                                   int* err, cudaStream_t st, double* vloc = nullptr);
   static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                               const uint32_t* perm, const void* far, const void* nearres,
                               void* forces, void* pot, bool out_double, double* partials,
@@ -59,8 +62,12 @@ struct Launch {
 long long scan_tiles(long long n);
 cudaError_t launch_scan(const uint32_t* count, uint32_t* start, uint32_t* tile_sum, long long n,
                         cudaStream_t st);
+// vpart/vloc/vout (nullable): virial partials of the scale kernel, local
+// virial sums, and the per-system totals [nsys][6] (xx, yy, zz, xy, xz, yz).
 cudaError_t launch_energy(const SysDesc* sys, int nsys, const double* fourier, int n_fourier_blocks,
                           const double* partials, int n_chunks, const int* chunk_first,
-                          const double* consts, double* out, double* user_energy, cudaStream_t st);
+                          const double* consts, double* out, double* user_energy, cudaStream_t st,
+                          const double* vpart = nullptr, const double* vloc = nullptr,
+                          double* vout = nullptr);
 
 }  // namespace espk

@@ -256,6 +256,13 @@ double Split::chihat(double kappa) const {
   return s;
 }
 
+double Split::dchihat(double kappa) const {
+  if (kind == 1) return -kappa / (2.0 * alpha) * std::exp(-kappa * kappa / (4.0 * alpha));
+  double s = 0.0;
+  for (size_t i = 0; i < gx.size(); ++i) s -= gw[i] * gx[i] * chi_at[i] * std::sin(kappa * gx[i]);
+  return s;
+}
+
 double Split::second_moment() const {
   if (kind == 1) return 1.0 / (2.0 * alpha);
   double s = 0.0;

@@ -39,6 +39,7 @@ struct Split {
   double one_minus_g(double x) const;   // int_x^1 chi (PSWF) or erfc(sqrt(a) x)
   double dchi(double x) const;          // chi'(x) for 0 <= x <= 1
   double chihat(double kappa) const;    // int_0^inf chi(x) cos(kappa x) dx
+  double dchihat(double kappa) const;   // d chihat / d kappa
   double chi0() const { return chi(0.0); }
   double second_moment() const;         // int_0^inf x^2 chi
 };

@@ -66,12 +66,17 @@ struct ClusterSmem {
 // column (upwards, including the periodic images above), and its pairs among
 // themselves; the reaction on each candidate is added to its result with one
 // float4 atomic, and the cluster's own sums likewise (results zeroed before).
-template <int NC, bool HALF>
+// VIR (HALF only): also the local virial 1/2 sum_ij F_ij d_ij^T, summed per
+// warp over its clusters of one system and added to vloc[6 * system + c]
+// (xx, yy, zz, xy, xz, yz) with FP64 atomics when the system changes and at
+// the end.
+template <int NC, bool HALF, bool VIR = false>
 __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
     const SysDesc* __restrict__ sys, const int2* __restrict__ cmap, const int2* __restrict__ catoms,
     const uint32_t* __restrict__ n_clusters, const float4* __restrict__ rel,
     const uint32_t* __restrict__ start, float4* __restrict__ nearres, const NearCoef<float> nc,
-    int* __restrict__ err) {
+    int* __restrict__ err, double* __restrict__ vloc = nullptr) {
+  static_assert(HALF || !VIR, "the virial is formed in the half form");
   __shared__ ClusterSmem<HALF> smem_all[kClusterWarps];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -86,9 +91,31 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
   const long long per_block = (total_clusters + gridDim.x - 1) / gridDim.x;
   const long long g_begin = (long long)blockIdx.x * per_block;
   const long long g_end = min(total_clusters, g_begin + per_block);
+  float vir[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};    // VIR: this lane's pair sums
+  int vsys = -1;                                    // VIR: their system
+  auto flush_virial = [&]() {
+    if constexpr (VIR) {
+      if (vsys >= 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          float t = vir[c];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+          if (lane == 0) atomicAdd(vloc + 6 * vsys + c, (double)t * (1.0 / kFourPi));
+          vir[c] = 0.f;
+        }
+      }
+    }
+  };
 
   for (long long g = g_begin + wib; g < g_end; g += kClusterWarps) {
     const int2 cm = cmap[g];
+    if constexpr (VIR) {
+      if (cm.x != vsys) {
+        flush_virial();
+        vsys = cm.x;
+      }
+    }
     const SysDesc& S = sys[cm.x];
     const int n_c = S.n_c, bc = S.bc, nb = S.nb, R = S.reach;
     const float inv_bc = S.inv_bcf;
@@ -174,6 +201,17 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
           fjx = fmaf(fsj, dx, fjx);
           fjy = fmaf(fsj, dy, fjy);
           fjz = fmaf(fsj, dz, fjz);
+          if constexpr (VIR) {
+            // pair virial q_i q_j t2 d d^T (the 1/(4 pi) at the flush)
+            const float v = fsj * jd.w;
+            const float vx = v * dx, vy = v * dy, vz = v * dz;
+            vir[0] = fmaf(vx, dx, vir[0]);
+            vir[1] = fmaf(vy, dy, vir[1]);
+            vir[2] = fmaf(vz, dz, vir[2]);
+            vir[3] = fmaf(vx, dy, vir[3]);
+            vir[4] = fmaf(vx, dz, vir[4]);
+            vir[5] = fmaf(vy, dz, vir[5]);
+          }
         }
       }
       if constexpr (HALF) {
@@ -315,7 +353,9 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
           __syncwarp();
           const float4 jd = W.queue[slot];
           const int jx = HALF ? W.qidx[slot] : -1;
-          evaluate(qn >= 32 || has ? jd : make_float4(far_away, far_away, far_away, 0.f),
+          // padding candidates sit at -far_away, the cluster's padding atoms at
+          // +far_away: never within r_c of each other (no 0 * inf)
+          evaluate(qn >= 32 || has ? jd : make_float4(-far_away, -far_away, -far_away, 0.f),
                    (HALF && (qn >= 32 || has)) ? jx : -1);
           __syncwarp();
           qn = qn >= 32 ? qn - 32 : 0;
@@ -412,6 +452,17 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
         sx = fmaf(fs, dx, sx);
         sy = fmaf(fs, dy, sy);
         sz = fmaf(fs, dz, sz);
+        if constexpr (VIR) {
+          // ordered pairs: each unordered pair twice, half weight
+          const float v = 0.5f * ra.w * fs;
+          const float vx = v * dx, vy = v * dy, vz = v * dz;
+          vir[0] = fmaf(vx, dx, vir[0]);
+          vir[1] = fmaf(vy, dy, vir[1]);
+          vir[2] = fmaf(vz, dz, vir[2]);
+          vir[3] = fmaf(vx, dy, vir[3]);
+          vir[4] = fmaf(vx, dz, vir[4]);
+          vir[5] = fmaf(vy, dz, vir[5]);
+        }
       }
 #pragma unroll
       for (int o = 8; o < 32; o <<= 1) {
@@ -434,6 +485,7 @@ __global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
     }
     __syncwarp();
   }
+  flush_virial();
 }
 
 }  // namespace espk

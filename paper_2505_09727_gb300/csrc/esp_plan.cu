@@ -283,6 +283,12 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
 
   if (o.window != ESP_WINDOW_PSWF && o.window != ESP_WINDOW_BSPLINE) { msg = "unknown SI window"; return ESP_ERR_INVALID_ARG; }
   if (o.diff != ESP_DIFF_AD && o.diff != ESP_DIFF_IK) { msg = "diff must be ESP_DIFF_AD or ESP_DIFF_IK"; return ESP_ERR_INVALID_ARG; }
+  if (o.virial != 0 && o.virial != 1) { msg = "virial must be 0 or 1"; return ESP_ERR_INVALID_ARG; }
+  if (o.virial && (prec == ESP_FP32 ? (o.near_variant != 0 && o.near_variant != 4)
+                                    : (o.near_variant != 0 && o.near_variant != 1))) {
+    msg = "the virial needs the default local-part kernel";
+    return ESP_ERR_UNSUPPORTED;
+  }
   const bool bspline = o.window == ESP_WINDOW_BSPLINE;
   const double c = o.c > 0 ? o.c : cached_c(tol);
   // the B-spline comparator defaults to the usual smooth-PME order 4
@@ -453,9 +459,12 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
 
   // influence tables (Eq. pk, Phi in grid units)
   hp.G.assign(d.gsize, 0.0);
+  hp.H.assign(d.gsize, 0.0);
   for (int m = 1; m < d.gsize; ++m) {
     const double xi = 2.0 * kPi * std::sqrt((double)m) / L;
     hp.G[m] = split.chihat(r_c * xi) / (xi * xi) / (L * L * L);
+    // virial: (r_c xi chihat'(r_c xi) - 2 chihat(r_c xi)) / (xi^2 L^3)
+    hp.H[m] = (r_c * xi * split.dchihat(r_c * xi) - 2.0 * split.chihat(r_c * xi)) / (xi * xi) / (L * L * L);
   }
   hp.W.assign(n_f / 2 + 1, 0.0);
   for (int k = 0; k <= n_f / 2; ++k) {
@@ -486,6 +495,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   info.si_degree = (prec == ESP_FP32 ? espk::Deg<float>::si : espk::Deg<double>::si) - 1;
   info.window = o.window;
   info.diff = o.diff;
+  info.virial = o.virial;
   info.near_degree = (prec == ESP_FP32 ? espk::Deg<float>::nr : espk::Deg<double>::nr) - 1;
   return ESP_OK;
 }

@@ -21,6 +21,7 @@ struct HostPlan {
   espk::NearCoef<float> nc32{};
   espk::NearCoef<double> nc64{};
   std::vector<double> G, W;    // influence tables: G[|k|^2], W[|k_a|]
+  std::vector<double> H;       // virial table: d G / d ln|k| at |k|^2
   long long n_keys = 0;        // n_c^3 * kSub: length of the cell-list count array
   long long grid_elems = 0;    // n_f^3
   long long spec_elems = 0;    // n_f^2 (n_f/2 + 1)

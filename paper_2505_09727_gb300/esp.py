@@ -47,7 +47,7 @@ class esp_plan_opts(ctypes.Structure):
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("allow_background", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("timeout_ms", ctypes.c_double),
         ("cell_reach", ctypes.c_int), ("window", ctypes.c_int), ("near_variant", ctypes.c_int),
-        ("diff", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+        ("diff", ctypes.c_int), ("virial", ctypes.c_int), ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -62,7 +62,7 @@ class esp_plan_params(ctypes.Structure):
         ("cell_reach", ctypes.c_int), ("near_terms", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("tile", ctypes.c_int), ("si_degree", ctypes.c_int),
         ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("window", ctypes.c_int),
-        ("diff", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+        ("diff", ctypes.c_int), ("virial", ctypes.c_int), ("reserved", ctypes.c_int * 1),
     ]
 
     def as_dict(self) -> dict:
@@ -109,6 +109,8 @@ _SIGNATURES = {
     "esp_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "esp_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "esp_last_spectral_energy": (ctypes.c_int, [_P, _D, _D]),
+    "esp_last_virial": (ctypes.c_int, [_P, _D]),
+    "esp_batch_last_virial": (ctypes.c_int, [_P, _D]),
     "esp_destroy": (ctypes.c_int, [_P]),
     "esp_batch_create": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
@@ -276,6 +278,25 @@ def esp_phase_times(plan: int) -> dict:
     buf = (ctypes.c_float * len(PHASES))()
     _check(load_library().esp_phase_times(_P(plan), buf, len(PHASES)))
     return dict(zip(PHASES, list(buf)))
+
+
+def esp_last_virial(plan: int) -> np.ndarray:
+    """Virial of the last compute as a symmetric 3 x 3 array."""
+    buf = (ctypes.c_double * 6)()
+    _check(load_library().esp_last_virial(_P(plan), buf))
+    xx, yy, zz, xy, xz, yz = list(buf)
+    return np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]])
+
+
+def esp_batch_last_virial(batch: int, n_systems: int) -> np.ndarray:
+    """Virials of the last batch compute, shape (n_systems, 3, 3)."""
+    buf = (ctypes.c_double * (6 * n_systems))()
+    _check(load_library().esp_batch_last_virial(_P(batch), buf))
+    v = np.array(list(buf)).reshape(n_systems, 6)
+    out = np.empty((n_systems, 3, 3))
+    for i, (xx, yy, zz, xy, xz, yz) in enumerate(v):
+        out[i] = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
+    return out
 
 
 def esp_last_spectral_energy(plan: int) -> tuple[float, float]:
