@@ -134,6 +134,7 @@ struct esp_plan_s {
   double* d_vout = nullptr;      // virial: totals [nsys][6]
   bool virial = false;
   bool computed = false;         // a compute has been enqueued
+  int* h_flag = nullptr;         // pinned host copy of the device error flag
   double* d_energy = nullptr;    // per system: E (batch output)
   void* d_outF = nullptr;        // staging for outputs (FP64)
   void* d_outU = nullptr;
@@ -210,6 +211,8 @@ void release(esp_plan_s* p) {
   for (auto& e : p->tev) if (e) cudaEventDestroy(e);
   if (p->st2) cudaStreamDestroy(p->st2);
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+  if (p->h_flag) cudaFreeHost(p->h_flag);
+  p->h_flag = nullptr;
   cudaSetDevice(cur);
 }
 
@@ -224,6 +227,9 @@ struct DeviceGuard {
 };
 
 // Bounded wait: poll the stream until done or the plan deadline passes.
+// Bounded wait: polls without sleeping for the first 2 ms (a step's host
+// round trip is then a few microseconds), then every 20 us until the
+// plan's deadline.
 esp_status wait_stream(esp_plan_s* p, cudaStream_t s) {
   auto t0 = std::chrono::steady_clock::now();
   for (;;) {
@@ -232,20 +238,33 @@ esp_status wait_stream(esp_plan_s* p, cudaStream_t s) {
     if (e != cudaErrorNotReady) return fail(ESP_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (ms > p->timeout_ms) return fail(ESP_ERR_TIMEOUT, "device work exceeded the plan deadline");
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
+    if (ms < 2.0) std::this_thread::yield();
+    else std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 
-esp_status check_err_flag(esp_plan_s* p) {
-  int flag = 0;
-  ESP_CU(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st));
-  ESP_TRY(wait_stream(p, p->st));
+// The device error flag: its read is enqueued with a call's other copies
+// (one wait for all), then interpreted.
+esp_status enqueue_flag_read(esp_plan_s* p) {
+  ESP_CU(cudaMemcpyAsync(p->h_flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  return ESP_OK;
+}
+
+esp_status flag_result(esp_plan_s* p) {
+  const int flag = *p->h_flag;
   if (flag) {
+    *p->h_flag = 0;
     ESP_CU(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->st));
     if (flag & 1) return fail(ESP_ERR_NONFINITE, "a position is NaN or infinite");
     return fail(ESP_ERR_INTERNAL, "a kernel bounds check failed (flag " + std::to_string(flag) + ")");
   }
   return ESP_OK;
+}
+
+esp_status check_err_flag(esp_plan_s* p) {
+  ESP_TRY(enqueue_flag_read(p));
+  ESP_TRY(wait_stream(p, p->st));
+  return flag_result(p);
 }
 
 void rec(esp_plan_s* p, int i, cudaStream_t s) {
@@ -497,7 +516,13 @@ esp_status do_set_positions(esp_plan_s* p, const void* xyz, bool is_double, int 
   ESP_TRY(launch_sort<real>(p, src, is_double));
   rec(p, 1, p->st);
   p->have_pos = true;
-  if (where == ESP_HOST) return wait_stream(p, p->st);
+  if (where == ESP_HOST) {
+    // the caller may reuse xyz on return; the ingest's finiteness check is
+    // read in the same wait
+    ESP_TRY(enqueue_flag_read(p));
+    ESP_TRY(wait_stream(p, p->st));
+    return flag_result(p);
+  }
   return ESP_OK;
 }
 
@@ -621,13 +646,14 @@ esp_status finish_host(esp_plan_s* p, double* energy, void* forces, void* potent
   if (potential) ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * ob, cudaMemcpyDeviceToHost, p->st));
   std::vector<double> e3(3 * p->nsys);
   ESP_CU(cudaMemcpyAsync(e3.data(), p->d_eout, e3.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  ESP_TRY(enqueue_flag_read(p));
   ESP_TRY(wait_stream(p, p->st));
   for (int s = 0; s < p->nsys; ++s) {
     if (energy) energy[s] = e3[3 * s];
     p->e_fourier[s] = e3[3 * s + 1];
     p->e_gather[s] = e3[3 * s + 2];
   }
-  return check_err_flag(p);
+  return flag_result(p);
 }
 
 constexpr int kMaxRecaptures = 4;
@@ -705,6 +731,9 @@ esp_status create_streams(esp_plan_s* p, const esp_plan_opts& o) {
     return fail(ESP_ERR_CUDA, "stream/event creation failed");
   for (auto& e : p->tev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(ESP_ERR_CUDA, "event creation failed");
+  if (cudaMallocHost(reinterpret_cast<void**>(&p->h_flag), sizeof(int)) != cudaSuccess)
+    return fail(ESP_ERR_CUDA, "pinned host allocation failed");
+  *p->h_flag = 0;
   return ESP_OK;
 }
 
@@ -833,7 +862,6 @@ static esp_status set_positions_any(esp_plan_t p, const void* x, bool dbl, int w
   DeviceGuard g(p->device);
   esp_status s = p->prec == ESP_FP32 ? do_set_positions<float>(p, x, dbl, where)
                                      : do_set_positions<double>(p, x, dbl, where);
-  if (s == ESP_OK && where == ESP_HOST) s = check_err_flag(p);
   return s;
 }
 
@@ -1156,8 +1184,9 @@ esp_status esp_batch_compute(esp_batch_t b, const double* xyz, double* energies,
   if (potential) ESP_CU(cudaMemcpyAsync(potential, p->d_outU, N * sizeof(double), kind, p->st));
   if (energies) ESP_CU(cudaMemcpyAsync(energies, p->d_energy, p->nsys * sizeof(double), kind, p->st));
   if (where == ESP_HOST) {
+    ESP_TRY(enqueue_flag_read(p));
     ESP_TRY(wait_stream(p, p->st));
-    return check_err_flag(p);
+    return flag_result(p);
   }
   return ESP_OK;
 }

@@ -240,6 +240,7 @@ void finish(esp_server_s* s, Request* r, esp_status st, const std::string& msg) 
 void worker_loop(esp_server_s* s) {
   cudaSetDevice(s->opts.device);
   std::unique_lock<std::mutex> lk(s->mu);
+  Clock::time_point last_progress = Clock::now();
   while (!s->stop) {
     bool progress = false;
     // completions
@@ -311,11 +312,17 @@ void worker_loop(esp_server_s* s) {
       it = s->pending.erase(it);
       progress = true;
     }
-    if (!progress) {
+    if (progress) {
+      last_progress = Clock::now();
+    } else {
       if (s->running.empty()) s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
       else {
+        // requests in flight: poll without sleeping for 1 ms after the last
+        // event (completions are then seen within microseconds), then every
+        // 20 us
         lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (Clock::now() - last_progress < std::chrono::milliseconds(1)) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(20));
         lk.lock();
       }
     }
