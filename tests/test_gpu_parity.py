@@ -304,3 +304,25 @@ def test_full_size_water_sampled(esp):
     # properties at any size: the energy identity and finite outputs
     assert abs(g["e_fourier"] - g["e_gather"]) <= 1e-5 * abs(g["e_fourier"])
     assert np.all(np.isfinite(g["forces"]))
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_forces_are_the_energy_gradient(esp, kernel):
+    """FP64: central differences of the computed energy in a few coordinates
+    equal -F (the AD forces are the exact gradient of the discrete energy;
+    the PSWF local part is continuous at r_c)."""
+    s = inputs.uniform_charges(120, 4.0, 61)
+    h = 1e-5
+    with esp.Plan(s.L, s.n, 1e-6, r_c=1.3, precision=esp.ESP_FP64, kernel=kernel) as p:
+        p.set_charges(s.q)
+        p.set_positions(s.pos)
+        _, f, _ = p.compute()
+        for i, a in [(0, 0), (7, 1), (55, 2), (119, 0)]:
+            e = []
+            for sgn in (1.0, -1.0):
+                pos = s.pos.copy()
+                pos[i, a] += sgn * h
+                p.set_positions(pos)
+                e.append(p.compute()[0])
+            fd = -(e[0] - e[1]) / (2 * h)
+            assert abs(fd - f[i, a]) <= 1e-6 * np.max(np.abs(f)), (i, a, fd, f[i, a])

@@ -73,3 +73,18 @@ def test_ik_forces_within_tolerance_of_ewald(eps):
     assert d_ik <= eps, d_ik
     assert metrics.relative_rms_force_error(ik["forces"], ad["forces"]) <= 2 * eps
     assert d_ad <= eps
+
+
+def test_oracle_forces_are_the_energy_gradient():
+    """The oracle's AD forces equal central differences of its energy."""
+    s = inputs.uniform_charges(60, 3.0, 63)
+    p = oesp.default_params(1e-6, s.L, 1.2)
+    f = oesp.esp(s.pos, s.q, s.L, p)["forces"]
+    h = 1e-5
+    for i, a in [(0, 0), (11, 1), (42, 2)]:
+        e = []
+        for sgn in (1.0, -1.0):
+            pos = s.pos.copy()
+            pos[i, a] += sgn * h
+            e.append(oesp.esp(pos, s.q, s.L, p)["energy"])
+        assert abs(-(e[0] - e[1]) / (2 * h) - f[i, a]) <= 1e-7 * np.max(np.abs(f))
