@@ -7,6 +7,42 @@
 
 namespace espk {
 
+// The pair kernel with WARPS warps per block, on a persistent grid of as many
+// blocks as fit on the device at once, each taking a contiguous run of
+// clusters.
+template <int WARPS>
+static cudaError_t launch_near_cluster(const SysDesc* sys, long long n_cols, const uint32_t* start, const void* rel,
+                                       void* nearres, const NearCoef<float>& nc, int terms, const uint32_t* cstart,
+                                       const int2* cmap, const int2* catoms, long long cmap_cap, bool half, int* err,
+                                       cudaStream_t st, double* vloc, int sms) {
+  decltype(&k_near_cluster<10, false, false, WARPS>) kern = nullptr;
+  switch (terms) {
+#define ESP_NC_CASE(T)                                                                       \
+    case T:                                                                                  \
+      kern = vloc ? k_near_cluster<T, true, true, WARPS>                                     \
+                  : half ? k_near_cluster<T, true, false, WARPS> : k_near_cluster<T, false, false, WARPS>; \
+      break;
+    ESP_NC_CASE(8)
+    ESP_NC_CASE(9)
+    ESP_NC_CASE(10)
+    ESP_NC_CASE(12)
+#undef ESP_NC_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  static int blocks[3] = {0, 0, 0};                 // per form: full, half, half + virial
+  int& nb = blocks[vloc ? 2 : half ? 1 : 0];
+  if (nb == 0) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, 0);
+    nb = std::max(1, sms * std::max(1, per_sm));
+  }
+  const long long need = (cmap_cap + WARPS - 1) / WARPS;
+  const int grid = (int)std::min<long long>(nb, std::max<long long>(1, need));
+  kern<<<grid, WARPS * 32, 0, st>>>(sys, cmap, catoms, cstart + n_cols, (const float4*)rel, start,
+                                    (float4*)nearres, nc, err, vloc);
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long n_cols,
                                          const uint32_t* start, const void* rel, void* nearres,
@@ -26,35 +62,21 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
     if (stage == 2) return cudaGetLastError();
   }
   if (vloc && !half) return cudaErrorNotSupported;         // the virial is formed in the half form
-  decltype(&k_near_cluster<10, false>) kern = nullptr;
-  switch (terms) {
-    case 8: kern = vloc ? k_near_cluster<8, true, true> : half ? k_near_cluster<8, true> : k_near_cluster<8, false>; break;
-    case 9: kern = vloc ? k_near_cluster<9, true, true> : half ? k_near_cluster<9, true> : k_near_cluster<9, false>; break;
-    case 10: kern = vloc ? k_near_cluster<10, true, true> : half ? k_near_cluster<10, true> : k_near_cluster<10, false>; break;
-    case 12: kern = vloc ? k_near_cluster<12, true, true> : half ? k_near_cluster<12, true> : k_near_cluster<12, false>; break;
-    default: return cudaErrorInvalidValue;
-  }
   if (half) {
     // every result is accumulated with atomics
     e = cudaMemsetAsync(nearres, 0, (size_t)n_atoms * sizeof(float4), st);
     if (e != cudaSuccess) return e;
   }
-  // persistent grid: as many blocks as fit on the device at once, each block
-  // taking a contiguous run of clusters
-  static int blocks_full = 0, blocks_half = 0, blocks_vir = 0;
-  int& blocks = vloc ? blocks_vir : half ? blocks_half : blocks_full;
-  if (blocks == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kClusterWarps * 32, 0);
-    blocks = std::max(1, sms * std::max(1, per_sm));
-  }
-  const long long need = (cmap_cap + kClusterWarps - 1) / kClusterWarps;
-  const int grid = (int)std::min<long long>(blocks, std::max<long long>(1, need));
-  kern<<<grid, kClusterWarps * 32, 0, st>>>(sys, cmap, catoms, cstart + n_cols, (const float4*)rel, start,
-                                           (float4*)nearres, nc, err, vloc);
-  return cudaGetLastError();
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the list's capacity decides the block shape: 16-warp blocks once every
+  // SM gets at least 4 clusters per warp
+  const bool large = cmap_cap >= (long long)sms * kClusterWarpsLarge * 4;
+  return large ? launch_near_cluster<kClusterWarpsLarge>(sys, n_cols, start, rel, nearres, nc, terms, cstart, cmap,
+                                                          catoms, cmap_cap, half, err, st, vloc, sms)
+               : launch_near_cluster<kClusterWarpsSmall>(sys, n_cols, start, rel, nearres, nc, terms, cstart, cmap,
+                                                          catoms, cmap_cap, half, err, st, vloc, sms);
 }
 
 }  // namespace espk

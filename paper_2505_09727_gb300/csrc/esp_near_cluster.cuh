@@ -25,7 +25,11 @@
 
 namespace espk {
 
-constexpr int kClusterWarps = 8;                 // warps per block
+// Warps per block: 16 (one block per SM, 16 consecutive clusters sharing its
+// L1) for long cluster lists, 8 (two blocks per SM) for short ones, whose
+// blocks then leave room for concurrent work on the same SMs.
+constexpr int kClusterWarpsLarge = 16;
+constexpr int kClusterWarpsSmall = 8;
 constexpr int kWalk = 4;                         // candidates per lane and step
 constexpr int kClusterQueue = 32 + 32 * kWalk;   // queued candidates per warp
 constexpr int kSegCap = 96;                      // listed ranges per warp
@@ -70,13 +74,14 @@ struct ClusterSmem {
 // warp over its clusters of one system and added to vloc[6 * system + c]
 // (xx, yy, zz, xy, xz, yz) with FP64 atomics when the system changes and at
 // the end.
-template <int NC, bool HALF, bool VIR = false>
-__global__ void __launch_bounds__(kClusterWarps * 32, 2) k_near_cluster(
+template <int NC, bool HALF, bool VIR, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     const SysDesc* __restrict__ sys, const int2* __restrict__ cmap, const int2* __restrict__ catoms,
     const uint32_t* __restrict__ n_clusters, const float4* __restrict__ rel,
     const uint32_t* __restrict__ start, float4* __restrict__ nearres, const NearCoef<float> nc,
     int* __restrict__ err, double* __restrict__ vloc = nullptr) {
   static_assert(HALF || !VIR, "the virial is formed in the half form");
+  constexpr int kClusterWarps = WARPS;
   __shared__ ClusterSmem<HALF> smem_all[kClusterWarps];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -127,6 +128,7 @@ struct esp_server_s {
   std::mutex mu;
   std::condition_variable cv_done;     // a request finished
   std::condition_variable cv_work;     // new request or a slot freed
+  std::atomic<uint64_t> n_submitted{0};  // read by the worker while it polls unlocked
   std::thread worker;
   bool stop = false;
   std::vector<SystemRec> systems;
@@ -317,12 +319,25 @@ void worker_loop(esp_server_s* s) {
     } else {
       if (s->running.empty()) s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
       else {
-        // requests in flight: poll without sleeping for 1 ms after the last
-        // event (completions are then seen within microseconds), then every
-        // 20 us
+        // requests in flight: poll their completion events with the lock
+        // released (clients submit and wait meanwhile), without sleeping for
+        // 1 ms after the last event, then every 20 us; a new submission or
+        // 200 us end the poll
+        std::vector<cudaEvent_t> evs;
+        evs.reserve(s->running.size());
+        for (Request* r : s->running) evs.push_back(r->ev);
+        const uint64_t sub0 = s->n_submitted.load(std::memory_order_acquire);
         lk.unlock();
-        if (Clock::now() - last_progress < std::chrono::milliseconds(1)) std::this_thread::yield();
-        else std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const Clock::time_point t0 = Clock::now();
+        for (bool done = false; !done;) {
+          for (cudaEvent_t e : evs)
+            if (cudaEventQuery(e) != cudaErrorNotReady) done = true;
+          if (done || s->n_submitted.load(std::memory_order_acquire) != sub0) break;
+          const Clock::time_point now = Clock::now();
+          if (now - t0 > std::chrono::microseconds(200)) break;
+          if (now - last_progress < std::chrono::milliseconds(1)) std::this_thread::yield();
+          else std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
         lk.lock();
       }
     }
@@ -418,6 +433,7 @@ esp_status esp_server_submit(esp_server_t s, int id, double tolerance, const dou
     }
     s->pending.push_back(r.get());
     s->tickets[r->ticket] = std::move(r);
+    s->n_submitted.fetch_add(1, std::memory_order_release);
   }
   s->cv_work.notify_one();
   return ESP_OK;
