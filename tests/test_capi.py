@@ -147,3 +147,28 @@ def test_autotune_argument_checks(lib):
     box = lib.esp_box((ctypes.c_double * 3)(5.0, 5.0, 5.0))
     out = lib.esp_plan_opts()
     assert so.esp_autotune(ctypes.byref(box), 10, 1e-4, None, None, None, 0, 3, ctypes.byref(out), None) == 1
+
+
+def test_planner_ik_and_virial_options(lib):
+    L, N, eps = 14.4129, 300_000, 1e-4
+    base = lib.esp_plan_query(L, N, eps, r_c=1.0)
+    ik = lib.esp_plan_query(L, N, eps, r_c=1.0, diff=lib.ESP_DIFF_IK)
+    vir = lib.esp_plan_query(L, N, eps, r_c=1.0, virial=1)
+    assert base["diff"] == lib.ESP_DIFF_AD and ik["diff"] == lib.ESP_DIFF_IK
+    assert vir["virial"] == 1 and base["virial"] == 0
+    # the ik method holds three more grids and spectra
+    extra = 3 * (ik["n_f"] ** 3 * 4 + ik["n_f"] ** 2 * (ik["n_f"] // 2 + 1) * 8)
+    assert ik["device_bytes"] - base["device_bytes"] == extra
+    assert ik["n_f"] == base["n_f"] and ik["P"] == base["P"]
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(diff=2), 1),
+    (dict(virial=2), 1),
+    (dict(virial=1, near_variant=2), 10),         # the virial needs the default local part
+    (dict(virial=1, near_variant=3), 10),
+])
+def test_planner_rejects_bad_ik_and_virial_options(lib, kw, status):
+    with pytest.raises(lib.EspError) as exc:
+        lib.esp_plan_query(10.0, 1000, 1e-4, r_c=1.0, **kw)
+    assert exc.value.status == status
