@@ -202,6 +202,16 @@ esp_status esp_phase_times(esp_plan_t plan, float* ms, int n);
 /* Spectral energy 1/2 sum_k p_k |bh_k|^2 of the last compute (host double). */
 esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* e_gather);
 
+/* One step: esp_set_positions(xyz) followed by esp_compute, in one call.
+ * With host buffers the call copies the positions in, computes, copies the
+ * results out and waits once; after its first run the sort and the compute
+ * replay as one captured CUDA graph (per position source and output
+ * pointers, as for esp_compute). Errors as for the two calls (a non-finite
+ * position is reported as ESP_ERR_NONFINITE by this call with host
+ * buffers, by the next synchronising call otherwise). */
+esp_status esp_step(esp_plan_t plan, const double* xyz, double* energy, double* forces,
+                    double* potential, int where);
+
 /* Virial of the last compute of a plan made with opts.virial = 1: W_ab =
  * -dE/d eps_ab under the homogeneous deformation r -> (1 + eps) r of atoms
  * and box (the grid deforms with the box), in energy units (times the

@@ -163,6 +163,12 @@ struct esp_plan_s {
   cudaGraph_t cgraph = nullptr;
   cudaGraphExec_t cgexec = nullptr;
   const void* ckey[4] = {};
+  // esp_step: sort + compute captured together, keyed like the compute graph
+  // plus the position source
+  int s_direct_runs = 0, s_captures = 0;
+  cudaGraph_t sgraph = nullptr;
+  cudaGraphExec_t sgexec = nullptr;
+  const void* skey[5] = {};
 };
 
 struct esp_batch_s {
@@ -199,6 +205,8 @@ void release(esp_plan_s* p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->cgexec) cudaGraphExecDestroy(p->cgexec);
   if (p->cgraph) cudaGraphDestroy(p->cgraph);
+  if (p->sgexec) cudaGraphExecDestroy(p->sgexec);
+  if (p->sgraph) cudaGraphDestroy(p->sgraph);
   for (void* a : p->allocs) cudaFree(a);
   p->allocs.clear();
   for (Bucket& b : p->buckets) {
@@ -688,6 +696,8 @@ esp_status compute_enqueue(esp_plan_s* p, void* outF, void* outU, bool out_doubl
   if (e != cudaSuccess) return fail(ESP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   if (p->cgexec) cudaGraphExecDestroy(p->cgexec);
   if (p->cgraph) cudaGraphDestroy(p->cgraph);
+  if (p->sgexec) cudaGraphExecDestroy(p->sgexec);
+  if (p->sgraph) cudaGraphDestroy(p->sgraph);
   p->cgexec = nullptr;
   p->cgraph = graph;
   ++p->c_captures;
@@ -715,6 +725,72 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
   p->timed_valid = p->timing;
   return ESP_OK;
 }
+
+// esp_step: positions at `src` (device) sorted and computed; after a first
+// direct run, sort and compute replay as one captured graph for the same
+// source and output pointers.
+template <typename real>
+esp_status step_enqueue(esp_plan_s* p, const void* src, void* outF, void* outU, bool out_double, double* outE) {
+  const void* key[5] = {outF, outU, out_double ? (const void*)1 : nullptr, outE, src};
+  if (p->sgexec && std::equal(key, key + 5, p->skey)) {
+    ESP_CU(cudaGraphLaunch(p->sgexec, p->st));
+    return ESP_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ESP_CU(cudaStreamIsCapturing(p->st, &cs));
+  if (p->s_direct_runs == 0 || cs != cudaStreamCaptureStatusNone || p->s_captures >= kMaxRecaptures) {
+    ++p->s_direct_runs;
+    ESP_TRY(launch_sort<real>(p, src, true));
+    return launch_compute<real>(p, outF, outU, out_double, outE);
+  }
+  cudaGraph_t graph = nullptr;
+  ESP_CU(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+  esp_status st = launch_sort<real>(p, src, true);
+  if (st == ESP_OK) st = launch_compute<real>(p, outF, outU, out_double, outE);
+  const cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+  if (st != ESP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(ESP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (p->sgexec) cudaGraphExecDestroy(p->sgexec);
+  if (p->sgraph) cudaGraphDestroy(p->sgraph);
+  p->sgexec = nullptr;
+  p->sgraph = graph;
+  ++p->s_captures;
+  ESP_CU(cudaGraphInstantiate(&p->sgexec, graph, 0));
+  std::copy(key, key + 5, p->skey);
+  ESP_CU(cudaGraphLaunch(p->sgexec, p->st));
+  return ESP_OK;
+}
+
+template <typename real>
+esp_status do_step(esp_plan_s* p, const double* xyz, double* energy, void* forces, void* potential, bool out_double,
+                   int where) {
+  if (!p->have_q) return fail(ESP_ERR_NOT_READY, "charges not set");
+  if (p->timing) {
+    // timing mode: the two calls, with their phase events
+    ESP_TRY(do_set_positions<real>(p, xyz, true, where));
+    return do_compute<real>(p, energy, forces, potential, out_double, where);
+  }
+  const void* src = xyz;
+  void* outF = forces;
+  void* outU = potential;
+  double* outE = energy;
+  if (where == ESP_HOST) {
+    ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, p->N * 3 * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    src = p->d_pos;
+    outF = forces ? p->d_outF : nullptr;
+    outU = potential ? p->d_outU : nullptr;
+    outE = nullptr;
+  }
+  ESP_TRY(step_enqueue<real>(p, src, outF, outU, out_double, outE));
+  p->have_pos = true;
+  p->timed_valid = false;
+  if (where == ESP_HOST) ESP_TRY(finish_host(p, energy, forces, potential, out_double));
+  return ESP_OK;
+}
+
 
 esp_status create_streams(esp_plan_s* p, const esp_plan_opts& o) {
   if (o.stream) {
@@ -888,6 +964,15 @@ esp_status esp_compute(esp_plan_t p, double* energy, double* forces, double* pot
 }
 esp_status esp_compute_f32(esp_plan_t p, double* energy, float* forces, float* potential, int where) {
   return compute_any(p, energy, forces, potential, false, where);
+}
+
+esp_status esp_step(esp_plan_t p, const double* xyz, double* energy, double* forces, double* potential, int where) {
+  if (!p || (!xyz && p->N > 0)) return fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  if (where != ESP_HOST && where != ESP_DEVICE) return fail(ESP_ERR_INVALID_ARG, "bad 'where'");
+  DeviceGuard g(p->device);
+  if (p->N == 0) return compute_any(p, energy, forces, potential, true, where);
+  return p->prec == ESP_FP32 ? do_step<float>(p, xyz, energy, forces, potential, true, where)
+                             : do_step<double>(p, xyz, energy, forces, potential, true, where);
 }
 
 esp_status esp_synchronize(esp_plan_t p) {

@@ -110,6 +110,7 @@ _SIGNATURES = {
     "esp_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "esp_last_spectral_energy": (ctypes.c_int, [_P, _D, _D]),
     "esp_last_virial": (ctypes.c_int, [_P, _D]),
+    "esp_step": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "esp_batch_last_virial": (ctypes.c_int, [_P, _D]),
     "esp_destroy": (ctypes.c_int, [_P]),
     "esp_batch_create": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
@@ -242,6 +243,21 @@ def esp_set_positions(plan: int, xyz, where: int | None = None):
     f32 = str(getattr(xyz, "dtype", "")).endswith("float32")
     fn = load_library().esp_set_positions_f32 if f32 else load_library().esp_set_positions
     _check(fn(_P(plan), ptr, where if where is not None else w))
+
+
+def esp_step(plan: int, xyz, energy=None, forces=None, potential=None, where: int | None = None):
+    """esp_set_positions(xyz) and esp_compute in one call (FP64 buffers: NumPy
+    arrays or torch tensors, all host or all device)."""
+    xp, xw = _ptr(xyz, np.float64 if isinstance(xyz, np.ndarray) else None)
+    ws = {w for _, w in (_ptr(energy), _ptr(forces), _ptr(potential)) if w is not None} | {xw}
+    if where is None:
+        if len(ws) != 1:
+            raise ValueError("esp_step needs all buffers on the host or all on the device")
+        where = ws.pop()
+    _check(load_library().esp_step(_P(plan), xp, _ptr(energy)[0], _ptr(forces)[0], _ptr(potential)[0], where))
+    if isinstance(energy, np.ndarray):
+        return float(energy[0])
+    return None
 
 
 def esp_compute(plan: int, energy=None, forces=None, potential=None, where: int | None = None):

@@ -96,3 +96,38 @@ def test_energy_only_matches_full_compute(esp, prec):
             assert abs(float(e.cpu()[0]) - float(e_full.cpu()[0])) <= bound * abs(float(e_full.cpu()[0]))
     finally:
         esp.esp_destroy(h)
+
+
+def test_step_matches_set_positions_and_compute(esp):
+    """esp_step (positions in, compute, results out in one call; sort and
+    compute replayed as one graph) equals fresh plans, host and device."""
+    import torch
+    dev = torch.device("cuda:0")
+    s = inputs.spce_water(2000, seed=44)
+    with esp.Plan(s.L, s.n, 1e-4, r_c=1.0) as p:
+        p.set_charges(s.q)
+        for k in range(4):                       # direct run, capture, replays
+            pos = inputs.perturb(s, 0.02, seed=600 + k).pos
+            e = np.zeros(1)
+            f = np.zeros((s.n, 3))
+            u = np.zeros(s.n)
+            esp.esp_step(p.handle, np.ascontiguousarray(pos), e, f, u)
+            e0, f0, u0 = fresh(esp, s, pos)
+            assert rel_rms(f, f0) <= FP32_PARITY and rel_rms(u, u0) <= FP32_PARITY
+            assert abs(e[0] - e0) <= FP32_PARITY * abs(e0)
+        x = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
+        ed = torch.zeros(1, dtype=torch.float64, device=dev)
+        fd = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
+        for k in range(3):                       # device buffers, the same source pointer
+            pos = inputs.perturb(s, 0.02, seed=700 + k).pos
+            x.copy_(torch.tensor(pos))
+            esp.esp_step(p.handle, x, ed, fd, None)
+            torch.cuda.synchronize()
+            e0, f0, _ = fresh(esp, s, pos)
+            assert rel_rms(fd.cpu().numpy(), f0) <= FP32_PARITY
+            assert abs(float(ed.cpu()[0]) - e0) <= FP32_PARITY * abs(e0)
+        bad = s.pos.copy()
+        bad[3, 0] = np.inf
+        with pytest.raises(esp.EspError) as exc:
+            esp.esp_step(p.handle, bad, np.zeros(1), np.zeros((s.n, 3)), None)
+        assert exc.value.status == 4
