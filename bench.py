@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -70,7 +71,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"esp_bench_clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -122,7 +123,10 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-NEAR_FLOPS_PER_PAIR = 71     # flops of one unordered pair evaluation
+# flops of one unordered pair evaluation: difference 3, r^2 5, rsqrt 1,
+# polynomial argument 2, two 9-term Horner polynomials 2 x 18, potentials
+# 2 + 2, r^-3 terms 4, forces on both atoms 2 x (1 + 6)
+NEAR_FLOPS_PER_PAIR = 71
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "near_cluster_water3e5_traffic.md")
 NEAR_SOURCE = os.path.join(ROOT, "paper_2505_09727_gb300", "csrc", "esp_near_cluster.cuh")
 
