@@ -6,12 +6,10 @@
 #define ESP_P_MIN 4
 #define ESP_NEAR_SHORT 10
 #define ESP_P_MAX 12
+// P = 4 ... 7 here, 8 ... 12 in esp_kern_f32_rest.cu (compiled in parallel)
 #define ESP_P_CASES(FN, ...)                                              \
   ESP_P_CASE(4, FN, __VA_ARGS__) ESP_P_CASE(5, FN, __VA_ARGS__)           \
-  ESP_P_CASE(6, FN, __VA_ARGS__) ESP_P_CASE(7, FN, __VA_ARGS__)           \
-  ESP_P_CASE(8, FN, __VA_ARGS__) ESP_P_CASE(9, FN, __VA_ARGS__)           \
-  ESP_P_CASE(10, FN, __VA_ARGS__) ESP_P_CASE(11, FN, __VA_ARGS__)         \
-  ESP_P_CASE(12, FN, __VA_ARGS__)
+  ESP_P_CASE(6, FN, __VA_ARGS__) ESP_P_CASE(7, FN, __VA_ARGS__)
 #include "esp_kern_impl.cuh"
 
 namespace espk {

@@ -3,14 +3,10 @@
 #define ESP_P_MIN 4
 #define ESP_NEAR_SHORT 24
 #define ESP_P_MAX 16
+// P = 4 ... 7 here, 8 ... 16 in esp_kern_f64_rest.cu (compiled in parallel)
 #define ESP_P_CASES(FN, ...)                                              \
   ESP_P_CASE(4, FN, __VA_ARGS__) ESP_P_CASE(5, FN, __VA_ARGS__)           \
-  ESP_P_CASE(6, FN, __VA_ARGS__) ESP_P_CASE(7, FN, __VA_ARGS__)           \
-  ESP_P_CASE(8, FN, __VA_ARGS__) ESP_P_CASE(9, FN, __VA_ARGS__)           \
-  ESP_P_CASE(10, FN, __VA_ARGS__) ESP_P_CASE(11, FN, __VA_ARGS__)         \
-  ESP_P_CASE(12, FN, __VA_ARGS__) ESP_P_CASE(13, FN, __VA_ARGS__)         \
-  ESP_P_CASE(14, FN, __VA_ARGS__) ESP_P_CASE(15, FN, __VA_ARGS__)         \
-  ESP_P_CASE(16, FN, __VA_ARGS__)
+  ESP_P_CASE(6, FN, __VA_ARGS__) ESP_P_CASE(7, FN, __VA_ARGS__)
 #include "esp_kern_impl.cuh"
 
 namespace espk {

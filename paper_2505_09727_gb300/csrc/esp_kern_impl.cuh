@@ -38,6 +38,7 @@ static int brick_splits(int n_work) {
 
 }  // namespace detail
 
+#ifndef ESP_IMPL_REST
 template <>
 cudaError_t Launch<ESP_REAL>::ingest(const SysDesc* sys, const int2* chunks, int n_chunks,
                                      const void* xyz, bool xyz_is_double, void* coord,
@@ -66,6 +67,7 @@ cudaError_t Launch<ESP_REAL>::scatter(const SysDesc* sys, const int2* chunks, in
                                                              start, q, (A*)atoms, (R*)rel, perm);
   return cudaGetLastError();
 }
+#endif  // ESP_IMPL_REST
 
 template <int P>
 static cudaError_t spread_p(const SysDesc* sys, const int2* work, int n_work, size_t smem,
@@ -124,6 +126,38 @@ static cudaError_t gather_p(const SysDesc* sys, const int2* work, int n_work, si
 #define ESP_P_CASE(PP, FN, ...) \
   case PP: return FN<PP>(__VA_ARGS__);
 
+// The stencil widths are split over two units compiled in parallel: the
+// main unit's ESP_P_CASES, and the rest in a second unit (ESP_IMPL_REST)
+// reached through spread_rest / gather_rest.
+cudaError_t spread_rest(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem, const void* atoms,
+                        const uint32_t* start, ESP_REAL* grids, const SICoef<ESP_REAL>& si, int* err,
+                        cudaStream_t st);
+cudaError_t gather_rest(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem, const void* atoms,
+                        const uint32_t* start, const ESP_REAL* grids, const ESP_REAL* grids_ik, long long grid_total,
+                        void* far, const SICoef<ESP_REAL>& si, int* err, cudaStream_t st);
+
+#ifdef ESP_IMPL_REST
+
+cudaError_t spread_rest(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem, const void* atoms,
+                        const uint32_t* start, ESP_REAL* grids, const SICoef<ESP_REAL>& si, int* err,
+                        cudaStream_t st) {
+  switch (P) {
+    ESP_P_CASES(spread_p, sys, work, n_work, smem, atoms, start, grids, si, err, st)
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t gather_rest(int P, const SysDesc* sys, const int2* work, int n_work, size_t smem, const void* atoms,
+                        const uint32_t* start, const ESP_REAL* grids, const ESP_REAL* grids_ik, long long grid_total,
+                        void* far, const SICoef<ESP_REAL>& si, int* err, cudaStream_t st) {
+  switch (P) {
+    ESP_P_CASES(gather_p, sys, work, n_work, smem, atoms, start, grids, grids_ik, grid_total, far, si, err, st)
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+#else
+
 template <>
 cudaError_t Launch<ESP_REAL>::spread(int P, const SysDesc* sys, const int2* work, int n_work,
                                      size_t smem, const void* atoms, const uint32_t* start,
@@ -132,7 +166,7 @@ cudaError_t Launch<ESP_REAL>::spread(int P, const SysDesc* sys, const int2* work
   if (n_work == 0) return cudaSuccess;
   switch (P) {
     ESP_P_CASES(spread_p, sys, work, n_work, smem, atoms, start, grids, si, err, st)
-    default: return cudaErrorInvalidValue;
+    default: return spread_rest(P, sys, work, n_work, smem, atoms, start, grids, si, err, st);
   }
 }
 
@@ -144,7 +178,8 @@ cudaError_t Launch<ESP_REAL>::gather(int P, const SysDesc* sys, const int2* work
   if (n_work == 0) return cudaSuccess;
   switch (P) {
     ESP_P_CASES(gather_p, sys, work, n_work, smem, atoms, start, grids, grids_ik, grid_total, far, si, err, st)
-    default: return cudaErrorInvalidValue;
+    default: return gather_rest(P, sys, work, n_work, smem, atoms, start, grids, grids_ik, grid_total, far, si,
+                                err, st);
   }
 }
 
@@ -221,5 +256,7 @@ template <>
 size_t Launch<ESP_REAL>::atom_bytes() { return sizeof(typename Types<ESP_REAL>::atom); }
 template <>
 size_t Launch<ESP_REAL>::res_bytes() { return sizeof(typename Types<ESP_REAL>::res); }
+
+#endif  // ESP_IMPL_REST
 
 }  // namespace espk
