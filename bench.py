@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--molecules", type=int, default=WORKLOAD["molecules"])
+    ap.add_argument("--tolerance", type=float, default=WORKLOAD["tolerance"],
+                    help="relative RMS force tolerance of the main line (profiling other stencil widths)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64, Gaussian, batched and served comparison lines")
@@ -252,7 +254,7 @@ def run_gpu(args, world, rank, local):
     # not adopt)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    h = esp.esp_plan(L, N, WORKLOAD["tolerance"], r_c=WORKLOAD["r_c_nm"], device=local,
+    h = esp.esp_plan(L, N, args.tolerance, r_c=WORKLOAD["r_c_nm"], device=local,
                      stream=stream.cuda_stream)
     info = esp.esp_plan_info(h)
     q = torch.tensor(s.q, device=dev)
@@ -618,7 +620,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, molecules=args.molecules, atoms=N, L_nm=r["L"], n_f=r["info"]["n_f"],
+        "config": dict(WORKLOAD, molecules=args.molecules, tolerance=args.tolerance, atoms=N, L_nm=r["L"], n_f=r["info"]["n_f"],
                        P=r["info"]["P"], c=r["info"]["c"], c1=r["info"]["c1"], l2="flushed_between_steps",
                        parallelism=f"replicas{world}"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * 3 * 8,
