@@ -143,7 +143,9 @@ typedef struct {
   int window;              /* ESP_WINDOW_PSWF or ESP_WINDOW_BSPLINE          */
   int diff;                /* ESP_DIFF_AD or ESP_DIFF_IK                     */
   int virial;              /* 1 when computes form the virial                */
-  int reserved[1];
+  int triclinic;           /* 1 for a plan of esp_plan_cell (L is then the
+                              longest cell vector, n_cells counts cells of
+                              fractional coordinates per axis)               */
 } esp_plan_params;
 
 /* Fill opts with defaults (all planner choices, FP32, PSWF, device 0). */
@@ -162,6 +164,29 @@ esp_status esp_plan_info(esp_plan_t plan, esp_plan_params* out);
  * that excludes the cuFFT work areas. */
 esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance,
                           const esp_plan_opts* opts, esp_plan_params* out);
+
+/* Triclinic (or orthorhombic) periodic cell: the cell vectors a, b, c in the
+ * reduced orientation a = (ax, 0, 0), b = (bx, by, 0), c = (cx, cy, cz) with
+ * ax, by, cz > 0 (the truncated-octahedral and rhombic-dodecahedral boxes of
+ * Table 1 take this form). Images of r are r + n_a a + n_b b + n_c c. */
+typedef struct { double a[3], b[3], c[3]; } esp_cell;
+
+/* Plan for N charges in a triclinic cell (Eq. task on the lattice of the
+ * cell). The n_f^3 grid and the cell list are laid over fractional
+ * coordinates s = H^-1 r (H = [a b c]); spread and interpolation use the SI
+ * kernel per fractional axis, the influence function is Eq. pk with
+ * |xi(k)| = 2 pi |H^-T k| and Phi in grid units, forces are
+ * -q H^-T grad_s u~ plus the local part over every image within r_c.
+ * n_f, c, c1 and P follow the cubic rules on the longest cell vector.
+ * Errors: ESP_ERR_INVALID_ARG for a cell not in the reduced orientation,
+ * ESP_ERR_CUTOFF_TOO_LARGE unless r_c is below half the smallest distance
+ * between opposite faces, ESP_ERR_UNSUPPORTED for ESP_FP64, ESP_DIFF_IK, the
+ * virial, a local-part variant other than 0/4, or n_f > 384. The plan is used
+ * like any other (esp_set_*, esp_compute, esp_step, esp_destroy). */
+esp_status esp_plan_cell(const esp_cell* cell, int64_t N, double tolerance,
+                         const esp_plan_opts* opts, esp_plan_t* out);
+esp_status esp_plan_query_cell(const esp_cell* cell, int64_t N, double tolerance,
+                               const esp_plan_opts* opts, esp_plan_params* out);
 
 /* Charges q[N] (double or float). Must be called before the first compute
  * and whenever charges change. */

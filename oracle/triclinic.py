@@ -50,18 +50,22 @@ def fractional(pos, H) -> np.ndarray:
 
 
 def _image_shifts(H, r_max):
-    """Integer n with |H n| possibly below r_max + the cell diagonal."""
+    """Integer n that can give |H (ds - n)| < r_max for a fractional
+    difference ds in (-1, 1)^3: the a-th fractional component of a vector is
+    at most its length over the height h_a, so |ds_a - n_a| < r_max / h_a and
+    |n_a| <= floor(r_max / h_a) + 1."""
     h = heights(H)
-    diag = float(np.linalg.norm(H.sum(axis=1))) + float(np.linalg.norm(H[:, 0] - H[:, 1])) \
-        + float(np.linalg.norm(H[:, 0] - H[:, 2])) + float(np.linalg.norm(H[:, 1] - H[:, 2]))
-    K = [int(math.ceil((r_max + diag) / h[a])) for a in range(3)]
+    K = [int(math.floor(r_max / h[a])) + 1 for a in range(3)]
     return np.array(list(itertools.product(range(-K[0], K[0] + 1), range(-K[1], K[1] + 1),
                                            range(-K[2], K[2] + 1))), dtype=np.float64)
 
 
 def _pairs_within(pos, H, r_max):
     """(i, j, d) for every ordered pair and image with 0 < |d| < r_max,
-    d = r_i - r_j - H n."""
+    d = r_i - r_j - H n. The positions are first wrapped into the cell (a
+    lattice shift of one atom permutes its images and changes no d), so the
+    fractional differences lie in (-1, 1)^3 as _image_shifts assumes."""
+    pos = fractional(pos, H) @ H.T
     shifts = _image_shifts(H, r_max) @ H.T
     out_i, out_j, out_d = [], [], []
     for i in range(pos.shape[0]):

@@ -85,6 +85,16 @@ struct SysDesc {
   float wf, r_cf, rc2f, inv_rcf, inv_rc2x2f, inv_rc3f, inv_bcf;
   float w32f;                       // wf / 2^32 (exact)
   float self_coef_f, bg_shift_f, prefactor_f;
+  double vol;                       // cell volume (L^3 for a cube)
+  // Triclinic cell (tri = 1): H = [a b c] with a = (ax,0,0), b = (bx,by,0),
+  // c = (cx,cy,cz); the grid, cells and fixed-point coordinates are laid over
+  // fractional coordinates s = H^-1 r. Unused when tri = 0.
+  int tri;
+  double tfix[6];   // 2^32 H^-1: (xx, xy, xz, yy, yz, zz) entries of the upper triangle
+  double tcell[6];  // cell vectors / n_c: a_x, b_x, b_y, c_x, c_y, c_z
+  float tgrad[6];   // n_f H^-T (lower triangle): (xx, yx, yy, zx, zy, zz)
+  float tcol[3];    // a_x, b_x, b_y over n_c: offsets of neighbouring columns
+  float tbrick[3];  // bc c / n_c: offset of one brick up the column
 };
 
 // Padded pitches of a spread/gather tile of edge T (elements): rows of odd

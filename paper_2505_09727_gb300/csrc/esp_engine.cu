@@ -578,7 +578,7 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
     rec(p, 9, st2);
     ESP_CU(L::near_clusters(p->d_desc, p->nsys, p->n_cols, p->d_start, p->d_rel, p->d_near, nc, hp.near_nc,
                             p->d_ccount, p->d_cstart, p->d_ctiles, p->d_cmap, p->d_catoms, p->cmap_cap,
-                            hp.near_half, p->N, 1, p->d_err, st2, p->d_vloc));
+                            hp.near_half, p->N, 1, p->d_err, st2, p->d_vloc, hp.desc.tri != 0));
   } else {
     rec(p, 9, st2);
     ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
@@ -864,16 +864,18 @@ void esp_plan_opts_init(esp_plan_opts* o) {
   o->timeout_ms = 60000.0;
 }
 
-esp_status esp_plan(const esp_box* box, int64_t N, double tolerance, const esp_plan_opts* opts,
-                    esp_plan_t* out) {
-  if (!box || !out) return fail(ESP_ERR_INVALID_ARG, "box and out must not be NULL");
+// A single-system plan from the box (cubic: cell == nullptr) or the cell.
+static esp_status plan_single(const esp_box* box, const esp_cell* cell, int64_t N, double tolerance,
+                              const esp_plan_opts* opts, esp_plan_t* out) {
+  if ((!box && !cell) || !out) return fail(ESP_ERR_INVALID_ARG, "box/cell and out must not be NULL");
   *out = nullptr;
   const esp_plan_opts o = resolve_opts(opts);
-  if (!cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
+  if (box && !cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
   esp_plan_s* p = new esp_plan_s();
   p->hps.resize(1);
   std::string msg;
-  esp_status s = espe::make_host_plan(box->L[0], N, tolerance, o, p->hps[0], msg);
+  esp_status s = box ? espe::make_host_plan(box->L[0], N, tolerance, o, p->hps[0], msg)
+                     : espe::make_host_plan_cell(&cell->a[0], N, tolerance, o, p->hps[0], msg);
   if (s != ESP_OK) {
     delete p;
     return fail(s, msg);
@@ -889,14 +891,15 @@ esp_status esp_plan(const esp_box* box, int64_t N, double tolerance, const esp_p
   return ESP_OK;
 }
 
-esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const esp_plan_opts* opts,
-                          esp_plan_params* out) {
-  if (!box || !out) return fail(ESP_ERR_INVALID_ARG, "box and out must not be NULL");
+static esp_status query_single(const esp_box* box, const esp_cell* cell, int64_t N, double tolerance,
+                               const esp_plan_opts* opts, esp_plan_params* out) {
+  if ((!box && !cell) || !out) return fail(ESP_ERR_INVALID_ARG, "box/cell and out must not be NULL");
   const esp_plan_opts o = resolve_opts(opts);
-  if (!cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
+  if (box && !cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
   espe::HostPlan hp;
   std::string msg;
-  esp_status s = espe::make_host_plan(box->L[0], N, tolerance, o, hp, msg);
+  esp_status s = box ? espe::make_host_plan(box->L[0], N, tolerance, o, hp, msg)
+                     : espe::make_host_plan_cell(&cell->a[0], N, tolerance, o, hp, msg);
   if (s != ESP_OK) return fail(s, msg);
   const size_t rb = o.precision == ESP_FP32 ? 4 : 8;
   const size_t ab = o.precision == ESP_FP32 ? 16 : 32;
@@ -913,6 +916,30 @@ esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const
   hp.info.device_bytes = bytes;
   *out = hp.info;
   return ESP_OK;
+}
+
+esp_status esp_plan(const esp_box* box, int64_t N, double tolerance, const esp_plan_opts* opts,
+                    esp_plan_t* out) {
+  if (!box) return fail(ESP_ERR_INVALID_ARG, "box must not be NULL");
+  return plan_single(box, nullptr, N, tolerance, opts, out);
+}
+
+esp_status esp_plan_cell(const esp_cell* cell, int64_t N, double tolerance, const esp_plan_opts* opts,
+                         esp_plan_t* out) {
+  if (!cell) return fail(ESP_ERR_INVALID_ARG, "cell must not be NULL");
+  return plan_single(nullptr, cell, N, tolerance, opts, out);
+}
+
+esp_status esp_plan_query(const esp_box* box, int64_t N, double tolerance, const esp_plan_opts* opts,
+                          esp_plan_params* out) {
+  if (!box) return fail(ESP_ERR_INVALID_ARG, "box must not be NULL");
+  return query_single(box, nullptr, N, tolerance, opts, out);
+}
+
+esp_status esp_plan_query_cell(const esp_cell* cell, int64_t N, double tolerance, const esp_plan_opts* opts,
+                               esp_plan_params* out) {
+  if (!cell) return fail(ESP_ERR_INVALID_ARG, "cell must not be NULL");
+  return query_single(nullptr, cell, N, tolerance, opts, out);
 }
 
 esp_status esp_plan_info(esp_plan_t p, esp_plan_params* out) {

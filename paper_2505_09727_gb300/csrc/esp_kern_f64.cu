@@ -16,7 +16,7 @@ template <>
 cudaError_t Launch<double>::near_clusters(const SysDesc*, int, long long, const uint32_t*, const void*,
                                           void*, const NearCoef<double>&, int, uint32_t*, uint32_t*,
                                           uint32_t*, int2*, int2*, long long, bool, long long, int, int*,
-                                          cudaStream_t, double*) {
+                                          cudaStream_t, double*, bool) {
   return cudaErrorNotSupported;
 }
 

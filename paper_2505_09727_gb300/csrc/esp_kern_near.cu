@@ -14,12 +14,13 @@ template <int WARPS>
 static cudaError_t launch_near_cluster(const SysDesc* sys, long long n_cols, const uint32_t* start, const void* rel,
                                        void* nearres, const NearCoef<float>& nc, int terms, const uint32_t* cstart,
                                        const int2* cmap, const int2* catoms, long long cmap_cap, bool half, int* err,
-                                       cudaStream_t st, double* vloc, int sms) {
+                                       cudaStream_t st, double* vloc, int sms, bool tri) {
   decltype(&k_near_cluster<10, false, false, WARPS>) kern = nullptr;
   switch (terms) {
 #define ESP_NC_CASE(T)                                                                       \
     case T:                                                                                  \
-      kern = vloc ? k_near_cluster<T, true, true, WARPS>                                     \
+      kern = tri ? k_near_cluster<T, true, false, WARPS, true>                                \
+           : vloc ? k_near_cluster<T, true, true, WARPS>                                      \
                   : half ? k_near_cluster<T, true, false, WARPS> : k_near_cluster<T, false, false, WARPS>; \
       break;
     ESP_NC_CASE(8)
@@ -29,8 +30,8 @@ static cudaError_t launch_near_cluster(const SysDesc* sys, long long n_cols, con
 #undef ESP_NC_CASE
     default: return cudaErrorInvalidValue;
   }
-  static int blocks[3] = {0, 0, 0};                 // per form: full, half, half + virial
-  int& nb = blocks[vloc ? 2 : half ? 1 : 0];
+  static int blocks[4] = {0, 0, 0, 0};              // per form: full, half, half + virial, triclinic
+  int& nb = blocks[tri ? 3 : vloc ? 2 : half ? 1 : 0];
   if (nb == 0) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, 0);
@@ -49,7 +50,7 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
                                          const NearCoef<float>& nc, int terms, uint32_t* ccount,
                                          uint32_t* cstart, uint32_t* ctiles, int2* cmap, int2* catoms,
                                          long long cmap_cap, bool half, long long n_atoms, int stage,
-                                         int* err, cudaStream_t st, double* vloc) {
+                                         int* err, cudaStream_t st, double* vloc, bool tri) {
   if (n_cols == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   if (!(stage & 1)) {
@@ -62,6 +63,7 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
     if (stage == 2) return cudaGetLastError();
   }
   if (vloc && !half) return cudaErrorNotSupported;         // the virial is formed in the half form
+  if (tri && (vloc || !half)) return cudaErrorNotSupported; // triclinic: half form, no virial
   if (half) {
     // every result is accumulated with atomics
     e = cudaMemsetAsync(nearres, 0, (size_t)n_atoms * sizeof(float4), st);
@@ -74,9 +76,9 @@ cudaError_t Launch<float>::near_clusters(const SysDesc* sys, int nsys, long long
   // SM gets at least 4 clusters per warp
   const bool large = cmap_cap >= (long long)sms * kClusterWarpsLarge * 4;
   return large ? launch_near_cluster<kClusterWarpsLarge>(sys, n_cols, start, rel, nearres, nc, terms, cstart, cmap,
-                                                          catoms, cmap_cap, half, err, st, vloc, sms)
+                                                          catoms, cmap_cap, half, err, st, vloc, sms, tri)
                : launch_near_cluster<kClusterWarpsSmall>(sys, n_cols, start, rel, nearres, nc, terms, cstart, cmap,
-                                                          catoms, cmap_cap, half, err, st, vloc, sms);
+                                                          catoms, cmap_cap, half, err, st, vloc, sms, tri);
 }
 
 }  // namespace espk

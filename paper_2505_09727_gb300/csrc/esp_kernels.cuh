@@ -155,6 +155,24 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
   typename Types<real>::atom out;
   if constexpr (sizeof(real) == 4) {
     uint32_t u[3];
+    if (S.tri) {
+      // triclinic cell: u = floor(s 2^32) mod 2^32 of the fractional
+      // coordinates s = H^-1 r (H^-1 upper triangular)
+      const double* t = S.tfix;
+      const double sv[3] = {fma(p[0], t[0], fma(p[1], t[1], p[2] * t[2])), fma(p[1], t[3], p[2] * t[4]),
+                            p[2] * t[5]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        long long v = __double2ll_rd(sv[a]);
+        if (v == LLONG_MAX || v == LLONG_MIN) {   // saturated: |s| beyond 2^31
+          double f = sv[a] * 2.3283064365386962890625e-10;
+          f -= floor(f);
+          v = (long long)(f * 4294967296.0);
+        }
+        u[a] = (uint32_t)(unsigned long long)v;
+        c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
+      }
+    } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       // u = floor(x 2^32 / L) mod 2^32: one FP64 product rounded down to a
@@ -168,6 +186,7 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
       }
       u[a] = (uint32_t)(unsigned long long)v;
       c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
+    }
     }
     // slab: fractional position inside the z cell, in kSub parts
     const uint32_t zfrac = (uint32_t)((uint64_t)u[2] * (uint64_t)S.n_c);
@@ -323,6 +342,20 @@ __device__ inline float brick_relative(const SysDesc& S, uint32_t u) {
   const uint64_t in_brick = ((uint64_t)(c % (uint32_t)S.bc) << 32) | (uint32_t)t;
   return (float)((double)in_brick * S.w32);
 }
+// Triclinic cell: the position relative to the brick corner H (cx, cy,
+// bz bc) / n_c in Cartesian coordinates, H applied in FP64 to the exact
+// fixed-point fractions inside the cell (x, y) and the brick (z).
+__device__ inline float4 tri_relative(const SysDesc& S, uint4 a) {
+  const double f = 2.3283064365386962890625e-10;
+  const double fx = (double)(uint32_t)((uint64_t)a.x * (uint64_t)S.n_c) * f;
+  const double fy = (double)(uint32_t)((uint64_t)a.y * (uint64_t)S.n_c) * f;
+  const uint64_t t = (uint64_t)a.z * (uint64_t)S.n_c;
+  const uint32_t c = (uint32_t)(t >> 32);
+  const double fz = (double)(((uint64_t)(c % (uint32_t)S.bc) << 32) | (uint32_t)t) * f;
+  const double* e = S.tcell;     // a_x, b_x, b_y, c_x, c_y, c_z over n_c
+  return make_float4((float)fma(fx, e[0], fma(fy, e[1], fz * e[3])), (float)fma(fy, e[2], fz * e[4]),
+                     (float)(fz * e[5]), 0.f);
+}
 __device__ inline double brick_relative(const SysDesc&, double x) { return x; }
 // FP64 mode keeps absolute wrapped coordinates in the pair records, so pair
 // differences are the same FP64 subtractions as a plain minimum-image sum.
@@ -343,9 +376,19 @@ __global__ void __launch_bounds__(kChunk) k_scatter(
   const uint32_t dst = start[S.cell0 + key[i]] + rank[i];
   typename Types<real>::atom a = coord[i];
   typename Types<real>::res r;
-  r.x = cell_relative(S, a.x);
-  r.y = cell_relative(S, a.y);
-  r.z = brick_relative(S, a.z);
+  if constexpr (sizeof(real) == 4) {
+    if (S.tri) {
+      r = tri_relative(S, a);
+    } else {
+      r.x = cell_relative(S, a.x);
+      r.y = cell_relative(S, a.y);
+      r.z = brick_relative(S, a.z);
+    }
+  } else {
+    r.x = cell_relative(S, a.x);
+    r.y = cell_relative(S, a.y);
+    r.z = brick_relative(S, a.z);
+  }
   r.w = (real)q[i];
   if constexpr (sizeof(real) == 4) a.w = __float_as_uint((float)q[i]);
   else a.w = (double)q[i];
@@ -552,7 +595,9 @@ __global__ void __launch_bounds__(256) k_scale(
     const int ky = kyi < half ? kyi : kyi - n;
     const int kz = kzi < half ? kzi : kzi - n;
     const int m = kx * kx + ky * ky + kz * kz;
-    const real p = __ldg(G + m) * __ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz));
+    // cube: G over |k|^2; triclinic cell: G over the half spectrum itself
+    const long long gi = S.tri ? idx : (long long)m;
+    const real p = __ldg(G + gi) * __ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz));
     typename Types<real>::cplx v = sp[idx];
     const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
     e += wgt * (double)p * ((double)v.x * v.x + (double)v.y * v.y);
@@ -747,9 +792,17 @@ __global__ void __launch_bounds__(256) k_gather(
       gy += wzc * gyc;
     }
     out.x = u;
-    out.y = gx * inv_h;
-    out.z = gy * inv_h;
-    out.w = gz * inv_h;
+    if (sizeof(real) == 4 && S.tri) {
+      // triclinic cell: grad_r = n_f H^-T grad_t (H^-T lower triangular)
+      const float* m = S.tgrad;
+      out.y = gx * (real)m[0];
+      out.z = gx * (real)m[1] + gy * (real)m[2];
+      out.w = gx * (real)m[3] + gy * (real)m[4] + gz * (real)m[5];
+    } else {
+      out.y = gx * inv_h;
+      out.z = gy * inv_h;
+      out.w = gz * inv_h;
+    }
     far[i] = out;
   }
 }

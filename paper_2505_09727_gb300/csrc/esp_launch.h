@@ -45,7 +45,7 @@ struct Launch {
                                    const void* rel, void* nearres, const NearCoef<real>& nc, int terms,
                                    uint32_t* ccount, uint32_t* cstart, uint32_t* ctiles, int2* cmap,
                                    int2* catoms, long long cmap_cap, bool half, long long n_atoms, int stage,
-                                   int* err, cudaStream_t st, double* vloc = nullptr);
+                                   int* err, cudaStream_t st, double* vloc = nullptr, bool tri = false);
   static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                               const uint32_t* perm, const void* far, const void* nearres,
                               void* forces, void* pot, bool out_double, double* partials,

@@ -74,13 +74,20 @@ struct ClusterSmem {
 // warp over its clusters of one system and added to vloc[6 * system + c]
 // (xx, yy, zz, xy, xz, yz) with FP64 atomics when the system changes and at
 // the end.
-template <int NC, bool HALF, bool VIR, int WARPS>
+// TRI: triclinic cell. Cells are cells of fractional coordinates, a column
+// (ox, oy) away sits at ox a/n_c + oy b/n_c and a brick up the column at
+// bc c/n_c (Cartesian offsets), and the records hold Cartesian positions
+// relative to their brick corner. The z window is the cutoff around the box
+// in Cartesian z (z depends on the fractional z alone); columns are not
+// culled by their xy gap, every candidate passes the box filter.
+template <int NC, bool HALF, bool VIR, int WARPS, bool TRI = false>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     const SysDesc* __restrict__ sys, const int2* __restrict__ cmap, const int2* __restrict__ catoms,
     const uint32_t* __restrict__ n_clusters, const float4* __restrict__ rel,
     const uint32_t* __restrict__ start, float4* __restrict__ nearres, const NearCoef<float> nc,
     int* __restrict__ err, double* __restrict__ vloc = nullptr) {
   static_assert(HALF || !VIR, "the virial is formed in the half form");
+  static_assert(!(TRI && VIR), "no virial on a triclinic cell");
   constexpr int kClusterWarps = WARPS;
   __shared__ ClusterSmem<HALF> smem_all[kClusterWarps];
   const unsigned full = 0xffffffffu;
@@ -144,17 +151,40 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
     if (mine) {
       ri = rel[my_idx];
-      ri.z += (float)(my_bz - bz_0) * bcw;
+      if constexpr (TRI) {
+        const float dbz = (float)(my_bz - bz_0);
+        ri.x = fmaf(dbz, S.tbrick[0], ri.x);
+        ri.y = fmaf(dbz, S.tbrick[1], ri.y);
+        ri.z = fmaf(dbz, S.tbrick[2], ri.z);
+      } else {
+        ri.z += (float)(my_bz - bz_0) * bcw;
+      }
     }
-    // bounding box (all coordinates are >= 0 in this frame, so the float bit
-    // patterns order like the values)
-    const unsigned inf_bits = 0x7f800000u;
-    const float bx_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.x) : inf_bits));
-    const float by_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.y) : inf_bits));
-    const float bz_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.z) : inf_bits));
-    const float bx_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.x) : 0u));
-    const float by_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.y) : 0u));
-    const float bz_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.z) : 0u));
+    // bounding box. Cube: all coordinates are >= 0 in this frame, so the
+    // float bit patterns order like the values. Triclinic: x and y may be
+    // negative; the keys flip the sign bit (and the rest for negatives).
+    float bx_lo, by_lo, bz_lo, bx_hi, by_hi, bz_hi;
+    if constexpr (TRI) {
+      auto key = [](float v) {
+        const unsigned b = __float_as_uint(v);
+        return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+      };
+      auto unkey = [](unsigned k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); };
+      bx_lo = unkey(__reduce_min_sync(full, mine ? key(ri.x) : 0xffffffffu));
+      by_lo = unkey(__reduce_min_sync(full, mine ? key(ri.y) : 0xffffffffu));
+      bz_lo = unkey(__reduce_min_sync(full, mine ? key(ri.z) : 0xffffffffu));
+      bx_hi = unkey(__reduce_max_sync(full, mine ? key(ri.x) : 0u));
+      by_hi = unkey(__reduce_max_sync(full, mine ? key(ri.y) : 0u));
+      bz_hi = unkey(__reduce_max_sync(full, mine ? key(ri.z) : 0u));
+    } else {
+      const unsigned inf_bits = 0x7f800000u;
+      bx_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.x) : inf_bits));
+      by_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.y) : inf_bits));
+      bz_lo = __uint_as_float(__reduce_min_sync(full, mine ? __float_as_uint(ri.z) : inf_bits));
+      bx_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.x) : 0u));
+      by_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.y) : 0u));
+      bz_hi = __uint_as_float(__reduce_max_sync(full, mine ? __float_as_uint(ri.z) : 0u));
+    }
     // missing atoms (m < 8) sit far away with zero charge: every pair with
     // them is masked off, so the eight pair evaluations need no branch
     if (lane < kClusterAtoms)
@@ -169,7 +199,8 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     const float inv_rc2x2 = S.inv_rc2x2f, inv_rc3 = S.inv_rc3f;
     const float margin = 1e-4f * w;
     const float cull2 = rc2 + 2.f * margin * S.r_cf;
-    const float slab_per_len = (float)kSub / w;
+    // slabs per unit of z (cube: w per cell; triclinic: c_z / n_c per cell)
+    const float slab_per_len = TRI ? (float)kSub / (S.tbrick[2] * inv_bc) : (float)kSub / w;
     int qn = 0;                                   // queued candidates
     int nseg = 0, total = 0;                      // listed ranges, their candidates
 
@@ -258,9 +289,12 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
           const bool own = ox == 0 && oy == 0;
           bool use = ci < ncol;
           if constexpr (HALF) use = use && (oy > 0 || (oy == 0 && ox >= 0));
-          const float gx = fmax3(0.f, (float)ox * w - bx_hi, bx_lo - (float)(ox + 1) * w);
-          const float gy = fmax3(0.f, (float)oy * w - by_hi, by_lo - (float)(oy + 1) * w);
-          const float d2 = gx * gx + gy * gy;
+          float d2 = 0.f;
+          if constexpr (!TRI) {
+            const float gx = fmax3(0.f, (float)ox * w - bx_hi, bx_lo - (float)(ox + 1) * w);
+            const float gy = fmax3(0.f, (float)oy * w - by_hi, by_lo - (float)(oy + 1) * w);
+            d2 = gx * gx + gy * gy;
+          }
           const bool col_on = use && d2 < cull2;
           cur = 0;
           u_hi = -1;
@@ -274,8 +308,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
             yy = wrap_index(cy + oy, n_c);
             kxy = cell_key(S, xx, yy, 0);
           }
-          offx = (float)ox * w;
-          offy = (float)oy * w;
+          if constexpr (TRI) {
+            offx = fmaf((float)ox, S.tcol[0], (float)oy * S.tcol[1]);
+            offy = (float)oy * S.tcol[2];
+          } else {
+            offx = (float)ox * w;
+            offy = (float)oy * w;
+          }
           // HALF, own column: the first range runs from just after the
           // cluster's last atom to the window top inside that atom's brick;
           // the listing then continues with the next brick up
@@ -297,10 +336,12 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
         // one round: each lane with slabs left lists its next brick range
         long long pos = 0, end = 0;
         float offz = 0.f;
+        int dbrick = 0;                                             // TRI: bricks up from bz_0
         if (own_first) {
           pos = own_pos;
           end = own_end;
           offz = (float)(bz_last - bz_0) * bcw;
+          dbrick = bz_last - bz_0;
           own_first = false;
         } else if (cur <= u_hi) {
           const int ucell = cur >> 2;                               // kSub = 4
@@ -317,6 +358,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
           pos = st[k0 * kSub + (cur & 3)];
           end = st[k1 * kSub + (send & 3) + 1];
           offz = (float)(ubrick - bz_0) * bcw;
+          dbrick = ubrick - bz_0;
           cur = send + 1;
         }
         if (pos < end && (pos < a_lo || end > a_hi)) {
@@ -336,7 +378,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
           const int slot = nseg + __popc(bal & lt_mask);
           W.seg_pos[slot] = (uint32_t)pos;
           W.seg_pre[slot] = total + incl - cnt;
-          W.seg_off[slot] = make_float4(offx, offy, offz, 0.f);
+          if constexpr (TRI) {
+            const float db = (float)dbrick;
+            W.seg_off[slot] = make_float4(fmaf(db, S.tbrick[0], offx), fmaf(db, S.tbrick[1], offy),
+                                          db * S.tbrick[2], 0.f);
+          } else {
+            W.seg_off[slot] = make_float4(offx, offy, offz, 0.f);
+          }
         }
         nseg += __popc(bal);
         total += __shfl_sync(full, incl, 31);

@@ -270,6 +270,44 @@ static int tile_edge(const espk::SysDesc& d, int P, int precision) {
   return T;
 }
 
+// Cell count n_c <= nc_max (a multiple of the brick edge bc) and the tile edge
+// T of the spread and gather bricks. A brick is bc^3 cells; the choice prefers
+// a brick edge near 6.5 grid points (measured best for the spread and gather
+// tiles) among shapes that keep at least 90% of the finest admissible cell
+// count. L only feeds the FP64 tile bound (FP64 coordinates are Cartesian).
+static esp_status choose_bricks(int n_f, int nc_max, double L, int P, const esp_plan_opts& o, int& n_c, int& bc,
+                                int& T, std::string& msg) {
+  const int prec = o.precision;
+  n_c = bc = T = 0;
+  double best_score = -1e300;
+  const size_t rb = prec == ESP_FP32 ? 4 : 8;
+  for (int b = 1; b <= 8; ++b) {
+    if (o.brick_cells > 0 && b != o.brick_cells) continue;
+    const int nc = (nc_max / b) * b;
+    if (nc < b || nc == 0) continue;
+    espk::SysDesc d{};
+    d.n_f = n_f; d.n_c = nc; d.bc = b; d.nb = nc / b;
+    d.L = L; d.inv_h = n_f / L;
+    const int t = tile_edge(d, P, prec);
+    int tpy = 0, tpz = 0;
+    espk::tile_pitches(t, P, tpy, tpz);
+    const size_t tiles = o.diff == ESP_DIFF_IK ? 4 : 1;      // the ik gather holds four tiles
+    if ((size_t)tpz * t * rb * tiles > 200 * 1024) continue;
+    const double edge = (double)b * n_f / nc;            // brick edge in grid points
+    const double keep = (double)nc / nc_max;
+    double score = -std::fabs(std::log(edge / 6.5));
+    if (keep < 0.9) score -= 10.0 + (1.0 - keep) * 10.0;
+    if (score > best_score) { best_score = score; n_c = nc; bc = b; T = t; }
+  }
+  if (o.brick_cells > 0 && n_c == 0) {
+    // requested brick does not divide any usable cell count: use single-cell bricks
+    msg = "brick_cells incompatible with the cell grid";
+    return ESP_ERR_INVALID_ARG;
+  }
+  if (n_c == 0) { msg = "no brick/tile shape fits in shared memory"; return ESP_ERR_UNSUPPORTED; }
+  return ESP_OK;
+}
+
 esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts& o, HostPlan& hp,
                           std::string& msg) {
   if (!(L > 0.0) || !std::isfinite(L)) { msg = "box edge must be positive and finite"; return ESP_ERR_INVALID_ARG; }
@@ -382,37 +420,12 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     return ESP_ERR_UNSUPPORTED;
   }
   const int nc_max = std::max(1, (int)std::floor(reach * L / r_c * (1.0 - 1e-12)));
-  // brick = bc^3 cells; prefer a brick edge near 6.5 grid points (measured
-  // best for the spread and gather tiles) among shapes
-  // that keep at least 90% of the finest admissible cell count
   const double h = L / n_f;
   int n_c = 0, bc = 0, T = 0;
-  double best_score = -1e300;
-  const size_t rb = prec == ESP_FP32 ? 4 : 8;
-  for (int b = 1; b <= 8; ++b) {
-    if (o.brick_cells > 0 && b != o.brick_cells) continue;
-    const int nc = (nc_max / b) * b;
-    if (nc < b || nc == 0) continue;
-    espk::SysDesc d{};
-    d.n_f = n_f; d.n_c = nc; d.bc = b; d.nb = nc / b;
-    d.L = L; d.inv_h = n_f / L;
-    const int t = tile_edge(d, P, prec);
-    int tpy = 0, tpz = 0;
-    espk::tile_pitches(t, P, tpy, tpz);
-    const size_t tiles = o.diff == ESP_DIFF_IK ? 4 : 1;      // the ik gather holds four tiles
-    if ((size_t)tpz * t * rb * tiles > 200 * 1024) continue;
-    const double edge = (double)b * n_f / nc;            // brick edge in grid points
-    const double keep = (double)nc / nc_max;
-    double score = -std::fabs(std::log(edge / 6.5));
-    if (keep < 0.9) score -= 10.0 + (1.0 - keep) * 10.0;
-    if (score > best_score) { best_score = score; n_c = nc; bc = b; T = t; }
+  {
+    const esp_status bs = choose_bricks(n_f, nc_max, L, P, o, n_c, bc, T, msg);
+    if (bs != ESP_OK) return bs;
   }
-  if (o.brick_cells > 0 && n_c == 0) {
-    // requested brick does not divide any usable cell count: use single-cell bricks
-    msg = "brick_cells incompatible with the cell grid";
-    return ESP_ERR_INVALID_ARG;
-  }
-  if (n_c == 0) { msg = "no brick/tile shape fits in shared memory"; return ESP_ERR_UNSUPPORTED; }
 
   // descriptor
   espk::SysDesc& d = hp.desc;
@@ -423,6 +436,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.n_atoms = (int)N;
   d.gsize = 3 * (n_f / 2) * (n_f / 2) + 1;
   d.L = L; d.inv_L = 1.0 / L; d.h = h; d.inv_h = n_f / L;
+  d.vol = L * L * L;
   d.r_c = r_c; d.rc2 = r_c * r_c; d.inv_rc = 1.0 / r_c;
   d.inv_rc2 = d.inv_rc * d.inv_rc; d.inv_rc3 = d.inv_rc2 * d.inv_rc;
   d.w = L / n_c;
@@ -500,9 +514,162 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   return ESP_OK;
 }
 
+// ------------------------------------------------------------ triclinic cell
+// Influence over the half spectrum of a triclinic cell (Eq. pk with
+// |xi(k)| = 2 pi |H^-T k| and Phi in grid units per fractional axis):
+// G[idx] = chihat(r_c |xi|) / (|xi|^2 V) at the index order of the scale
+// kernel ([kz][ky][kx], kx in [0, n_f/2]). chihat of the PSWF split comes
+// from a cubic Hermite table in kappa (step 0.01; the fourth derivative of
+// chihat is bounded by int_0^1 x^4 chi <= 1, so the table error is below
+// 3e-11); the Gaussian split has its closed form.
+static void triclinic_influence(const espm::Split& split, int n_f, const double Hi[6], double V, double r_c,
+                                std::vector<double>& G) {
+  const int nh = n_f / 2 + 1, half = n_f / 2;
+  const double twopi = 2.0 * kPi;
+  auto xi2_of = [&](int kx, int ky, int kz) {
+    // H^-T k with H^-1 = [[i00, i01, i02], [0, i11, i12], [0, 0, i22]]
+    const double vx = Hi[0] * kx;
+    const double vy = Hi[1] * kx + Hi[3] * ky;
+    const double vz = Hi[2] * kx + Hi[4] * ky + Hi[5] * kz;
+    return twopi * twopi * (vx * vx + vy * vy + vz * vz);
+  };
+  double xi2_max = 0.0;
+  for (int kzi = 0; kzi < n_f; ++kzi)
+    for (int kyi = 0; kyi < n_f; ++kyi)
+      for (int kx = 0; kx < nh; ++kx) {
+        const int ky = kyi < half ? kyi : kyi - n_f, kz = kzi < half ? kzi : kzi - n_f;
+        xi2_max = std::max(xi2_max, xi2_of(kx, ky, kz));
+      }
+  const double step = 0.01;
+  const bool table = split.kind != 1;
+  std::vector<double> f, df;
+  if (table) {
+    const int nt = (int)std::ceil(r_c * std::sqrt(xi2_max) / step) + 2;
+    f.resize(nt);
+    df.resize(nt);
+    for (int i = 0; i < nt; ++i) {
+      f[i] = split.chihat(i * step);
+      df[i] = split.dchihat(i * step);
+    }
+  }
+  auto chihat = [&](double kappa) {
+    if (!table) return split.chihat(kappa);
+    const double x = kappa / step;
+    const int i = std::min((int)x, (int)f.size() - 2);
+    const double t = x - i, t2 = t * t, t3 = t2 * t;
+    return (2 * t3 - 3 * t2 + 1) * f[i] + (t3 - 2 * t2 + t) * step * df[i] + (-2 * t3 + 3 * t2) * f[i + 1] +
+           (t3 - t2) * step * df[i + 1];
+  };
+  G.assign((size_t)n_f * n_f * nh, 0.0);
+  size_t idx = 0;
+  for (int kzi = 0; kzi < n_f; ++kzi)
+    for (int kyi = 0; kyi < n_f; ++kyi)
+      for (int kx = 0; kx < nh; ++kx, ++idx) {
+        const int ky = kyi < half ? kyi : kyi - n_f, kz = kzi < half ? kzi : kzi - n_f;
+        const double xi2 = xi2_of(kx, ky, kz);
+        if (xi2 > 0.0) G[idx] = chihat(r_c * std::sqrt(xi2)) / xi2 / V;
+      }
+}
+
+esp_status make_host_plan_cell(const double cell[9], long long N, double tol, const esp_plan_opts& o,
+                               HostPlan& hp, std::string& msg) {
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(cell[i])) { msg = "cell vectors must be finite"; return ESP_ERR_INVALID_ARG; }
+  const double ax = cell[0], bx = cell[3], by = cell[4], cx = cell[6], cy = cell[7], cz = cell[8];
+  if (cell[1] != 0.0 || cell[2] != 0.0 || cell[5] != 0.0 || !(ax > 0) || !(by > 0) || !(cz > 0)) {
+    msg = "cell vectors must be a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz) with ax, by, cz > 0";
+    return ESP_ERR_INVALID_ARG;
+  }
+  if (o.precision != ESP_FP32) { msg = "triclinic cells need ESP_FP32"; return ESP_ERR_UNSUPPORTED; }
+  if (o.diff != ESP_DIFF_AD) { msg = "triclinic cells use AD forces"; return ESP_ERR_UNSUPPORTED; }
+  if (o.virial) { msg = "no virial on a triclinic cell"; return ESP_ERR_UNSUPPORTED; }
+  if (o.near_variant != 0 && o.near_variant != 4) {
+    msg = "triclinic cells need the default local-part kernel";
+    return ESP_ERR_UNSUPPORTED;
+  }
+  // heights (distances between opposite faces) and the longest cell vector
+  const double V = ax * by * cz;
+  const double la = ax, lb = std::sqrt(bx * bx + by * by), lc = std::sqrt(cx * cx + cy * cy + cz * cz);
+  const double bxc = std::sqrt((by * cz) * (by * cz) + (bx * cz) * (bx * cz) + (bx * cy - by * cx) * (bx * cy - by * cx));
+  const double cxa = ax * std::sqrt(cz * cz + cy * cy);
+  const double hx = V / bxc, hy = V / cxa, hz = cz;
+  const double h_min = std::min(hx, std::min(hy, hz));
+  const double L_eff = std::max(la, std::max(lb, lc));
+  // parameters from the cubic rules on the longest cell vector (the grid
+  // resolves every fractional axis at least as finely as a cube of that edge)
+  esp_plan_opts o2 = o;
+  if (!(o2.r_c > 0)) {
+    HostPlan probe;
+    const esp_status st = make_host_plan(L_eff, N, tol, o2, probe, msg);
+    if (st != ESP_OK) return st;
+    o2.r_c = std::min(probe.info.r_c, 0.45 * h_min);
+  }
+  const double r_c = o2.r_c;
+  if (!(r_c < 0.5 * h_min)) {
+    msg = "cutoff r_c must be smaller than half the smallest cell height";
+    return ESP_ERR_CUTOFF_TOO_LARGE;
+  }
+  esp_status st = make_host_plan(L_eff, N, tol, o2, hp, msg);
+  if (st != ESP_OK) return st;
+  const int n_f = hp.info.n_f, P = hp.info.P;
+  if (n_f > 384) {
+    msg = "grid too large for a triclinic influence array (n_f > 384): raise r_c or the tolerance";
+    return ESP_ERR_UNSUPPORTED;
+  }
+  // cells of fractional coordinates: a pair within r_c is at most r_c n_c / h_a
+  // cells apart along axis a, so n_c <= reach h_min / r_c keeps it within reach
+  const int reach = hp.desc.reach;
+  const int nc_max = std::max(1, (int)std::floor(reach * h_min / r_c * (1.0 - 1e-12)));
+  int n_c = 0, bc = 0, T = 0;
+  st = choose_bricks(n_f, nc_max, L_eff, P, o2, n_c, bc, T, msg);
+  if (st != ESP_OK) return st;
+
+  espk::SysDesc& d = hp.desc;
+  d.n_c = n_c; d.bc = bc; d.nb = n_c / bc; d.T = T;
+  espk::tile_pitches(T, P, d.tpy, d.tpz);
+  d.w = h_min / n_c;                 // smallest cell height (margins of the local part)
+  d.wf = (float)d.w;
+  d.w32 = d.w / 4294967296.0;
+  d.w32f = d.wf * 2.3283064365386962890625e-10f;
+  d.inv_bcf = (float)(1.0 / bc);
+  d.vol = V;
+  d.tri = 1;
+  const double Hi[6] = {1.0 / ax, -bx / (ax * by), (bx * cy - by * cx) / (ax * by * cz),
+                        1.0 / by, -cy / (by * cz), 1.0 / cz};
+  for (int k = 0; k < 6; ++k) d.tfix[k] = 4294967296.0 * Hi[k];
+  const double e[6] = {ax, bx, by, cx, cy, cz};
+  for (int k = 0; k < 6; ++k) d.tcell[k] = e[k] / n_c;
+  // n_f H^-T, lower triangle row by row: (xx), (yx, yy), (zx, zy, zz)
+  const double g[6] = {Hi[0], Hi[1], Hi[3], Hi[2], Hi[4], Hi[5]};
+  for (int k = 0; k < 6; ++k) d.tgrad[k] = (float)(n_f * g[k]);
+  d.tcol[0] = (float)(ax / n_c);
+  d.tcol[1] = (float)(bx / n_c);
+  d.tcol[2] = (float)(by / n_c);
+  d.tbrick[0] = (float)(bc * cx / n_c);
+  d.tbrick[1] = (float)(bc * cy / n_c);
+  d.tbrick[2] = (float)(bc * cz / n_c);
+
+  // influence over the whole half spectrum (no virial table)
+  const espm::Split split = o2.kernel == ESP_KERNEL_PSWF ? cached_pswf_split(hp.info.c)
+                                                         : espm::make_gauss_split(hp.info.alpha);
+  triclinic_influence(split, n_f, Hi, V, r_c, hp.G);
+  d.gsize = (int)hp.G.size();
+  hp.H.clear();
+  hp.n_keys = (long long)n_c * n_c * n_c * espk::kSub;
+  hp.n_bricks = d.nb * d.nb * d.nb;
+
+  esp_plan_params& info = hp.info;
+  info.L = L_eff;
+  info.n_cells = n_c;
+  info.brick_cells = bc;
+  info.tile = T;
+  info.triclinic = 1;
+  return ESP_OK;
+}
+
 void charge_constants(const HostPlan& hp, double Q, double Q2, double* e_self, double* e_bg,
                       double* bg_shift) {
-  const double L = hp.desc.L, V = L * L * L, r_c = hp.desc.r_c;
+  const double V = hp.desc.vol, r_c = hp.desc.r_c;
   const double shift = -(Q / V) * 0.5 * r_c * r_c * hp.m2;
   *bg_shift = shift;
   *e_self = -0.5 * Q2 * hp.self_unit;

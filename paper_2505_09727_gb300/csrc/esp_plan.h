@@ -37,6 +37,11 @@ struct HostPlan {
 esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts& opts, HostPlan& hp,
                           std::string& msg);
 
+// The same for a triclinic cell: rows a, b, c of cell[9] with a = (ax,0,0),
+// b = (bx,by,0), c = (cx,cy,cz). FP32 only, AD forces, no virial.
+esp_status make_host_plan_cell(const double cell[9], long long N, double tol, const esp_plan_opts& opts,
+                               HostPlan& hp, std::string& msg);
+
 // Message reported by esp_last_error() for the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -39,6 +39,10 @@ class esp_box(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double * 3)]
 
 
+class esp_cell(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double * 3), ("b", ctypes.c_double * 3), ("c", ctypes.c_double * 3)]
+
+
 class esp_plan_opts(ctypes.Structure):
     _fields_ = [
         ("r_c", ctypes.c_double), ("P", ctypes.c_int), ("n_f", ctypes.c_int),
@@ -62,7 +66,7 @@ class esp_plan_params(ctypes.Structure):
         ("cell_reach", ctypes.c_int), ("near_terms", ctypes.c_int),
         ("brick_cells", ctypes.c_int), ("tile", ctypes.c_int), ("si_degree", ctypes.c_int),
         ("near_degree", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("window", ctypes.c_int),
-        ("diff", ctypes.c_int), ("virial", ctypes.c_int), ("reserved", ctypes.c_int * 1),
+        ("diff", ctypes.c_int), ("virial", ctypes.c_int), ("triclinic", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -97,6 +101,10 @@ _SIGNATURES = {
     "esp_plan": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
                                 ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
     "esp_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(esp_plan_params)]),
+    "esp_plan_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
+                                     ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
+    "esp_plan_query_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
+                                           ctypes.POINTER(esp_plan_opts), ctypes.POINTER(esp_plan_params)]),
     "esp_plan_query": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
                                       ctypes.POINTER(esp_plan_opts), ctypes.POINTER(esp_plan_params)]),
     "esp_set_charges": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -222,6 +230,37 @@ def esp_plan_query(L: float, N: int, tolerance: float, opts: esp_plan_opts | Non
     p = esp_plan_params()
     _check(load_library().esp_plan_query(ctypes.byref(box), int(N), float(tolerance), ctypes.byref(opts),
                                          ctypes.byref(p)))
+    return p.as_dict()
+
+
+def _cell(H) -> esp_cell:
+    """esp_cell from the 3x3 box matrix H whose columns are the cell vectors."""
+    H = np.asarray(H, dtype=np.float64)
+    if H.shape != (3, 3):
+        raise ValueError("H must be 3x3 (columns a, b, c)")
+    d3 = ctypes.c_double * 3
+    return esp_cell(d3(*H[:, 0]), d3(*H[:, 1]), d3(*H[:, 2]))
+
+
+def esp_plan_cell(H, N: int, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> int:
+    """Plan for a triclinic cell; H has the cell vectors a, b, c as columns."""
+    if opts is None:
+        opts = make_opts(**kw)
+    cell = _cell(H)
+    out = _P()
+    _check(load_library().esp_plan_cell(ctypes.byref(cell), int(N), float(tolerance), ctypes.byref(opts),
+                                        ctypes.byref(out)))
+    return out.value
+
+
+def esp_plan_query_cell(H, N: int, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> dict:
+    """Planner only for a triclinic cell (no GPU needed)."""
+    if opts is None:
+        opts = make_opts(**kw)
+    cell = _cell(H)
+    p = esp_plan_params()
+    _check(load_library().esp_plan_query_cell(ctypes.byref(cell), int(N), float(tolerance), ctypes.byref(opts),
+                                              ctypes.byref(p)))
     return p.as_dict()
 
 
@@ -432,8 +471,12 @@ def esp_version() -> str:
 class Plan:
     """Owning handle: plan + host-side convenience (host arrays in, host arrays out)."""
 
-    def __init__(self, L: float, N: int, tolerance: float, **opts):
-        self.handle = esp_plan(L, N, tolerance, **opts)
+    def __init__(self, L, N: int, tolerance: float, **opts):
+        """L: cube edge, or a 3x3 box matrix (columns a, b, c) for a triclinic cell."""
+        if np.ndim(L) == 2:
+            self.handle = esp_plan_cell(L, N, tolerance, **opts)
+        else:
+            self.handle = esp_plan(L, N, tolerance, **opts)
         self.N = int(N)
 
     @property

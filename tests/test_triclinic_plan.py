@@ -1,0 +1,92 @@
+"""The triclinic planner (esp_plan_query_cell) without a GPU.
+
+* A diagonal cell L I chooses the cube's parameters (c, c1, P, n_f, r_c and
+  the cell list) and marks the plan triclinic.
+* A sheared cell takes c, P and n_f from the cubic rules on its longest cell
+  vector, and a cell list whose reach covers r_c across the smallest height.
+* Cells outside the reduced orientation, cutoffs of half the smallest height
+  or more, and options the triclinic path does not have are refused.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import params as oparams
+from oracle import triclinic as tr
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_09727_gb300 import _build, esp
+    _build.build()
+    return esp
+
+
+SHEARED = tr.box_matrix([4.2, 0, 0], [1.1, 4.0, 0], [-0.8, 0.9, 3.9])
+
+
+def _dodecahedron(d):
+    """Rhombic dodecahedron (xy-square form) of nearest-image distance d."""
+    return tr.box_matrix([d, 0, 0], [0, d, 0], [d / 2, d / 2, d * math.sqrt(2) / 2])
+
+
+def _octahedron(d):
+    """Truncated octahedron of nearest-image distance d."""
+    return tr.box_matrix([d, 0, 0], [d / 3, 2 * math.sqrt(2) * d / 3, 0],
+                         [-d / 3, math.sqrt(2) * d / 3, math.sqrt(6) * d / 3])
+
+
+def test_diagonal_cell_chooses_the_cube_parameters(lib):
+    L, N, eps = 6.0, 20_000, 1e-4
+    cube = lib.esp_plan_query(L, N, eps, r_c=1.0)
+    cell = lib.esp_plan_query_cell(L * np.eye(3), N, eps, r_c=1.0)
+    for k in ("c", "c1", "P", "n_f", "r_c", "n_cells", "brick_cells", "tile", "cell_reach"):
+        assert cell[k] == cube[k], k
+    assert cell["triclinic"] == 1 and cube["triclinic"] == 0
+    # the influence array covers the half spectrum instead of |k|^2
+    n = cube["n_f"]
+    assert cell["device_bytes"] - cube["device_bytes"] == 4 * (n * n * (n // 2 + 1) - (3 * (n // 2) ** 2 + 1)) \
+        - 4 * (3 * (n // 2) ** 2 + 1)
+
+
+@pytest.mark.parametrize("H", [SHEARED, _dodecahedron(5.0), _octahedron(5.5), np.diag([4.0, 5.0, 6.5])],
+                         ids=["sheared", "dodecahedron", "octahedron", "orthorhombic"])
+@pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-5])
+def test_cell_parameters_follow_the_longest_vector(lib, H, eps):
+    r_c = 1.1
+    got = lib.esp_plan_query_cell(H, 5000, eps, r_c=r_c)
+    L_eff = float(np.max(np.linalg.norm(H, axis=0)))
+    cube = lib.esp_plan_query(L_eff, 5000, eps, r_c=r_c)
+    want = oparams.plan(eps, L_eff, r_c)
+    assert abs(got["c"] - want["c"]) < 1e-9 * want["c"]
+    assert got["P"] == want["P"] and got["n_f"] == cube["n_f"] and got["c1"] == cube["c1"]
+    assert got["L"] == pytest.approx(L_eff, rel=1e-15)
+    # every pair within r_c lies within cell_reach cells along each axis
+    h_min = float(np.min(tr.heights(H)))
+    assert got["n_cells"] * r_c <= got["cell_reach"] * h_min
+    assert got["n_cells"] % got["brick_cells"] == 0
+
+
+def test_automatic_cutoff_fits_the_cell(lib):
+    H = _octahedron(4.0)
+    got = lib.esp_plan_query_cell(H, 3000, 1e-4)
+    assert 0 < got["r_c"] <= 0.45 * float(np.min(tr.heights(H))) + 1e-12
+
+
+@pytest.mark.parametrize("H,kw,status", [
+    (np.array([[4.0, 0, 0], [0.1, 4.0, 0], [0, 0, 4.0]]), {}, 1),     # a has a y component
+    (SHEARED.T, {}, 1),                                                  # lower-triangular columns
+    (np.diag([4.0, -4.0, 4.0]), {}, 1),
+    (np.diag([4.0, 4.0, np.nan]), {}, 1),
+    (SHEARED, dict(r_c=2.0), 2),                                         # beyond half the smallest height
+    (SHEARED, dict(precision=1), 10),
+    (SHEARED, dict(diff=1), 10),
+    (SHEARED, dict(virial=1), 10),
+    (SHEARED, dict(near_variant=2), 10),
+])
+def test_cell_refusals(lib, H, kw, status):
+    kw = dict(dict(r_c=1.0), **kw)
+    with pytest.raises(lib.EspError) as exc:
+        lib.esp_plan_query_cell(H, 1000, 1e-4, **kw)
+    assert exc.value.status == status
