@@ -188,6 +188,19 @@ esp_status esp_plan_cell(const esp_cell* cell, int64_t N, double tolerance,
 esp_status esp_plan_query_cell(const esp_cell* cell, int64_t N, double tolerance,
                                const esp_plan_opts* opts, esp_plan_params* out);
 
+/* The influence function p_k (Eq. pk) the plan of (box or cell, N,
+ * tolerance, opts) would apply, in FP64 from the host planner (no GPU
+ * needed): out[(kz * n_f + ky) * (n_f/2 + 1) + kx] for the half spectrum of
+ * the forward transform sum_l b_l exp(-2 pi i k.l / n_f) of the grid
+ * b[z][y][x] (x fastest), index i standing for k = i below n_f/2 and
+ * i - n_f from n_f/2 on. Where a component is -n_f/2 the value is the
+ * average over k and the representative of -k (equal for a cube). Pass
+ * exactly one of box and cell. *len: in, the capacity of out; out, the
+ * number of entries n_f^2 (n_f/2 + 1). out may be NULL to query *len only.
+ * ESP_ERR_INVALID_ARG if the capacity is too small. */
+esp_status esp_influence_query(const esp_box* box, const esp_cell* cell, int64_t N, double tolerance,
+                               const esp_plan_opts* opts, double* out, int64_t* len);
+
 /* Charges q[N] (double or float). Must be called before the first compute
  * and whenever charges change. */
 esp_status esp_set_charges(esp_plan_t plan, const double* q, int where);

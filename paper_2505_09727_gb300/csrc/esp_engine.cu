@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -940,6 +941,35 @@ esp_status esp_plan_query_cell(const esp_cell* cell, int64_t N, double tolerance
                                esp_plan_params* out) {
   if (!cell) return fail(ESP_ERR_INVALID_ARG, "cell must not be NULL");
   return query_single(nullptr, cell, N, tolerance, opts, out);
+}
+
+esp_status esp_influence_query(const esp_box* box, const esp_cell* cell, int64_t N, double tolerance,
+                               const esp_plan_opts* opts, double* out, int64_t* len) {
+  if (!len || (!box) == (!cell)) return fail(ESP_ERR_INVALID_ARG, "pass exactly one of box and cell, and len");
+  const esp_plan_opts o = resolve_opts(opts);
+  if (box && !cubic(*box)) return fail(ESP_ERR_INVALID_ARG, "only cubic boxes are supported (L[0] = L[1] = L[2])");
+  espe::HostPlan hp;
+  std::string msg;
+  esp_status s = box ? espe::make_host_plan(box->L[0], N, tolerance, o, hp, msg)
+                     : espe::make_host_plan_cell(&cell->a[0], N, tolerance, o, hp, msg);
+  if (s != ESP_OK) return fail(s, msg);
+  const int n = hp.desc.n_f, nh = n / 2 + 1, half = n / 2;
+  const int64_t total = (int64_t)n * n * nh;
+  const int64_t cap = *len;
+  *len = total;
+  if (!out) return ESP_OK;
+  if (cap < total) return fail(ESP_ERR_INVALID_ARG, "out holds fewer than n_f^2 (n_f/2 + 1) entries");
+  const bool tri = hp.desc.tri != 0;
+  int64_t idx = 0;
+  for (int kzi = 0; kzi < n; ++kzi)
+    for (int kyi = 0; kyi < n; ++kyi)
+      for (int kx = 0; kx < nh; ++kx, ++idx) {
+        // the scale kernel's product, in FP64
+        const int ky = kyi < half ? kyi : kyi - n, kz = kzi < half ? kzi : kzi - n;
+        const double g = tri ? hp.G[idx] : hp.G[kx * kx + ky * ky + kz * kz];
+        out[idx] = g * hp.W[kx] * hp.W[std::abs(ky)] * hp.W[std::abs(kz)];
+      }
+  return ESP_OK;
 }
 
 esp_status esp_plan_info(esp_plan_t p, esp_plan_params* out) {

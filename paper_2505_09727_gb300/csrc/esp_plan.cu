@@ -518,10 +518,15 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
 // Influence over the half spectrum of a triclinic cell (Eq. pk with
 // |xi(k)| = 2 pi |H^-T k| and Phi in grid units per fractional axis):
 // G[idx] = chihat(r_c |xi|) / (|xi|^2 V) at the index order of the scale
-// kernel ([kz][ky][kx], kx in [0, n_f/2]). chihat of the PSWF split comes
-// from a cubic Hermite table in kappa (step 0.01; the fourth derivative of
-// chihat is bounded by int_0^1 x^4 chi <= 1, so the table error is below
-// 3e-11); the Gaussian split has its closed form.
+// kernel ([kz][ky][kx], kx in [0, n_f/2]), with the mode set
+// k_a in {-n_f/2, ..., n_f/2 - 1}. On a sheared lattice |xi(k)| is not even
+// in a single component, so where a component is -n_f/2 the mode and the
+// representative of -k carry different values; the real part of the inverse
+// transform averages them, and G holds that average (the scaled spectrum is
+// then exactly Hermitian, as the C2R transform assumes). chihat of the PSWF
+// split comes from a cubic Hermite table in kappa (step 0.01; the fourth
+// derivative of chihat is bounded by int_0^1 x^4 chi <= 1, so the table
+// error is below 3e-11); the Gaussian split has its closed form.
 static void triclinic_influence(const espm::Split& split, int n_f, const double Hi[6], double V, double r_c,
                                 std::vector<double>& G) {
   const int nh = n_f / 2 + 1, half = n_f / 2;
@@ -533,13 +538,13 @@ static void triclinic_influence(const espm::Split& split, int n_f, const double 
     const double vz = Hi[2] * kx + Hi[4] * ky + Hi[5] * kz;
     return twopi * twopi * (vx * vx + vy * vy + vz * vz);
   };
+  // signed component of an index, and of the representative of its negative
+  auto comp = [&](int i) { return i < half ? i : i - n_f; };
+  auto neg = [&](int k) { return k == -half ? -half : -k; };
   double xi2_max = 0.0;
-  for (int kzi = 0; kzi < n_f; ++kzi)
-    for (int kyi = 0; kyi < n_f; ++kyi)
-      for (int kx = 0; kx < nh; ++kx) {
-        const int ky = kyi < half ? kyi : kyi - n_f, kz = kzi < half ? kzi : kzi - n_f;
-        xi2_max = std::max(xi2_max, xi2_of(kx, ky, kz));
-      }
+  for (int kz = -half; kz < half; ++kz)
+    for (int ky = -half; ky < half; ++ky)
+      for (int kx = -half; kx < half; ++kx) xi2_max = std::max(xi2_max, xi2_of(kx, ky, kz));
   const double step = 0.01;
   const bool table = split.kind != 1;
   std::vector<double> f, df;
@@ -560,14 +565,18 @@ static void triclinic_influence(const espm::Split& split, int n_f, const double 
     return (2 * t3 - 3 * t2 + 1) * f[i] + (t3 - 2 * t2 + t) * step * df[i] + (-2 * t3 + 3 * t2) * f[i + 1] +
            (t3 - t2) * step * df[i + 1];
   };
+  auto p_of = [&](int kx, int ky, int kz) {
+    const double xi2 = xi2_of(kx, ky, kz);
+    return xi2 > 0.0 ? chihat(r_c * std::sqrt(xi2)) / xi2 / V : 0.0;
+  };
   G.assign((size_t)n_f * n_f * nh, 0.0);
   size_t idx = 0;
   for (int kzi = 0; kzi < n_f; ++kzi)
     for (int kyi = 0; kyi < n_f; ++kyi)
-      for (int kx = 0; kx < nh; ++kx, ++idx) {
-        const int ky = kyi < half ? kyi : kyi - n_f, kz = kzi < half ? kzi : kzi - n_f;
-        const double xi2 = xi2_of(kx, ky, kz);
-        if (xi2 > 0.0) G[idx] = chihat(r_c * std::sqrt(xi2)) / xi2 / V;
+      for (int kxi = 0; kxi < nh; ++kxi, ++idx) {
+        const int kx = comp(kxi), ky = comp(kyi), kz = comp(kzi);
+        const double p = p_of(kx, ky, kz);
+        G[idx] = (kx == -half || ky == -half || kz == -half) ? 0.5 * (p + p_of(neg(kx), neg(ky), neg(kz))) : p;
       }
 }
 

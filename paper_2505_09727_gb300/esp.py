@@ -105,6 +105,9 @@ _SIGNATURES = {
                                      ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
     "esp_plan_query_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
                                            ctypes.POINTER(esp_plan_opts), ctypes.POINTER(esp_plan_params)]),
+    "esp_influence_query": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.POINTER(esp_cell), ctypes.c_int64,
+                                           ctypes.c_double, ctypes.POINTER(esp_plan_opts), _D,
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "esp_plan_query": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
                                       ctypes.POINTER(esp_plan_opts), ctypes.POINTER(esp_plan_params)]),
     "esp_set_charges": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -262,6 +265,30 @@ def esp_plan_query_cell(H, N: int, tolerance: float, opts: esp_plan_opts | None 
     _check(load_library().esp_plan_query_cell(ctypes.byref(cell), int(N), float(tolerance), ctypes.byref(opts),
                                               ctypes.byref(p)))
     return p.as_dict()
+
+
+def esp_influence_query(L_or_H, N: int, tolerance: float, opts: esp_plan_opts | None = None, **kw) -> np.ndarray:
+    """The influence function p_k of the plan (host planner, no GPU needed), as
+    an array [kz][ky][kx] over the half spectrum (kx in [0, n_f/2])."""
+    if opts is None:
+        opts = make_opts(**kw)
+    lib = load_library()
+    if np.ndim(L_or_H) == 2:
+        box, cell = None, ctypes.byref(_cell(L_or_H))
+    else:
+        L = float(L_or_H)
+        box, cell = ctypes.byref(esp_box((ctypes.c_double * 3)(L, L, L))), None
+    n = ctypes.c_int64(0)
+    _check(lib.esp_influence_query(box, cell, int(N), float(tolerance), ctypes.byref(opts), None, ctypes.byref(n)))
+    out = np.zeros(n.value)
+    _check(lib.esp_influence_query(box, cell, int(N), float(tolerance), ctypes.byref(opts),
+                                   out.ctypes.data_as(_D), ctypes.byref(n)))
+    n_f = round((2 * n.value) ** (1.0 / 3.0))
+    while n_f * n_f * (n_f // 2 + 1) > n.value:
+        n_f -= 1
+    while n_f * n_f * (n_f // 2 + 1) < n.value:
+        n_f += 1
+    return out.reshape(n_f, n_f, n_f // 2 + 1)
 
 
 def esp_plan_info(plan: int) -> dict:

@@ -90,3 +90,55 @@ def test_cell_refusals(lib, H, kw, status):
     with pytest.raises(lib.EspError) as exc:
         lib.esp_plan_query_cell(H, 1000, 1e-4, **kw)
     assert exc.value.status == status
+
+
+def _oracle_influence(H, n_f, info):
+    """p_k from the oracle's split and window (Eq. pk on the lattice H) at
+    the GPU layout's modes, averaged with the representative of -k where a
+    component is -n_f/2 (the real part of the inverse transform)."""
+    from oracle import esp as oesp
+    p = oesp.ESPParams(1e-4, info["r_c"], info["P"], n_f, c=info["c"], c1=info["c1"])
+    split, window = p.split(), p.si_window()
+    V = abs(np.linalg.det(H))
+    Hi = np.linalg.inv(H)
+    half = n_f // 2
+    comp = np.where(np.arange(n_f) < half, np.arange(n_f), np.arange(n_f) - n_f)
+
+    def p_of(kx, ky, kz):
+        K = np.stack([kx, ky, kz], axis=-1).astype(np.float64)
+        xi = 2 * math.pi * K @ Hi
+        x = np.sqrt(np.sum(xi * xi, axis=-1))
+        Phi = window.Phi(2 * math.pi * np.stack([kx, ky, kz], -1) / n_f)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = np.where(x > 0, split.chihat(info["r_c"] * x) / np.where(x > 0, x, 1.0) ** 2, 0.0)
+        return s / (V * np.prod(Phi, axis=-1) ** 2)
+
+    kz, ky, kx = np.meshgrid(comp, comp, comp[:half + 1], indexing="ij")
+    kx = np.where(kx == half, -half, kx)
+    neg = lambda k: np.where(k == -half, -half, -k)
+    weight = np.prod(window.Phi(2 * math.pi * np.stack([kx, ky, kz], -1) / n_f), axis=-1) ** 2
+    return 0.5 * (p_of(kx, ky, kz) + p_of(neg(kx), neg(ky), neg(kz))), weight
+
+
+@pytest.mark.parametrize("H", [SHEARED, _dodecahedron(5.5), _octahedron(5.0), np.diag([4.0, 5.0, 6.5]),
+                               4.6 * np.eye(3)], ids=["sheared", "dodecahedron", "octahedron", "orthorhombic", "cube"])
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+def test_influence_matches_the_oracle(lib, H, eps):
+    """The planner's influence array (Hermite-tabulated chihat, per-axis
+    window factors, the Nyquist average) against the oracle's Eq. pk."""
+    r_c = 1.1
+    got = lib.esp_influence_query(H, 700, eps, r_c=r_c)
+    info = lib.esp_plan_query_cell(H, 700, eps, r_c=r_c)
+    want, weight = _oracle_influence(H, info["n_f"], info)
+    assert got.shape == want.shape
+    # compared as Shat / V = p Phi^6: near the corner modes chihat is ~1e-12
+    # of chihat(0), the two sides' quadratures differ there in the last
+    # digits, and 1/Phi^6 (up to ~1e10 at P = 8) would magnify that; the
+    # spread and gather multiply p_k by Phi^6 again, so this is the scale
+    # that reaches the potentials
+    err = np.max(np.abs(got - want) * weight)
+    assert err <= 1e-10 * np.max(np.abs(want) * weight)
+    # a cube plan applies the same values
+    if np.allclose(H, H[0, 0] * np.eye(3)):
+        cube = lib.esp_influence_query(H[0, 0], 700, eps, r_c=r_c)
+        assert np.max(np.abs(cube - got) * weight) <= 1e-10 * np.max(np.abs(want) * weight)

@@ -11,8 +11,8 @@ Two comparisons with the plan-based path on the same inputs:
   * Gaussian split with alpha = 1e-12: the spectral part vanishes
     identically (exp(-kappa^2/(4 alpha)) underflows to 0 for every k != 0), so
     the plan-based energy, forces and potential are the local part alone.
-This file is collected last (test_zz_*), so a run that stops at the first
-failure has already run every other test.
+This file is collected after the others but the triclinic tests (test_zz_*),
+so a run that stops at the first failure has already run the cubic paths.
 """
 import numpy as np
 import pytest

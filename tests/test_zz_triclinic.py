@@ -10,6 +10,10 @@ ESP and Ewald.
   energy within the tolerance and vanishing forces.
 * Coordinates shifted by lattice vectors give the same results; esp_step
   (graph replay) equals esp_compute.
+
+The triclinic path is the newest on the GPU, so this file is collected after
+every other (test_zz_*): a run that stops at the first failure has run the
+rest first.
 """
 import math
 
