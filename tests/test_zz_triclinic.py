@@ -107,8 +107,14 @@ def test_cell_matches_the_oracle(esp, name):
     assert g["info"]["triclinic"] == 1
     o = oracle_cell(H, pos, q, eps, g["info"])
     assert rel_rms(g["forces"], o["forces"]) <= FP32_PARITY
-    assert abs(g["energy"] - o["energy"]) <= FP32_PARITY * abs(o["energy"])
-    assert np.max(np.abs(g["potential"] - o["potential"])) <= FP32_PARITY * np.max(np.abs(o["potential"]))
+    # as for the cube: the FP32 spectral potential still holds each charge's
+    # smooth self-interaction (removed afterwards in FP64), so its rounding
+    # scales with the self energy, which for random charges exceeds |E|
+    e_self = -0.5 * float(np.sum(q * q)) * oesp.ESPParams(
+        eps, g["info"]["r_c"], g["info"]["P"], g["info"]["n_f"], c=g["info"]["c"]).split().chi0 \
+        / (4 * math.pi * g["info"]["r_c"])
+    assert abs(g["energy"] - o["energy"]) <= FP32_PARITY * max(abs(o["energy"]), abs(e_self))
+    assert rel_rms(g["potential"], o["potential"]) <= FP32_PARITY
 
 
 @pytest.mark.parametrize("name", ["sheared", "octahedron_eps1e-5"])
