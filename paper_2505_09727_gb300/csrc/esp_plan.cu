@@ -69,20 +69,53 @@ static espm::Window cached_window(double c1, int P) {
   return w;
 }
 
+// chihat(r_c xi_m) at the radial modes xi_m = 2 pi sqrt(m) / L of a cube
+// (m = |k|^2), evaluated once per m and shared by the aliasing estimates of
+// every grid size tried and the influence table.
+class RadialChihat {
+ public:
+  RadialChihat(const espm::Split& s, double L, double r_c) : s_(s), L_(L), r_c_(r_c) {}
+  double operator()(int m) {
+    while ((int)v_.size() <= m) {
+      const double xi = 2.0 * kPi * std::sqrt((double)v_.size()) / L_;
+      v_.push_back(s_.chihat(r_c_ * xi));
+    }
+    return v_[m];
+  }
+
+ private:
+  const espm::Split& s_;
+  double L_, r_c_;
+  std::vector<double> v_;
+};
+
 // Sum over ky, kz of |chihat(2 pi r_c |k| / L)| / |k|^2 for each kx in I.
-static std::vector<double> alias_rows(const espm::Split& s, int n_f, double L, double r_c) {
+static std::vector<double> alias_rows(RadialChihat& chi, int n_f) {
   const int h = n_f / 2;
   const int mmax = 3 * h * h;
   std::vector<double> base(mmax + 1, 0.0);
-  for (int m = 1; m <= mmax; ++m)
-    base[m] = std::fabs(s.chihat(2.0 * kPi * r_c * std::sqrt((double)m) / L)) / m;
-  // S2[q] = sum_{ky,kz} base[q + ky^2 + kz^2]
+  chi(mmax);
+  for (int m = 1; m <= mmax; ++m) base[m] = std::fabs(chi(m)) / m;
+  // rows[kx] = sum_{ky,kz} base[kx^2 + ky^2 + kz^2] = sum_s n(s) base[kx^2 + s]
+  // with n(s) the number of (ky, kz) in [-h, h)^2 with ky^2 + kz^2 = s (most
+  // s are no sum of two squares), and rows even in kx
+  std::vector<int> count(2 * h * h + 1, 0);
+  for (int ky = -h; ky < h; ++ky)
+    for (int kz = -h; kz < h; ++kz) ++count[ky * ky + kz * kz];
+  std::vector<int> sums;
+  std::vector<double> mult;
+  for (int v = 0; v <= 2 * h * h; ++v)
+    if (count[v]) {
+      sums.push_back(v);
+      mult.push_back((double)count[v]);
+    }
   std::vector<double> rows(n_f, 0.0);
-  for (int kx = -h; kx < h; ++kx) {
+  for (int k = 0; k <= h; ++k) {
+    const double* b = base.data() + k * k;
     double r = 0.0;
-    for (int ky = -h; ky < h; ++ky)
-      for (int kz = -h; kz < h; ++kz) r += base[kx * kx + ky * ky + kz * kz];
-    rows[kx + h] = r;
+    for (size_t i = 0; i < sums.size(); ++i) r += mult[i] * b[sums[i]];
+    if (k < h) rows[h + k] = r;        // kx = k
+    rows[h - k] = r;                   // kx = -k (k = h: the -n_f/2 row)
   }
   return rows;
 }
@@ -351,6 +384,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   if (!(r_c < 0.5 * L)) { msg = "cutoff r_c must be smaller than L/2"; return ESP_ERR_CUTOFF_TOO_LARGE; }
 
   // grid size and SI-kernel shape
+  RadialChihat chi(split, L, r_c);
   std::vector<double> ratios;
   if (o.c1 > 0) ratios.push_back(o.c1 / c);
   else for (int i = 0; i < 7; ++i) ratios.push_back(1.10 + 0.05 * i);
@@ -374,14 +408,26 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     // falls with n_f)
     bwin = espm::make_bspline_window(P);
     best_c1 = 0.0;
-    auto alias_at = [&](int n) { return alias_from_rows(alias_rows(split, n, L, r_c), bwin, n); };
+    auto alias_at = [&](int n) { return alias_from_rows(alias_rows(chi, n), bwin, n); };
     if (o.n_f > 0) {
       best_alias = alias_at(n_f);
     } else {
       std::vector<int> ladder;
       for (int n = n_f; n <= 1024; n = espm::round_grid(n + 1)) ladder.push_back(n);
-      int lo = 0, hi = (int)ladder.size() - 1;
-      if (alias_at(ladder[hi]) > 0.1 * tol) lo = hi;          // even the largest grid does not meet it
+      // the first ladder entry that meets the acceptance: probe upwards with
+      // steps that double (the estimate's cost grows as n^3, so the largest
+      // grids are evaluated only when needed), then bisect the last bracket
+      const int last = (int)ladder.size() - 1;
+      int lo = 0, hi = last, step = 1, probe = 0;
+      bool met = false;
+      while (true) {
+        if (alias_at(ladder[probe]) <= 0.1 * tol) { hi = probe; met = true; break; }
+        lo = probe + 1;
+        if (probe == last) break;
+        probe = std::min(last, probe + step);
+        step *= 2;
+      }
+      if (!met) lo = hi = last;                                 // even the largest grid does not meet it
       while (lo < hi) {
         const int mid = (lo + hi) / 2;
         if (alias_at(ladder[mid]) <= 0.1 * tol) hi = mid; else lo = mid + 1;
@@ -393,7 +439,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
     std::vector<espm::Window> windows;
     for (double r : ratios) windows.push_back(cached_window(r * c, P));
     for (int step = 0; step < 8; ++step) {
-      const std::vector<double> rows = alias_rows(split, n_f, L, r_c);
+      const std::vector<double> rows = alias_rows(chi, n_f);
       best_alias = 1e300;
       for (size_t i = 0; i < ratios.size(); ++i) {
         const double a = alias_from_rows(rows, windows[i], n_f);
@@ -471,14 +517,18 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   hp.near_nc = prec == ESP_FP32 ? nt.terms32 : espk::Deg<double>::nr;
   const double near_err = prec == ESP_FP32 ? nt.err32 : nt.err64;
 
-  // influence tables (Eq. pk, Phi in grid units)
+  // influence tables (Eq. pk, Phi in grid units); the virial table only for
+  // plans that form the virial (zeros otherwise: the scale kernel reads it
+  // only then)
   hp.G.assign(d.gsize, 0.0);
   hp.H.assign(d.gsize, 0.0);
+  chi(d.gsize - 1);
   for (int m = 1; m < d.gsize; ++m) {
     const double xi = 2.0 * kPi * std::sqrt((double)m) / L;
-    hp.G[m] = split.chihat(r_c * xi) / (xi * xi) / (L * L * L);
+    const double ch = chi(m);
+    hp.G[m] = ch / (xi * xi) / (L * L * L);
     // virial: (r_c xi chihat'(r_c xi) - 2 chihat(r_c xi)) / (xi^2 L^3)
-    hp.H[m] = (r_c * xi * split.dchihat(r_c * xi) - 2.0 * split.chihat(r_c * xi)) / (xi * xi) / (L * L * L);
+    if (o.virial) hp.H[m] = (r_c * xi * split.dchihat(r_c * xi) - 2.0 * ch) / (xi * xi) / (L * L * L);
   }
   hp.W.assign(n_f / 2 + 1, 0.0);
   for (int k = 0; k <= n_f / 2; ++k) {
