@@ -142,3 +142,29 @@ def test_influence_matches_the_oracle(lib, H, eps):
     if np.allclose(H, H[0, 0] * np.eye(3)):
         cube = lib.esp_influence_query(H[0, 0], 700, eps, r_c=r_c)
         assert np.max(np.abs(cube - got) * weight) <= 1e-10 * np.max(np.abs(want) * weight)
+
+
+def test_influence_query_arguments(lib):
+    import ctypes
+    so = lib.load_library()
+    o = lib.make_opts(r_c=1.0)
+    box = lib.esp_box((ctypes.c_double * 3)(5.0, 5.0, 5.0))
+    cell = lib._cell(5.0 * np.eye(3))
+    n = ctypes.c_int64(0)
+    # exactly one of box and cell
+    assert so.esp_influence_query(ctypes.byref(box), ctypes.byref(cell), 100, 1e-4, ctypes.byref(o), None,
+                                  ctypes.byref(n)) == 1
+    assert so.esp_influence_query(None, None, 100, 1e-4, ctypes.byref(o), None, ctypes.byref(n)) == 1
+    assert so.esp_influence_query(ctypes.byref(box), None, 100, 1e-4, ctypes.byref(o), None, None) == 1
+    # length query, then a buffer one entry short
+    assert so.esp_influence_query(ctypes.byref(box), None, 100, 1e-4, ctypes.byref(o), None, ctypes.byref(n)) == 0
+    n_f = lib.esp_plan_query(5.0, 100, 1e-4, r_c=1.0)["n_f"]
+    assert n.value == n_f * n_f * (n_f // 2 + 1)
+    short = ctypes.c_int64(n.value - 1)
+    buf = np.zeros(n.value)
+    assert so.esp_influence_query(ctypes.byref(box), None, 100, 1e-4, ctypes.byref(o),
+                                  buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(short)) == 1
+    # p_0 = 0 and p is even in k for a cube
+    p = lib.esp_influence_query(5.0, 100, 1e-4, r_c=1.0)
+    assert p[0, 0, 0] == 0.0
+    assert np.allclose(p[1:, 1:, :], p[:0:-1, :0:-1, :], rtol=1e-14, atol=0)
