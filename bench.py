@@ -337,6 +337,12 @@ def run_gpu(args, world, rank, local):
         extras["batched"] = batched(args, local, stream, flush)
         extras["served"] = served(args, local)
         extras["large"] = large(args, local, stream, flush)
+        # a triclinic cell (R28): the same water density in a truncated
+        # octahedron; last, and guarded, so that it cannot cost the lines above
+        try:
+            extras["triclinic"] = triclinic(args, local, stream, flush)
+        except Exception as exc:         # reported in the JSON line
+            extras["triclinic"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     total_ms, e2e_s = replicas.max_over_ranks([total_ms, e2e_s], device=dev)
     phases = {k: v / args.steps for k, v in phase_acc.items()}
@@ -383,6 +389,38 @@ def single_variant(args, local, stream, flush, s, tolerance=None, **opts):
     return {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
             "window": ("pswf", "bspline")[info["window"]], "diff": ("ad", "ik")[info["diff"]],
             "tolerance": tol, "steps": len(ms)}
+
+
+TRICLINIC = dict(workload="spce_water_1e5_molecules_truncated_octahedron", molecules=100_000, atoms=300_000,
+                 density_per_nm3=33.4, r_c_nm=1.0, tolerance=1e-4, seed=2505)
+
+
+def triclinic(args, local, stream, flush):
+    """atoms/s of a triclinic plan (esp_plan_cell): 1e5 SPC/E-shaped water
+    molecules in a truncated octahedron of the headline box's volume."""
+    import torch
+    from paper_2505_09727_gb300 import esp, inputs
+    dev = torch.device("cuda", local)
+    s = inputs.spce_water_cell(TRICLINIC["molecules"], density=TRICLINIC["density_per_nm3"], seed=TRICLINIC["seed"])
+    h = esp.esp_plan_cell(s.H, s.n, TRICLINIC["tolerance"], r_c=TRICLINIC["r_c_nm"], device=local,
+                          stream=stream.cuda_stream)
+    info = esp.esp_plan_info(h)
+    x = torch.tensor(s.pos, device=dev)
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    f = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
+    esp.esp_set_charges(h, torch.tensor(s.q, device=dev))
+
+    def step():
+        esp.esp_step(h, x, e, f, None)
+
+    for _ in range(3):
+        step()
+    ms = time_steps(step, stream, max(3, min(args.steps, 20)), flush)
+    esp.esp_destroy(h)
+    t = statistics.median(ms)
+    return {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
+            "n_cells": info["n_cells"], "steps": len(ms),
+            "config": dict(TRICLINIC, cell="truncated_octahedron", cell_vectors_nm=s.H.T.round(6).tolist())}
 
 
 LARGE = dict(workload="spce_water_1e6_molecules", molecules=1_000_000, atoms=3_000_000, density_per_nm3=33.4,

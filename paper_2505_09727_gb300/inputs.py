@@ -126,6 +126,54 @@ def spce_water(n_molecules: int = 100_000, density: float = WATER_DENSITY,
     return System(_wrap(pos, L), q, float(L), f"water{n_molecules}")
 
 
+@dataclass
+class CellSystem:
+    """A periodic system in a triclinic cell: ``H`` (3,3) has the cell vectors
+    a, b, c as columns (a = (ax,0,0), b = (bx,by,0)); ``pos`` (N,3) float64."""
+    pos: np.ndarray
+    q: np.ndarray
+    H: np.ndarray
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.q.shape[0])
+
+
+def truncated_octahedron(volume: float) -> np.ndarray:
+    """Cell vectors (columns) of a truncated octahedron of the given volume:
+    nearest-image distance d, a = (d,0,0), b = (d/3, 2 sqrt2 d/3, 0),
+    c = (-d/3, sqrt2 d/3, sqrt6 d/3), volume (4 sqrt3 / 9) d^3."""
+    d = (volume * 9.0 / (4.0 * math.sqrt(3.0))) ** (1.0 / 3.0)
+    return np.array([[d, d / 3.0, -d / 3.0],
+                     [0.0, 2.0 * math.sqrt(2.0) * d / 3.0, math.sqrt(2.0) * d / 3.0],
+                     [0.0, 0.0, math.sqrt(6.0) * d / 3.0]])
+
+
+def spce_water_cell(n_molecules: int, H: np.ndarray | None = None, density: float = WATER_DENSITY,
+                    jitter: float = 0.03, seed: int = 2505) -> CellSystem:
+    """SPC/E-shaped water in a triclinic cell (default: a truncated octahedron
+    of volume n / density). O atoms sit on an m^3 lattice of fractional
+    coordinates ((i + 1/2)/m per axis, n sites chosen without replacement),
+    mapped through H and jittered by +-jitter nm per Cartesian axis; each
+    molecule gets a uniformly random orientation."""
+    rng = np.random.default_rng(seed)
+    if H is None:
+        H = truncated_octahedron(n_molecules / density)
+    H = np.asarray(H, dtype=np.float64)
+    m = int(math.ceil(round(n_molecules ** (1.0 / 3.0), 9)))
+    while m ** 3 < n_molecules:
+        m += 1
+    sites = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m),
+                                 indexing="ij"), axis=-1).reshape(-1, 3)
+    if m ** 3 > n_molecules:
+        keep = np.sort(rng.choice(m ** 3, size=n_molecules, replace=False))
+        sites = sites[keep]
+    oxygen = ((sites + 0.5) / m) @ H.T + rng.uniform(-jitter, jitter, size=(n_molecules, 3))
+    pos, q = _water_sites(rng, oxygen)
+    return CellSystem(pos, q, H, f"water{n_molecules}_cell")
+
+
 def electrolyte(n_atoms: int, density: float = 100.0, ion_fraction: float = 0.006,
                 seed: int = 9727, jitter: float = 0.03) -> System:
     """Neutral +-1 ions plus SPC/E-shaped water at a total atom density.

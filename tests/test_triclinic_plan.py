@@ -168,3 +168,19 @@ def test_influence_query_arguments(lib):
     p = lib.esp_influence_query(5.0, 100, 1e-4, r_c=1.0)
     assert p[0, 0, 0] == 0.0
     assert np.allclose(p[1:, 1:, :], p[:0:-1, :0:-1, :], rtol=1e-14, atol=0)
+
+
+def test_water_in_a_truncated_octahedron():
+    """The triclinic bench input: volume n / density, SPC/E geometry, neutral,
+    oxygens spread over the whole cell."""
+    from paper_2505_09727_gb300 import inputs
+    s = inputs.spce_water_cell(2000, seed=3)
+    assert s.n == 6000 and abs(float(np.sum(s.q))) < 1e-12
+    assert abs(np.linalg.det(s.H) - 2000 / inputs.WATER_DENSITY) < 1e-9
+    h = tr.heights(s.H)
+    assert np.allclose(h, h[0])                      # all faces of a truncated octahedron's cell alike
+    o, h1, h2 = s.pos[0::3], s.pos[1::3], s.pos[2::3]
+    assert np.allclose(np.linalg.norm(h1 - o, axis=1), 0.1) and np.allclose(np.linalg.norm(h2 - o, axis=1), 0.1)
+    frac = np.linalg.solve(s.H, o.T).T
+    assert frac.min() > -0.05 and frac.max() < 1.05
+    assert np.all(np.ptp(frac, axis=0) > 0.9)
