@@ -211,6 +211,18 @@ esp_status esp_set_charges_f32(esp_plan_t plan, const float* q, int where);
 esp_status esp_set_positions(esp_plan_t plan, const double* xyz, int where);
 esp_status esp_set_positions_f32(esp_plan_t plan, const float* xyz, int where);
 
+/* Exclusions: the listed pairs (caller indices; pair k is pairs[2k],
+ * pairs[2k+1]) do not interact in the computes that follow: their direct
+ * interaction q_i q_j / (4 pi r) (times the prefactor) is removed from the
+ * energy, the potentials and the forces, while their other periodic images
+ * still count (the bonded pairs of molecules in MD). The pair vector is the
+ * image nearest in wrapped fractional coordinates, the minimum image for
+ * pairs closer than half the smallest cell height. n_pairs = 0 clears the
+ * list. pairs is a host array, copied; the call first waits for the plan's
+ * stream. ESP_ERR_INVALID_ARG for an index outside [0, N) or i = j;
+ * ESP_ERR_UNSUPPORTED on a plan made with opts.virial. */
+esp_status esp_set_exclusions(esp_plan_t plan, const int32_t* pairs, int64_t n_pairs);
+
 /* Spread, R2C FFT, fused influence scale + spectral energy, C2R FFT, gather,
  * local part, corrections and compensated FP64 energy. Any of energy,
  * forces, potential may be NULL; with forces and potential both NULL only

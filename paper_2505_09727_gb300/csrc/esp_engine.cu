@@ -170,6 +170,11 @@ struct esp_plan_s {
   cudaGraph_t sgraph = nullptr;
   cudaGraphExec_t sgexec = nullptr;
   const void* skey[5] = {};
+  // exclusions (single plans): pairs of caller indices, and the inverse of
+  // the sort permutation they are mapped through
+  int2* d_excl = nullptr;
+  long long n_excl = 0, excl_cap = 0;
+  uint32_t* d_inv = nullptr;
 };
 
 struct esp_batch_s {
@@ -585,6 +590,8 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
     ESP_CU(L::near(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_rel, p->d_start, p->d_near, nc,
                    hp.near_nc, hp.near_queued, st2, p->d_vloc));
   }
+  if (p->n_excl > 0)
+    ESP_CU(L::exclusions(p->d_desc, p->d_excl, p->n_excl, p->d_perm, p->d_inv, p->N, p->d_atoms, p->d_near, st2));
   rec(p, 10, st2);
   if (!serial) ESP_CU(cudaEventRecord(p->ev_join, st2));
 
@@ -1075,6 +1082,47 @@ esp_status esp_phase_times(esp_plan_t p, float* ms, int n) {
   p->phase_ms[7] = el(8, 11);             // join, finalize, energy
   p->phase_ms[8] = el(2, 11);             // whole compute
   for (int i = 0; i < n && i < kPhases; ++i) ms[i] = p->phase_ms[i];
+  return ESP_OK;
+}
+
+esp_status esp_set_exclusions(esp_plan_t p, const int32_t* pairs, int64_t n_pairs) {
+  if (!p || n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(ESP_ERR_INVALID_ARG, "NULL plan or pairs, or n_pairs < 0");
+  if (p->nsys != 1) return fail(ESP_ERR_UNSUPPORTED, "exclusions belong to single-system plans");
+  if (p->virial && n_pairs > 0) return fail(ESP_ERR_UNSUPPORTED, "exclusions are not combined with the virial");
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    const int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+    if (i < 0 || j < 0 || i >= p->N || j >= p->N || i == j)
+      return fail(ESP_ERR_INVALID_ARG, "exclusion pair " + std::to_string(k) + " = (" + std::to_string(i) + ", " +
+                                           std::to_string(j) + ") is not two distinct atoms of the plan");
+  }
+  DeviceGuard g(p->device);
+  ESP_TRY(wait_stream(p, p->st));                // nothing in flight reads the old list
+  if (n_pairs > p->excl_cap) {
+    if (p->d_excl) {
+      p->allocs.erase(std::find(p->allocs.begin(), p->allocs.end(), (void*)p->d_excl));
+      p->bytes -= (size_t)p->excl_cap * sizeof(int2);
+      cudaFree(p->d_excl);
+      p->d_excl = nullptr;
+      p->excl_cap = 0;
+    }
+    ESP_TRY(dev_alloc_t(p, &p->d_excl, (size_t)n_pairs));
+    p->excl_cap = n_pairs;
+  }
+  if (n_pairs > 0 && !p->d_inv) ESP_TRY(dev_alloc_t(p, &p->d_inv, (size_t)std::max<long long>(1, p->N)));
+  if (n_pairs > 0)
+    ESP_CU(cudaMemcpy(p->d_excl, pairs, (size_t)n_pairs * sizeof(int2), cudaMemcpyHostToDevice));
+  p->n_excl = n_pairs;
+  // the captured graphs hold the old launch sequence
+  if (p->cgexec) cudaGraphExecDestroy(p->cgexec);
+  if (p->cgraph) cudaGraphDestroy(p->cgraph);
+  if (p->sgexec) cudaGraphExecDestroy(p->sgexec);
+  if (p->sgraph) cudaGraphDestroy(p->sgraph);
+  p->cgexec = nullptr;
+  p->cgraph = nullptr;
+  p->sgexec = nullptr;
+  p->sgraph = nullptr;
+  std::fill(p->ckey, p->ckey + 4, nullptr);
+  std::fill(p->skey, p->skey + 5, nullptr);
   return ESP_OK;
 }
 

@@ -241,6 +241,19 @@ cudaError_t Launch<ESP_REAL>::finalize(const SysDesc* sys, const int2* chunks, i
 }
 
 template <>
+cudaError_t Launch<ESP_REAL>::exclusions(const SysDesc* sys, const int2* pairs, long long n_pairs,
+                                         const uint32_t* perm, uint32_t* inv, long long n_atoms, const void* atoms,
+                                         void* nearres, cudaStream_t st) {
+  using A = typename Types<ESP_REAL>::atom;
+  using R = typename Types<ESP_REAL>::res;
+  if (n_pairs == 0 || n_atoms == 0) return cudaSuccess;
+  k_inverse_perm<<<(int)((n_atoms + 255) / 256), 256, 0, st>>>(perm, inv, n_atoms);
+  k_exclusions<ESP_REAL><<<(int)((n_pairs + 255) / 256), 256, 0, st>>>(sys, pairs, n_pairs, inv, (const A*)atoms,
+                                                                       (R*)nearres);
+  return cudaGetLastError();
+}
+
+template <>
 cudaError_t Launch<ESP_REAL>::convert_charges(const void* src, bool src_double, ESP_REAL* dst,
                                               long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;

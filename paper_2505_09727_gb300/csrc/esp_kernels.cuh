@@ -1159,6 +1159,69 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
   }
 }
 
+// Exclusions: inv[perm[s]] = s, the sorted position of every caller index.
+static __global__ void __launch_bounds__(256) k_inverse_perm(const uint32_t* __restrict__ perm,
+                                                             uint32_t* __restrict__ inv, long long n) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) inv[perm[s]] = (uint32_t)s;
+}
+
+// Exclusions (one system): every listed pair (caller indices) loses its
+// direct interaction q_i q_j / (4 pi r), which the local and spectral parts
+// hold in full; the correction is added to the local-part results (sorted
+// order) before the finalize, so potentials, forces and the energy all see
+// it. The pair vector is the image nearest in wrapped fractional
+// coordinates, the minimum image for pairs closer than half the smallest
+// cell height.
+template <typename real>
+__global__ void __launch_bounds__(256) k_exclusions(
+    const SysDesc* __restrict__ sys, const int2* __restrict__ pairs, long long n_pairs,
+    const uint32_t* __restrict__ inv, const typename Types<real>::atom* __restrict__ atoms,
+    typename Types<real>::res* __restrict__ nearres) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_pairs) return;
+  const SysDesc& S = sys[0];
+  const int2 pr = pairs[k];
+  const uint32_t a = inv[pr.x], b = inv[pr.y];
+  const typename Types<real>::atom A = atoms[a], B = atoms[b];
+  real dx, dy, dz;
+  if constexpr (sizeof(real) == 4) {
+    if (S.tri) {
+      // wrapped fractional difference, then H (cell vectors = n_c tcell)
+      const double f = 2.3283064365386962890625e-10 * S.n_c;
+      const double sx = (double)(int)(A.x - B.x) * f, sy = (double)(int)(A.y - B.y) * f,
+                   sz = (double)(int)(A.z - B.z) * f;
+      const double* e = S.tcell;
+      dx = (float)(sx * e[0] + sy * e[1] + sz * e[3]);
+      dy = (float)(sy * e[2] + sz * e[4]);
+      dz = (float)(sz * e[5]);
+    } else {
+      pair_geometry<real>(S, A, B, dx, dy, dz);
+    }
+  } else {
+    pair_geometry<real>(S, A, B, dx, dy, dz);
+  }
+  const real r2 = dx * dx + dy * dy + dz * dz;
+  if (!(r2 > real(0))) return;                    // coincident sites: nothing was added either
+  const real rinv = real(1) / sqrt_real(r2);
+  const real k4 = real(1.0 / kFourPi);
+  const real qa = (real)atom_q(A), qb = (real)atom_q(B);
+  const real fs = qa * qb * rinv * rinv * rinv * k4;   // pair force on a is +fs d: removed
+  if constexpr (sizeof(real) == 4) {
+    atomicAdd(nearres + a, make_float4(-qb * rinv * k4, -fs * dx, -fs * dy, -fs * dz));
+    atomicAdd(nearres + b, make_float4(-qa * rinv * k4, fs * dx, fs * dy, fs * dz));
+  } else {
+    atomicAdd(&nearres[a].x, -qb * rinv * k4);
+    atomicAdd(&nearres[a].y, -fs * dx);
+    atomicAdd(&nearres[a].z, -fs * dy);
+    atomicAdd(&nearres[a].w, -fs * dz);
+    atomicAdd(&nearres[b].x, -qa * rinv * k4);
+    atomicAdd(&nearres[b].y, fs * dx);
+    atomicAdd(&nearres[b].z, fs * dy);
+    atomicAdd(&nearres[b].w, fs * dz);
+  }
+}
+
 // Compensated (Neumaier) sum of a strided range, then a pairwise block tree.
 __device__ inline void neumaier_add(double& s, double& c, double v) {
   double t = s + v;

@@ -52,6 +52,11 @@ struct Launch {
                               cudaStream_t st);
   static cudaError_t convert_charges(const void* src, bool src_double, real* dst, long long n,
                                      cudaStream_t st);
+  // Exclusions of one system: inv[perm[s]] = s, then every pair (caller
+  // indices) removes its direct interaction from nearres (sorted order).
+  static cudaError_t exclusions(const SysDesc* sys, const int2* pairs, long long n_pairs, const uint32_t* perm,
+                                uint32_t* inv, long long n_atoms, const void* atoms, void* nearres,
+                                cudaStream_t st);
   static bool supports_P(int P);
   static size_t atom_bytes();
   static size_t res_bytes();

@@ -101,6 +101,7 @@ _SIGNATURES = {
     "esp_plan": (ctypes.c_int, [ctypes.POINTER(esp_box), ctypes.c_int64, ctypes.c_double,
                                 ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
     "esp_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(esp_plan_params)]),
+    "esp_set_exclusions": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "esp_plan_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
                                      ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
     "esp_plan_query_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
@@ -289,6 +290,14 @@ def esp_influence_query(L_or_H, N: int, tolerance: float, opts: esp_plan_opts | 
     while n_f * n_f * (n_f // 2 + 1) < n.value:
         n_f += 1
     return out.reshape(n_f, n_f, n_f // 2 + 1)
+
+
+def esp_set_exclusions(plan: int, pairs):
+    """Pairs (n, 2) of caller indices whose direct interaction is removed
+    from every compute that follows (None or an empty array clears them)."""
+    arr = np.zeros((0, 2), dtype=np.int32) if pairs is None else \
+        np.ascontiguousarray(np.asarray(pairs).reshape(-1, 2), dtype=np.int32)
+    _check(load_library().esp_set_exclusions(_P(plan), arr.ctypes.data if len(arr) else None, int(len(arr))))
 
 
 def esp_plan_info(plan: int) -> dict:

@@ -11,9 +11,9 @@ ESP and Ewald.
 * Coordinates shifted by lattice vectors give the same results; esp_step
   (graph replay) equals esp_compute.
 
-The triclinic path is the newest on the GPU, so this file is collected after
-every other (test_zz_*): a run that stops at the first failure has run the
-rest first.
+The triclinic path is among the newest on the GPU, so this file is
+collected after the established ones (test_zz_*): a run that stops at the
+first failure has run those first.
 """
 import math
 
