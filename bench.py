@@ -343,6 +343,11 @@ def run_gpu(args, world, rank, local):
             extras["triclinic"] = triclinic(args, local, stream, flush)
         except Exception as exc:         # reported in the JSON line
             extras["triclinic"] = {"error": f"{type(exc).__name__}: {exc}"}
+        # the MD loop workload (velocity Verlet around the solve), likewise
+        try:
+            extras["md"] = md_loop(args, local, stream)
+        except Exception as exc:         # reported in the JSON line
+            extras["md"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     total_ms, e2e_s = replicas.max_over_ranks([total_ms, e2e_s], device=dev)
     phases = {k: v / args.steps for k, v in phase_acc.items()}
@@ -421,6 +426,35 @@ def triclinic(args, local, stream, flush):
     return {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
             "n_cells": info["n_cells"], "steps": len(ms),
             "config": dict(TRICLINIC, cell="truncated_octahedron", cell_vectors_nm=s.H.T.round(6).tolist())}
+
+
+MD_LOOP = dict(workload="spce_water_1e5_molecules_md", molecules=100_000, atoms=300_000, density_per_nm3=33.4,
+               r_c_nm=1.0, lj_cutoff_nm=1.0, tolerance=1e-4, dt_ps=0.0005, temperature_K=300.0, seed=2505)
+
+
+def md_loop(args, local, stream):
+    """ns/day and energy change of the MD loop (esp_md_*): 1e5 flexible
+    SPC/E-shaped water molecules, FP32 solve, velocity Verlet."""
+    import torch
+    from paper_2505_09727_gb300 import esp, inputs
+    s = inputs.spce_water(MD_LOOP["molecules"], seed=MD_LOOP["seed"])
+    v = inputs.water_velocities(MD_LOOP["molecules"], MD_LOOP["temperature_K"], seed=MD_LOOP["seed"])
+    n_steps = max(10, min(args.steps, 50))
+    with esp.Plan(s.L, s.n, MD_LOOP["tolerance"], r_c=MD_LOOP["r_c_nm"], device=local, stream=stream.cuda_stream,
+                  prefactor=esp.MD_PREFACTOR) as p:
+        p.set_charges(s.q)
+        with esp.MD(p.handle, s.pos, v, dt=MD_LOOP["dt_ps"], lj_cutoff=MD_LOOP["lj_cutoff_nm"]) as sim:
+            sim.run(3)                                   # graph capture, first forces
+            torch.cuda.synchronize(torch.device("cuda", local))
+            t0 = time.perf_counter()
+            e = sim.run(n_steps)                         # ends with a device sync
+            secs = time.perf_counter() - t0
+    tot = e.sum(axis=1)
+    ns_per_day = n_steps * MD_LOOP["dt_ps"] * 1e-3 / secs * 86400.0
+    return {"value": ns_per_day, "unit": "ns/day", "ms_per_step": 1e3 * secs / n_steps, "steps": n_steps,
+            "energy_change_kj_mol_per_atom": float(tot[-1] - tot[0]) / s.n,
+            "max_energy_excursion_over_kinetic": float(np.max(np.abs(tot - tot[0])) / np.mean(e[:, 3])),
+            "config": dict(MD_LOOP, L_nm=s.L)}
 
 
 LARGE = dict(workload="spce_water_1e6_molecules", molecules=1_000_000, atoms=3_000_000, density_per_nm3=33.4,

@@ -446,6 +446,46 @@ const char* esp_last_error(void);
 /* Library build identification (compile-time arch list and version). */
 const char* esp_version(void);
 
+/* ------------------------------------------------------------ MD loop
+ * A workload around the solve: velocity Verlet for flexible SPC/E-shaped
+ * water, the plan's atoms being consecutive (O, H, H) molecules. Forces:
+ * the plan's ESP solve with the three intramolecular pairs of every molecule
+ * excluded (esp_md_create sets the plan's exclusion list), harmonic O-H
+ * bonds and H-O-H angle, O-O Lennard-Jones within a cutoff (shifted to zero
+ * there). Units nm, ps, amu, kJ/mol: make the plan with
+ * opts.prefactor = 4 pi 138.935458 so that its energy is in kJ/mol for
+ * charges in e. Cubic plans, charges set before esp_md_create. */
+typedef struct esp_md_s* esp_md_t;
+typedef struct {
+  double dt;                 /* time step, ps                                    */
+  double k_bond, r0;         /* bonds k (r - r0)^2 / 2: kJ mol^-1 nm^-2, nm       */
+  double k_angle, theta0;    /* angle k (theta - theta0)^2 / 2: kJ mol^-1 rad^-2, rad */
+  double lj_sigma, lj_epsilon, lj_cutoff; /* O-O: nm, kJ/mol, nm (< L/2)      */
+  double mass_O, mass_H;     /* amu                                              */
+  int reserved[8];
+} esp_md_params;
+
+/* Defaults: dt 0.0005 ps, k_b 3.45e5, r0 0.1, k_theta 383, theta0 109.47 deg,
+ * SPC/E sigma 0.316557 nm and epsilon 0.650194 kJ/mol, cutoff 1.0 nm,
+ * masses 15.9994 and 1.008. */
+void esp_md_params_init(esp_md_params* params);
+
+/* Bind an MD state to `plan` (which it then drives; destroy the MD state
+ * before the plan): positions xyz and velocities vel (host, N x 3, nm and
+ * nm/ps) are copied to the device. ESP_ERR_INVALID_ARG for N not a multiple
+ * of 3 or bad parameters, ESP_ERR_UNSUPPORTED for a triclinic plan. */
+esp_status esp_md_create(esp_plan_t plan, const esp_md_params* params, const double* xyz, const double* vel,
+                         esp_md_t* out);
+
+/* n_steps velocity-Verlet steps. energies (host, nullable) receives
+ * (n_steps + 1) rows (Coulomb, bonded, Lennard-Jones, kinetic) in kJ/mol:
+ * the state before the first step, then after every step. */
+esp_status esp_md_run(esp_md_t md, int n_steps, double* energies);
+
+/* Current positions and velocities (host, N x 3; either may be NULL). */
+esp_status esp_md_state(esp_md_t md, double* xyz, double* vel);
+esp_status esp_md_destroy(esp_md_t md);
+
 #ifdef __cplusplus
 }
 #endif

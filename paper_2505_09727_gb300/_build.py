@@ -21,7 +21,7 @@ NVCC_FLAGS = [ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-pthread"]
 
 CU_SOURCES = ["esp_kern_f32.cu", "esp_kern_f32_rest.cu", "esp_kern_near.cu", "esp_kern_f64.cu",
-              "esp_kern_f64_rest.cu", "esp_plan.cu", "esp_engine.cu", "esp_static.cu"]
+              "esp_kern_f64_rest.cu", "esp_plan.cu", "esp_engine.cu", "esp_static.cu", "esp_md.cu"]
 CPP_SOURCES = ["esp_math.cpp", "esp_server.cpp", "esp_tune.cpp"]
 
 

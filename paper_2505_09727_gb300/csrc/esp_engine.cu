@@ -1193,6 +1193,8 @@ size_t plan_device_bytes(esp_plan_t p) { return p ? p->bytes : 0; }
 
 int plan_device(esp_plan_t p) { return p ? p->device : 0; }
 
+cudaStream_t plan_stream(esp_plan_t p) { return p ? p->st : nullptr; }
+
 }  // namespace espe
 
 // ==================================================================== batches

@@ -24,6 +24,9 @@ size_t plan_device_bytes(esp_plan_t p);
 // Device ordinal of the plan.
 int plan_device(esp_plan_t p);
 
+// The stream the plan's work runs on.
+cudaStream_t plan_stream(esp_plan_t p);
+
 // Message reported by esp_last_error() for the calling thread.
 void set_last_error(const std::string& msg);
 

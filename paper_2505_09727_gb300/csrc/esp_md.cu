@@ -1,0 +1,466 @@
+// MD loop around the solve: velocity Verlet for flexible SPC/E-shaped water
+// with ESP electrostatics (the plan, with the intramolecular pairs excluded),
+// harmonic O-H bonds and H-O-H angle, and O-O Lennard-Jones within a cutoff,
+// shifted to zero there. Molecules are consecutive (O, H, H) triples of the
+// plan's atoms; positions, velocities and forces stay on the device in FP64,
+// caller order. One step: kick + drift, esp_step on the device positions
+// (sort and compute replayed as one graph), bonded and Lennard-Jones forces
+// added to the ESP forces, kick with the kinetic energy summed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/esp.h"
+#include "esp_engine.h"
+#include "esp_launch.h"
+
+struct esp_md_s {
+  esp_plan_t plan = nullptr;
+  esp_md_params prm{};
+  int device = 0;
+  long long n_atoms = 0;
+  int n_mol = 0;
+  double L = 0.0;
+  int nc = 0;                      // Lennard-Jones cells per axis (0: all pairs)
+  bool fp32 = true;                // the plan's precision (the Lennard-Jones pairs follow it)
+  bool have_forces = false;
+  double* d_x = nullptr;
+  double* d_v = nullptr;
+  double* d_f = nullptr;
+  double* d_e = nullptr;           // energies [(capacity) x 4]
+  double* d_ec = nullptr;          // the solve's energy (a fixed address: the step graph replays)
+  long long e_cap = 0;
+  double e_now[4] = {0, 0, 0, 0};  // energies at the current positions
+  uint32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_tiles = nullptr, *d_cursor = nullptr,
+           *d_sorted = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr double kPiMd = 3.14159265358979323846;
+
+esp_status md_fail(esp_status s, const std::string& msg) {
+  espe::set_last_error(msg);
+  return s;
+}
+
+#define MD_CU(call)                                                                               \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return md_fail(ESP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct MdConst {
+  double dt, k_bond, r0, k_angle, theta0, sigma2, eps4, rc2, shift, inv_mO, inv_mH, L, inv_L;
+  int n_mol, nc;
+};
+
+__device__ __forceinline__ double wrap_d(double d, double L, double inv_L) { return d - L * rint(d * inv_L); }
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v over the block added to *out (blockDim.x a multiple of 32).
+__device__ void block_add(double v, double* out) {
+  __shared__ double red[32];
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    v = warp_sum_d(v);
+    if (lane == 0) atomicAdd(out, v);
+  }
+}
+
+__device__ __forceinline__ double inv_mass(const MdConst& C, long long i) { return i % 3 == 0 ? C.inv_mO : C.inv_mH; }
+
+// v += dt F / 2m; r += dt v
+__global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const double* __restrict__ f,
+                             MdConst C, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double h = 0.5 * C.dt * inv_mass(C, i);
+  for (int a = 0; a < 3; ++a) {
+    const double vv = v[3 * i + a] + h * f[3 * i + a];
+    v[3 * i + a] = vv;
+    x[3 * i + a] += C.dt * vv;
+  }
+}
+
+// v += dt F / 2m (scale 1) or nothing (scale 0); the kinetic energy added to *ek
+__global__ void k_kick(double* __restrict__ v, const double* __restrict__ f, MdConst C, long long n, double scale,
+                       double* __restrict__ ek) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < n) {
+    const double im = inv_mass(C, i);
+    const double h = 0.5 * C.dt * im * scale;
+    for (int a = 0; a < 3; ++a) {
+      const double vv = v[3 * i + a] + h * f[3 * i + a];
+      v[3 * i + a] = vv;
+      e += 0.5 * vv * vv / im;
+    }
+  }
+  block_add(e, ek);
+}
+
+// Bonds and angle of one molecule per thread, added to f; energy to *eb.
+__global__ void k_bonded(const double* __restrict__ x, double* __restrict__ f, MdConst C, double* __restrict__ eb) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (m < C.n_mol) {
+    const double* o = x + 9ll * m;
+    double d[2][3], r[2];
+    double fh[2][3];
+    for (int k = 0; k < 2; ++k) {
+      for (int a = 0; a < 3; ++a) d[k][a] = wrap_d(o[3 * (k + 1) + a] - o[a], C.L, C.inv_L);
+      r[k] = sqrt(d[k][0] * d[k][0] + d[k][1] * d[k][1] + d[k][2] * d[k][2]);
+      const double dr = r[k] - C.r0;
+      e += 0.5 * C.k_bond * dr * dr;
+      for (int a = 0; a < 3; ++a) fh[k][a] = -C.k_bond * dr / r[k] * d[k][a];
+    }
+    double c = (d[0][0] * d[1][0] + d[0][1] * d[1][1] + d[0][2] * d[1][2]) / (r[0] * r[1]);
+    c = fmin(1.0, fmax(-1.0, c));
+    const double th = acos(c);
+    const double s = sqrt(fmax(1.0 - c * c, 1e-300));
+    const double de = C.k_angle * (th - C.theta0);
+    e += 0.5 * C.k_angle * (th - C.theta0) * (th - C.theta0);
+    // d theta / d u = -(v / (|u||v|) - cos u / |u|^2) / sin theta, likewise for v
+    for (int a = 0; a < 3; ++a) {
+      const double dtu = -(d[1][a] / (r[0] * r[1]) - c / (r[0] * r[0]) * d[0][a]) / s;
+      const double dtv = -(d[0][a] / (r[0] * r[1]) - c / (r[1] * r[1]) * d[1][a]) / s;
+      fh[0][a] -= de * dtu;
+      fh[1][a] -= de * dtv;
+    }
+    double* fo = f + 9ll * m;
+    for (int a = 0; a < 3; ++a) {
+      fo[3 + a] += fh[0][a];
+      fo[6 + a] += fh[1][a];
+      fo[a] -= fh[0][a] + fh[1][a];
+    }
+  }
+  block_add(e, eb);
+}
+
+__device__ __forceinline__ int lj_cell_axis(double s, int nc) {
+  s -= floor(s);
+  const int c = (int)(s * nc);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Oxygen cells: cell of every molecule's O and the per-cell counts.
+__global__ void k_lj_bin(const double* __restrict__ x, MdConst C, uint32_t* __restrict__ cell,
+                         uint32_t* __restrict__ count) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= C.n_mol) return;
+  const double* o = x + 9ll * m;
+  const int cx = lj_cell_axis(o[0] * C.inv_L, C.nc), cy = lj_cell_axis(o[1] * C.inv_L, C.nc),
+            cz = lj_cell_axis(o[2] * C.inv_L, C.nc);
+  const uint32_t k = (uint32_t)((cx * C.nc + cy) * C.nc + cz);
+  cell[m] = k;
+  atomicAdd(count + k, 1u);
+}
+
+__global__ void k_lj_fill(const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
+                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted, int n_mol) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_mol) return;
+  const uint32_t k = cell[m];
+  sorted[start[k] + atomicAdd(cursor + k, 1u)] = (uint32_t)m;
+}
+
+// One O-O pair seen from i, in the precision of the plan (FP32 plans: FP32
+// coordinates and arithmetic, as the solve's own pair terms).
+template <typename real>
+__device__ __forceinline__ void lj_pair(const real* xi, const double* xj, const MdConst& C, real* fi, real& e) {
+  const real L = (real)C.L, inv_L = (real)C.inv_L;
+  real d[3];
+  for (int a = 0; a < 3; ++a) {
+    const real t = xi[a] - (real)xj[a];
+    d[a] = t - L * rint(t * inv_L);
+  }
+  const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  if (r2 >= (real)C.rc2 || r2 <= real(0)) return;
+  const real s2 = (real)C.sigma2 / r2, s6 = s2 * s2 * s2;
+  e += real(0.5) * ((real)C.eps4 * (s6 * s6 - s6) - (real)C.shift);   // every pair is met from both sides
+  const real fm = real(6) * (real)C.eps4 * (real(2) * s6 * s6 - s6) / r2;
+  fi[0] += fm * d[0];
+  fi[1] += fm * d[1];
+  fi[2] += fm * d[2];
+}
+
+// O-O Lennard-Jones, one O per thread: the 27 neighbouring cells (cell edge
+// >= cutoff), or every O when there are fewer than 3 cells per axis.
+template <typename real>
+__global__ void k_lj(const double* __restrict__ x, const uint32_t* __restrict__ cell,
+                     const uint32_t* __restrict__ start, const uint32_t* __restrict__ sorted, MdConst C,
+                     double* __restrict__ f, double* __restrict__ el) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  real e = 0;
+  if (m < C.n_mol) {
+    const real xi[3] = {(real)x[9ll * m], (real)x[9ll * m + 1], (real)x[9ll * m + 2]};
+    real fi[3] = {0, 0, 0};
+    if (C.nc >= 3) {
+      const int k = (int)cell[m];
+      const int cz = k % C.nc, cy = (k / C.nc) % C.nc, cx = k / (C.nc * C.nc);
+      for (int ox = -1; ox <= 1; ++ox)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int oz = -1; oz <= 1; ++oz) {
+            const int nx = (cx + ox + C.nc) % C.nc, ny = (cy + oy + C.nc) % C.nc, nz = (cz + oz + C.nc) % C.nc;
+            const int kk = (nx * C.nc + ny) * C.nc + nz;
+            for (uint32_t s = start[kk]; s < start[kk + 1]; ++s) {
+              const uint32_t j = sorted[s];
+              if ((int)j != m) lj_pair(xi, x + 9ll * j, C, fi, e);
+            }
+          }
+    } else {
+      for (int j = 0; j < C.n_mol; ++j)
+        if (j != m) lj_pair(xi, x + 9ll * j, C, fi, e);
+    }
+    double* fo = f + 9ll * m;
+    fo[0] += (double)fi[0];
+    fo[1] += (double)fi[1];
+    fo[2] += (double)fi[2];
+  }
+  block_add((double)e, el);
+}
+
+MdConst make_const(const esp_md_s* md) {
+  const esp_md_params& p = md->prm;
+  MdConst C;
+  C.dt = p.dt;
+  C.k_bond = p.k_bond;
+  C.r0 = p.r0;
+  C.k_angle = p.k_angle;
+  C.theta0 = p.theta0;
+  C.sigma2 = p.lj_sigma * p.lj_sigma;
+  C.eps4 = 4.0 * p.lj_epsilon;
+  C.rc2 = p.lj_cutoff * p.lj_cutoff;
+  const double sr6 = std::pow(p.lj_sigma / p.lj_cutoff, 6);
+  C.shift = 4.0 * p.lj_epsilon * (sr6 * sr6 - sr6);
+  C.inv_mO = 1.0 / p.mass_O;
+  C.inv_mH = 1.0 / p.mass_H;
+  C.L = md->L;
+  C.inv_L = 1.0 / md->L;
+  C.n_mol = md->n_mol;
+  C.nc = md->nc;
+  return C;
+}
+
+int blocks_of(long long n) { return (int)std::max<long long>(1, (n + 255) / 256); }
+
+// Forces and potential energies at the current positions into d_f and
+// e[0..2] (Coulomb, bonded, Lennard-Jones; e zeroed by the caller).
+esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st) {
+  esp_status s = esp_step(md->plan, md->d_x, md->d_ec, md->d_f, nullptr, ESP_DEVICE);
+  if (s != ESP_OK) return s;
+  MD_CU(cudaMemcpyAsync(e, md->d_ec, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const MdConst C = make_const(md);
+  k_bonded<<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_f, C, e + 1);
+  if (md->nc >= 3) {
+    const long long ncell = (long long)md->nc * md->nc * md->nc;
+    MD_CU(cudaMemsetAsync(md->d_count, 0, ncell * sizeof(uint32_t), st));
+    MD_CU(cudaMemsetAsync(md->d_cursor, 0, ncell * sizeof(uint32_t), st));
+    k_lj_bin<<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, C, md->d_cell, md->d_count);
+    MD_CU(espk::launch_scan(md->d_count, md->d_start, md->d_tiles, ncell, st));
+    k_lj_fill<<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_cell, md->d_start, md->d_cursor, md->d_sorted, md->n_mol);
+  }
+  if (md->fp32)
+    k_lj<float><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_cell, md->d_start, md->d_sorted, C, md->d_f,
+                                                     e + 2);
+  else
+    k_lj<double><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_cell, md->d_start, md->d_sorted, C, md->d_f,
+                                                      e + 2);
+  MD_CU(cudaGetLastError());
+  return ESP_OK;
+}
+
+template <typename T>
+esp_status md_alloc(esp_md_s* md, T** p, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(1, count) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return md_fail(ESP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  md->allocs.push_back(*p);
+  return ESP_OK;
+}
+
+void md_release(esp_md_s* md) {
+  for (void* a : md->allocs) cudaFree(a);
+  md->allocs.clear();
+}
+
+struct MdDevice {
+  int prev = 0;
+  explicit MdDevice(int dev) {
+    cudaGetDevice(&prev);
+    cudaSetDevice(dev);
+  }
+  ~MdDevice() { cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+extern "C" {
+
+void esp_md_params_init(esp_md_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dt = 0.0005;
+  p->k_bond = 345000.0;
+  p->r0 = 0.1;
+  p->k_angle = 383.0;
+  p->theta0 = 109.47 * kPiMd / 180.0;
+  p->lj_sigma = 0.316557;
+  p->lj_epsilon = 0.650194;
+  p->lj_cutoff = 1.0;
+  p->mass_O = 15.9994;
+  p->mass_H = 1.008;
+}
+
+esp_status esp_md_create(esp_plan_t plan, const esp_md_params* params, const double* xyz, const double* vel,
+                         esp_md_t* out) {
+  if (!plan || !params || !xyz || !vel || !out) return md_fail(ESP_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  esp_plan_params info;
+  esp_status s = esp_plan_info(plan, &info);
+  if (s != ESP_OK) return s;
+  if (info.triclinic) return md_fail(ESP_ERR_UNSUPPORTED, "the MD loop runs on cubic plans");
+  if (info.N <= 0 || info.N % 3 != 0) return md_fail(ESP_ERR_INVALID_ARG, "the plan's atoms must be (O, H, H) triples");
+  const esp_md_params& p = *params;
+  if (!(p.dt > 0) || !(p.mass_O > 0) || !(p.mass_H > 0) || !(p.r0 > 0) || !(p.lj_sigma > 0) ||
+      !(p.lj_cutoff > 0) || !(p.lj_cutoff < 0.5 * info.L) || !(p.k_bond >= 0) || !(p.k_angle >= 0) ||
+      !(p.lj_epsilon >= 0))
+    return md_fail(ESP_ERR_INVALID_ARG, "MD parameters: positive dt, masses, r0, sigma; 0 < cutoff < L/2");
+  esp_md_s* md = new esp_md_s();
+  md->plan = plan;
+  md->prm = p;
+  md->device = espe::plan_device(plan);
+  md->n_atoms = info.N;
+  md->n_mol = (int)(info.N / 3);
+  md->L = info.L;
+  md->nc = (int)std::floor(info.L / p.lj_cutoff);
+  md->fp32 = info.precision == ESP_FP32;
+  if (md->nc < 3) md->nc = 0;
+  MdDevice g(md->device);
+  const size_t n3 = (size_t)md->n_atoms * 3;
+  esp_status st = ESP_OK;
+  if ((st = md_alloc(md, &md->d_x, n3)) != ESP_OK || (st = md_alloc(md, &md->d_v, n3)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_f, n3)) != ESP_OK || (st = md_alloc(md, &md->d_ec, 1)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_cell, (size_t)md->n_mol)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_sorted, (size_t)md->n_mol)) != ESP_OK) {
+    md_release(md);
+    delete md;
+    return st;
+  }
+  if (md->nc >= 3) {
+    const long long ncell = (long long)md->nc * md->nc * md->nc;
+    if ((st = md_alloc(md, &md->d_count, (size_t)ncell)) != ESP_OK ||
+        (st = md_alloc(md, &md->d_cursor, (size_t)ncell)) != ESP_OK ||
+        (st = md_alloc(md, &md->d_start, (size_t)ncell + 1)) != ESP_OK ||
+        (st = md_alloc(md, &md->d_tiles, (size_t)espk::scan_tiles(ncell) + 1)) != ESP_OK) {
+      md_release(md);
+      delete md;
+      return st;
+    }
+  }
+  // the three intramolecular pairs of every molecule are excluded
+  std::vector<int32_t> pairs((size_t)md->n_mol * 6);
+  for (int m = 0; m < md->n_mol; ++m) {
+    const int32_t o = 3 * m;
+    const int32_t pr[6] = {o, o + 1, o, o + 2, o + 1, o + 2};
+    std::copy(pr, pr + 6, pairs.begin() + 6ll * m);
+  }
+  if ((st = esp_set_exclusions(plan, pairs.data(), (int64_t)md->n_mol * 3)) != ESP_OK) {
+    md_release(md);
+    delete md;
+    return st;
+  }
+  if (cudaMemcpy(md->d_x, xyz, n3 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(md->d_v, vel, n3 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    md_release(md);
+    delete md;
+    return md_fail(ESP_ERR_CUDA, "copy of the initial state failed");
+  }
+  *out = md;
+  return ESP_OK;
+}
+
+esp_status esp_md_run(esp_md_t md, int n_steps, double* energies) {
+  if (!md || n_steps < 0) return md_fail(ESP_ERR_INVALID_ARG, "NULL md or n_steps < 0");
+  MdDevice g(md->device);
+  cudaStream_t st = espe::plan_stream(md->plan);
+  const long long rows = (long long)n_steps + 1;
+  if (rows > md->e_cap) {
+    if (md->d_e) {
+      md->allocs.erase(std::find(md->allocs.begin(), md->allocs.end(), (void*)md->d_e));
+      cudaFree(md->d_e);
+      md->d_e = nullptr;
+    }
+    esp_status s = md_alloc(md, &md->d_e, (size_t)rows * 4);
+    if (s != ESP_OK) return s;
+    md->e_cap = rows;
+  }
+  MD_CU(cudaMemsetAsync(md->d_e, 0, (size_t)rows * 4 * sizeof(double), st));
+  const MdConst C = make_const(md);
+  const int nb = blocks_of(md->n_atoms);
+  // row 0: the current state (forces computed once, then carried over)
+  if (!md->have_forces) {
+    esp_status s = md_forces(md, md->d_e, st);
+    if (s != ESP_OK) return s;
+    md->have_forces = true;
+  } else {
+    MD_CU(cudaMemcpyAsync(md->d_e, md->e_now, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 0.0, md->d_e + 3);
+  for (int k = 1; k <= n_steps; ++k) {
+    double* e = md->d_e + 4ll * k;
+    k_kick_drift<<<nb, 256, 0, st>>>(md->d_x, md->d_v, md->d_f, C, md->n_atoms);
+    esp_status s = md_forces(md, e, st);
+    if (s != ESP_OK) return s;
+    k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 1.0, e + 3);
+  }
+  MD_CU(cudaGetLastError());
+  std::vector<double> h((size_t)rows * 4);
+  MD_CU(cudaMemcpyAsync(h.data(), md->d_e, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  MD_CU(cudaStreamSynchronize(st));
+  std::copy(h.end() - 4, h.end() - 1, md->e_now);
+  if (energies) std::copy(h.begin(), h.end(), energies);
+  return ESP_OK;
+}
+
+esp_status esp_md_state(esp_md_t md, double* xyz, double* vel) {
+  if (!md) return md_fail(ESP_ERR_INVALID_ARG, "NULL md");
+  MdDevice g(md->device);
+  cudaStream_t st = espe::plan_stream(md->plan);
+  const size_t bytes = (size_t)md->n_atoms * 3 * sizeof(double);
+  if (xyz) MD_CU(cudaMemcpyAsync(xyz, md->d_x, bytes, cudaMemcpyDeviceToHost, st));
+  if (vel) MD_CU(cudaMemcpyAsync(vel, md->d_v, bytes, cudaMemcpyDeviceToHost, st));
+  MD_CU(cudaStreamSynchronize(st));
+  return ESP_OK;
+}
+
+esp_status esp_md_destroy(esp_md_t md) {
+  if (!md) return ESP_OK;
+  {
+    MdDevice g(md->device);
+    cudaStream_t st = espe::plan_stream(md->plan);
+    if (st) cudaStreamSynchronize(st);
+    md_release(md);
+  }
+  delete md;
+  return ESP_OK;
+}
+
+}  // extern "C"

@@ -8,6 +8,7 @@ computes anything itself and raises if the library is not built.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -73,6 +74,15 @@ class esp_plan_params(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class esp_md_params(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("k_bond", ctypes.c_double), ("r0", ctypes.c_double),
+        ("k_angle", ctypes.c_double), ("theta0", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+        ("lj_epsilon", ctypes.c_double), ("lj_cutoff", ctypes.c_double), ("mass_O", ctypes.c_double),
+        ("mass_H", ctypes.c_double), ("reserved", ctypes.c_int * 8),
+    ]
+
+
 class esp_server_opts(ctypes.Structure):
     _fields_ = [
         ("memory_budget", ctypes.c_size_t), ("device", ctypes.c_int), ("max_inflight", ctypes.c_int),
@@ -102,6 +112,11 @@ _SIGNATURES = {
                                 ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
     "esp_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(esp_plan_params)]),
     "esp_set_exclusions": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "esp_md_params_init": (None, [ctypes.POINTER(esp_md_params)]),
+    "esp_md_create": (ctypes.c_int, [_P, ctypes.POINTER(esp_md_params), _P, _P, ctypes.POINTER(_P)]),
+    "esp_md_run": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "esp_md_state": (ctypes.c_int, [_P, _P, _P]),
+    "esp_md_destroy": (ctypes.c_int, [_P]),
     "esp_plan_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
                                      ctypes.POINTER(esp_plan_opts), ctypes.POINTER(_P)]),
     "esp_plan_query_cell": (ctypes.c_int, [ctypes.POINTER(esp_cell), ctypes.c_int64, ctypes.c_double,
@@ -298,6 +313,52 @@ def esp_set_exclusions(plan: int, pairs):
     arr = np.zeros((0, 2), dtype=np.int32) if pairs is None else \
         np.ascontiguousarray(np.asarray(pairs).reshape(-1, 2), dtype=np.int32)
     _check(load_library().esp_set_exclusions(_P(plan), arr.ctypes.data if len(arr) else None, int(len(arr))))
+
+
+COULOMB_KJ_MOL_NM = 138.935458          # 1/(4 pi eps0) in kJ mol^-1 nm e^-2
+MD_PREFACTOR = 4.0 * math.pi * COULOMB_KJ_MOL_NM   # plan prefactor for kJ/mol with the 1/(4 pi r) kernel
+
+
+class MD:
+    """Velocity-Verlet MD of flexible SPC/E-shaped water driven by a plan
+    (esp_md_*). The plan must be cubic, hold (O, H, H) molecules, have its
+    charges set and use prefactor MD_PREFACTOR."""
+
+    def __init__(self, plan: int, xyz, vel, **params):
+        lib = load_library()
+        self.prm = esp_md_params()
+        lib.esp_md_params_init(ctypes.byref(self.prm))
+        for k, v in params.items():
+            setattr(self.prm, k, v)
+        x = np.ascontiguousarray(xyz, dtype=np.float64)
+        v = np.ascontiguousarray(vel, dtype=np.float64)
+        self.n = x.shape[0]
+        out = _P()
+        _check(lib.esp_md_create(_P(plan), ctypes.byref(self.prm), x.ctypes.data, v.ctypes.data, ctypes.byref(out)))
+        self.handle = out.value
+
+    def run(self, n_steps: int) -> np.ndarray:
+        """(n_steps + 1, 4) energies: Coulomb, bonded, Lennard-Jones, kinetic (kJ/mol)."""
+        e = np.zeros((n_steps + 1, 4))
+        _check(load_library().esp_md_run(_P(self.handle), int(n_steps), e.ctypes.data))
+        return e
+
+    def state(self):
+        x = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        _check(load_library().esp_md_state(_P(self.handle), x.ctypes.data, v.ctypes.data))
+        return x, v
+
+    def close(self):
+        if self.handle:
+            load_library().esp_md_destroy(_P(self.handle))
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def esp_plan_info(plan: int) -> dict:

@@ -174,6 +174,16 @@ def spce_water_cell(n_molecules: int, H: np.ndarray | None = None, density: floa
     return CellSystem(pos, q, H, f"water{n_molecules}_cell")
 
 
+def water_velocities(n_molecules: int, temperature: float = 300.0, seed: int = 2505,
+                     mass_o: float = 15.9994, mass_h: float = 1.008) -> np.ndarray:
+    """Maxwell-Boltzmann velocities (nm/ps) of (O, H, H) molecules at the
+    temperature (K), total momentum removed."""
+    rng = np.random.default_rng(seed)
+    m = np.tile([mass_o, mass_h, mass_h], n_molecules)
+    v = rng.normal(size=(m.shape[0], 3)) * np.sqrt(0.0083144626 * temperature / m)[:, None]
+    return v - np.sum(m[:, None] * v, axis=0) / np.sum(m)
+
+
 def electrolyte(n_atoms: int, density: float = 100.0, ion_fraction: float = 0.006,
                 seed: int = 9727, jitter: float = 0.03) -> System:
     """Neutral +-1 ions plus SPC/E-shaped water at a total atom density.
