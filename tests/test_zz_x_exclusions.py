@@ -114,13 +114,13 @@ def test_triclinic_cell_with_exclusions(esp):
 
 
 def test_exclusion_arguments(esp):
-    s = inputs.spce_water(50, seed=24)
-    with esp.Plan(s.L, s.n, 1e-4, r_c=0.9) as p:
+    s = inputs.spce_water(50, seed=24)                       # L = 1.14 nm
+    with esp.Plan(s.L, s.n, 1e-4, r_c=0.5) as p:
         for bad in ([[0, s.n]], [[-1, 2]], [[3, 3]]):
             with pytest.raises(esp.EspError) as exc:
                 esp.esp_set_exclusions(p.handle, np.array(bad))
             assert exc.value.status == 1
-    with esp.Plan(s.L, s.n, 1e-4, r_c=0.9, virial=1) as p:
+    with esp.Plan(s.L, s.n, 1e-4, r_c=0.5, virial=1) as p:
         with pytest.raises(esp.EspError) as exc:
             esp.esp_set_exclusions(p.handle, md.exclusion_pairs(s.n))
         assert exc.value.status == 10
