@@ -172,3 +172,25 @@ def test_planner_rejects_bad_ik_and_virial_options(lib, kw, status):
     with pytest.raises(lib.EspError) as exc:
         lib.esp_plan_query(10.0, 1000, 1e-4, r_c=1.0, **kw)
     assert exc.value.status == status
+
+
+def test_md_and_exclusion_entry_points_without_device(lib):
+    """esp_md_* and esp_set_exclusions reject NULL handles before any device
+    work; the MD defaults are the oracle's water model (oracle/md.py)."""
+    import ctypes
+    import math
+    from oracle import md
+    so = lib.load_library()
+    assert so.esp_set_exclusions(None, None, 0) == 1
+    p = lib.esp_md_params()
+    so.esp_md_params_init(ctypes.byref(p))
+    m = md.WaterModel()
+    assert (p.k_bond, p.r0, p.k_angle, p.lj_sigma, p.lj_epsilon, p.mass_O, p.mass_H) == \
+        (m.k_bond, m.r0, m.k_angle, m.sigma, m.epsilon, m.m_O, m.m_H)
+    assert abs(p.theta0 - m.theta0) < 1e-15 and p.dt == 0.0005
+    out = ctypes.c_void_p()
+    assert so.esp_md_create(None, ctypes.byref(p), None, None, ctypes.byref(out)) == 1
+    assert so.esp_md_run(None, 1, None) == 1
+    assert so.esp_md_state(None, None, None) == 1
+    assert so.esp_md_destroy(None) == 0
+    assert abs(lib.MD_PREFACTOR - 4 * math.pi * md.COULOMB_F) < 1e-9
