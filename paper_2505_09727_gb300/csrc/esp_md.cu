@@ -204,9 +204,12 @@ template <typename real>
 __global__ void k_lj(const double* __restrict__ x, const uint32_t* __restrict__ cell,
                      const uint32_t* __restrict__ start, const uint32_t* __restrict__ sorted, MdConst C,
                      double* __restrict__ f, double* __restrict__ el) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
   real e = 0;
   if (m < C.n_mol) {
+    // with cells, threads take the O atoms in cell order: the lanes of a
+    // warp then read the same neighbouring cells
+    if (C.nc >= 3) m = (int)sorted[m];
     const real xi[3] = {(real)x[9ll * m], (real)x[9ll * m + 1], (real)x[9ll * m + 2]};
     real fi[3] = {0, 0, 0};
     if (C.nc >= 3) {
