@@ -586,6 +586,10 @@ class Plan:
     def set_positions(self, xyz, where=None):
         esp_set_positions(self.handle, xyz, where)
 
+    def set_exclusions(self, pairs):
+        """Pairs (n, 2) of atom indices without direct interaction (None clears)."""
+        esp_set_exclusions(self.handle, pairs)
+
     def compute(self):
         """Host arrays: returns (energy, forces (N,3), potential (N,))."""
         e = np.zeros(1)
