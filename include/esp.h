@@ -66,7 +66,9 @@ typedef enum {
   ESP_ERR_CUFFT = 7,           /* cuFFT error                                 */
   ESP_ERR_TIMEOUT = 8,         /* a device wait exceeded the plan deadline    */
   ESP_ERR_BUSY = 9,            /* admission refused (memory budget)           */
-  ESP_ERR_UNSUPPORTED = 10,    /* a size beyond a compiled limit (e.g. P>16) */
+  ESP_ERR_UNSUPPORTED = 10,    /* a size beyond a compiled limit (e.g. P>16)
+                                  or an option combination without a kernel
+                                  (e.g. a triclinic cell in FP64)             */
   ESP_ERR_INTERNAL = 11,       /* a kernel bounds check failed                */
   ESP_ERR_NOT_READY = 12       /* positions or charges not set yet           */
 } esp_status;
