@@ -56,12 +56,14 @@ class ESPParams:
     alpha: float | None = None    # Gaussian shape (default: ln(1/eps))
     window: str = "pswf"          # SI window: "pswf" (psi_0^{c1}) or "bspline" (order P)
     diff: str = "ad"              # spectral forces: "ad" (derivatives of phi) or "ik"
+    virial_nyquist: str = "component"   # off-diagonal Nyquist products (spectral_virial)
 
     def resolved(self) -> "ESPParams":
         c = self.c if self.c is not None else pswf.c_from_tolerance(self.eps)
         c1 = self.c1 if self.c1 is not None else prm.C1_RATIO * c
         alpha = self.alpha if self.alpha is not None else math.log(1.0 / self.eps)
-        return ESPParams(self.eps, self.r_c, self.P, self.n_f, c, c1, self.kind, alpha, self.window, self.diff)
+        return ESPParams(self.eps, self.r_c, self.P, self.n_f, c, c1, self.kind, alpha, self.window, self.diff,
+                         self.virial_nyquist)
 
     def si_window(self):
         p = self.resolved()
@@ -165,16 +167,27 @@ def influence_virial(L, n_f, r_c, split, window):
     return d / den
 
 
-def spectral_virial(bh, p, pv, n_f):
+def spectral_virial(bh, p, pv, n_f, nyquist="component"):
     """sum_k 1/2 |bh_k|^2 [p_k delta + p'_k k k^T / |k|^2] (3 x 3).
 
-    A Nyquist index k_a = -n_f/2 stands for both aliases +-n_f/2; the
-    off-diagonal products k_a k_b (a != b) take their average, zero
-    (reading for even n_f; the diagonal k_a^2 is the same for both)."""
+    A Nyquist index k_a = -n_f/2 stands for both aliases +-n_f/2 (the
+    diagonal k_a^2 is the same for both). Off-diagonal products k_a k_b:
+    "component" (R27): each Nyquist component is averaged on its own, so a
+    product with any Nyquist component is zero. "alias": the mode and the
+    representative of -k, whose Nyquist components flip together (the
+    pairing the real part of the inverse transform applies to the energy of
+    a deformed cell): zero when exactly one of k_a, k_b is Nyquist, k_a k_b
+    when both are. "alias" is the exact -dE/d eps_ab; the two differ only
+    through the modes with two Nyquist components."""
     k = np.fft.fftfreq(n_f, d=1.0 / n_f)
     K = np.stack(np.meshgrid(k, k, k, indexing="ij"))         # (3, n, n, n)
-    ks = np.where(k == -(n_f // 2), 0.0, k) if n_f % 2 == 0 else k
-    Ks = np.stack(np.meshgrid(ks, ks, ks, indexing="ij"))
+    if nyquist == "alias" and n_f % 2 == 0:
+        nyq = K == -(n_f // 2)
+        Kp = {(i, j): np.where(nyq[i] ^ nyq[j], 0.0, K[i] * K[j]) for i in range(3) for j in range(3)}
+    else:
+        ks = np.where(k == -(n_f // 2), 0.0, k) if n_f % 2 == 0 else k
+        Ks = np.stack(np.meshgrid(ks, ks, ks, indexing="ij"))
+        Kp = {(i, j): Ks[i] * Ks[j] for i in range(3) for j in range(3)}
     k2 = np.sum(K * K, axis=0)
     a = 0.5 * np.abs(bh) ** 2
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -182,11 +195,11 @@ def spectral_virial(bh, p, pv, n_f):
     W = np.eye(3) * float(np.sum(a * p))
     for i in range(3):
         for j in range(3):
-            W[i, j] += float(np.sum(t * K[i] * K[j])) if i == j else float(np.sum(t * Ks[i] * Ks[j]))
+            W[i, j] += float(np.sum(t * K[i] * K[j])) if i == j else float(np.sum(t * Kp[(i, j)]))
     return W
 
 
-def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad", virial=None):
+def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad", virial=None, virial_nyquist="component"):
     """Steps 1-5: (u~ at targets, grad u~ at targets, 1/2 sum_k p_k |bh_k|^2).
     With a dict `virial`, its key "spectral" receives the spectral virial."""
     b = spread(pos, q, L, n_f, window)
@@ -194,7 +207,8 @@ def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad", virial=Non
     p = influence(L, n_f, r_c, split, window)
     fourier_energy = 0.5 * float(np.sum(p * np.abs(bh) ** 2))
     if virial is not None:
-        virial["spectral"] = spectral_virial(bh, p, influence_virial(L, n_f, r_c, split, window), n_f)
+        virial["spectral"] = spectral_virial(bh, p, influence_virial(L, n_f, r_c, split, window), n_f,
+                                             virial_nyquist)
     ch = p * bh
     cgrid = np.fft.fftn(ch).real                              # exp(-2 pi i k.l/n_f)
     idx, w, dw = stencil(pos[targets], L, n_f, window)
@@ -274,7 +288,8 @@ def esp(pos, q, L, p: ESPParams, targets=None):
     split = p.split()
     window = p.si_window()
     parts = {} if all_atoms else None
-    u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt, p.diff, parts)
+    u_s, grad_s, e_fourier = far_field(pos, q, L, p.n_f, p.r_c, split, window, tgt, p.diff, parts,
+                                       p.virial_nyquist)
     u_l, f_l = near_field(pos, q, L, p.r_c, split, tgt, parts)
     self_term = q[tgt] * split.chi0 / (4.0 * math.pi * p.r_c)
     Q = float(np.sum(q))

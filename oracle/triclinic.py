@@ -125,10 +125,19 @@ def ewald_converged(pos, q, H, acc: float = 1e-14):
     return ewald(pos, q, H, g, r_cut, xi_max)
 
 
-def esp(pos, q, H, split, window, n_f: int, r_c: float):
+def esp(pos, q, H, split, window, n_f: int, r_c: float, virial: bool = False):
     """ESP on the lattice H (module docstring). split, window: the oracle's
     splitting function and SI kernel (oracle.pswf / oracle.bspline).
-    Returns dict(energy, potential, forces, fourier_energy)."""
+    Returns dict(energy, potential, forces, fourier_energy, virial).
+
+    virial: W_ab = -dE/d eps_ab under r -> (1 + eps) r, H -> (1 + eps) H (the
+    grid deforms with the cell, so b_l and the grid-unit Phi stay; xi(k)
+    becomes (1 + eps)^-T xi and V becomes V (1 + tr eps)): the spectral part
+    sum_k 1/2 |bh_k|^2 [p_k delta_ab + p'_k xi_a xi_b / |xi|^2] with
+    p'_k = (r_c |xi| chihat'(r_c |xi|) - 2 chihat(r_c |xi|)) / (|xi|^2 V Phi^6),
+    averaged over the two aliases of a mode with a component -n_f/2 (the
+    reading of the energy, R28); the local part 1/2 sum_ij F_ij d_ij^T; the
+    background E_bg delta_ab."""
     pos = np.asarray(pos, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     n = pos.shape[0]
@@ -160,6 +169,19 @@ def esp(pos, q, H, split, window, n_f: int, r_c: float):
         shat = np.where(xin > 0, split.chihat(r_c * xin) / xin ** 2, 0.0)
     p = shat / den
     fourier_energy = 0.5 * float(np.sum(p * np.abs(bh) ** 2))
+    W = np.zeros((3, 3))
+    if virial:
+        a = 0.5 * np.abs(bh) ** 2
+        for alias in (K, np.where(K == -(n_f // 2), n_f // 2, K)):
+            xa = 2.0 * math.pi * alias @ np.linalg.inv(H)
+            x = np.sqrt(np.sum(xa * xa, axis=-1))
+            with np.errstate(divide="ignore", invalid="ignore"):
+                pa = np.where(x > 0, split.chihat(r_c * x) / x ** 2, 0.0) / den
+                pv = np.where(x > 0, (r_c * x * split.dchihat(r_c * x) - 2.0 * split.chihat(r_c * x)) / x ** 2,
+                              0.0) / den
+                t = np.where(x > 0, a * pv / x ** 2, 0.0)
+            W += 0.5 * np.eye(3) * float(np.sum(a * pa))
+            W += 0.5 * np.einsum("xyza,xyzb,xyz->ab", xa, xa, t)
     cgrid = np.fft.fftn(p * bh).real
     # 5. interpolate potential and fractional gradient, grad_r = H^-T grad_s
     u = np.zeros(n)
@@ -180,7 +202,13 @@ def esp(pos, q, H, split, window, n_f: int, r_c: float):
     np.add.at(u, i, q[j] * omg / (4.0 * math.pi * r))
     mag = (omg / r ** 2 + split.chi(x) / (r_c * r)) / (4.0 * math.pi)
     np.add.at(f, i, (q[i] * q[j] * mag / r)[:, None] * d)
+    if virial:
+        W += 0.5 * np.einsum("n,na,nb->ab", q[i] * q[j] * mag / r, d, d)
     # self term and neutralising background
     Q = float(np.sum(q))
-    u += -q * split.chi0 / (4.0 * math.pi * r_c) - (Q / V) * 0.5 * r_c ** 2 * split.second_moment()
-    return dict(energy=0.5 * float(np.dot(q, u)), potential=u, forces=f, fourier_energy=fourier_energy)
+    bg = -(Q / V) * 0.5 * r_c ** 2 * split.second_moment()
+    u += -q * split.chi0 / (4.0 * math.pi * r_c) + bg
+    if virial:
+        W += 0.5 * Q * bg * np.eye(3)
+    return dict(energy=0.5 * float(np.dot(q, u)), potential=u, forces=f, fourier_energy=fourier_energy,
+                virial=W if virial else None)

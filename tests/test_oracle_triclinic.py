@@ -127,3 +127,53 @@ def test_triclinic_forces_are_the_energy_gradient():
             p2[i, a] += sgn * h
             e.append(tr.esp(p2, q, H, split, window, n_f, 1.0)["energy"])
         assert abs(-(e[0] - e[1]) / (2 * h) - f[i, a]) <= 1e-7 * np.max(np.abs(f))
+
+
+def _deformation_fd(energy_of, H, pos, h=1e-6):
+    """W_ab = -dE/d eps_ab by central differences under r -> (1 + eps) r,
+    H -> (1 + eps) H with a symmetric eps."""
+    W = np.zeros((3, 3))
+    for a in range(3):
+        for b in range(a, 3):
+            e = []
+            for sgn in (1.0, -1.0):
+                eps = np.zeros((3, 3))
+                eps[a, b] += sgn * h
+                if a != b:
+                    eps[b, a] += sgn * h
+                D = np.eye(3) + eps
+                e.append(energy_of(pos @ D.T, D @ H))
+            W[a, b] = W[b, a] = -(e[0] - e[1]) / (2 * h) / (1.0 if a == b else 2.0)
+    return W
+
+
+def test_triclinic_virial_is_the_deformation_derivative():
+    rng = np.random.default_rng(17)
+    H = tr.box_matrix([3.2, 0, 0], [0.9, 3.0, 0], [-0.6, 0.7, 2.9])
+    n = 60
+    pos = rng.random((n, 3)) @ H.T
+    q = np.repeat([1.0, -1.0], n // 2)
+    q[0] += 0.3                                                  # background term too
+    split, window, n_f = _esp_params(1e-4, H, 1.0)
+    W = tr.esp(pos, q, H, split, window, n_f, 1.0, virial=True)["virial"]
+    fd = _deformation_fd(lambda x, Hd: tr.esp(x, q, Hd, split, window, n_f, 1.0)["energy"], H, pos)
+    assert np.max(np.abs(W - fd)) <= 1e-7 * np.max(np.abs(W))
+
+
+def test_cube_virial_readings_against_the_deformation_derivative():
+    """The cube's full virial tensor pinned by shearing it (the triclinic
+    energy of the deformed cell): the "alias" Nyquist reading is the exact
+    derivative; the "component" reading (R27, the CUDA path's) differs only
+    in the off-diagonal terms of modes with two Nyquist components."""
+    import dataclasses
+    s = inputs.uniform_charges(80, 3.0, 5)
+    p = oesp.default_params(1e-4, s.L, 1.1).resolved()
+    H = s.L * np.eye(3)
+    fd = _deformation_fd(lambda x, Hd: tr.esp(x, s.q, Hd, p.split(), p.si_window(), p.n_f, p.r_c)["energy"],
+                         H, s.pos)
+    W_alias = oesp.esp(s.pos, s.q, s.L, dataclasses.replace(p, virial_nyquist="alias"))["virial"]
+    W_comp = oesp.esp(s.pos, s.q, s.L, p)["virial"]
+    scale = np.max(np.abs(fd))
+    assert np.max(np.abs(W_alias - fd)) <= 1e-7 * scale
+    assert np.array_equal(np.diag(W_alias), np.diag(W_comp))
+    assert 0 < np.max(np.abs(W_comp - W_alias)) <= 1e-5 * scale
