@@ -14,6 +14,9 @@ Modules
   esp     plain CPU ESP: five-step spectral part, local part, self/background
   params  the paper's parameter rules and Table 2
   metrics relative RMS force error (Eq. Deltadef)
+  bspline centred cardinal B-spline window (the "Default" comparator)
+  triclinic  Ewald and ESP on a general lattice (triclinic cells), virial
+  md      the MD loop workload: flexible water, exclusions, velocity Verlet
 
 Parity status: every function here is pinned by tests under ``tests/`` that
 do not use the CUDA path (``-m "not gpu"``), except the parameter *planner
