@@ -104,9 +104,10 @@ typedef struct {
   int cell_reach;      /* tuning: cell edge ~ r_c / cell_reach (2 or 3; 0 auto) */
   int window;          /* SI kernel: ESP_WINDOW_PSWF (default, Eq. pswf) or
                           ESP_WINDOW_BSPLINE (centred cardinal B-spline of
-                          order P, default P 4, n_f raised until the aliasing
-                          estimate is <= tolerance/10: the "Default" PME-style
-                          comparator of Table 1, meant with ESP_KERNEL_GAUSS) */
+                          order P, default P 5, n_f = R_default^(1/3) c L /
+                          (pi r_c) with Table 2's R_default: the "Default"
+                          PME-style comparator of Tables 1 and 2, meant with
+                          ESP_KERNEL_GAUSS)                                  */
   int near_variant;    /* tuning: local-part kernel, 1 = one thread per atom,
                           pairs evaluated in the scan, 2 = the same with pairs
                           queued per lane, 3 = one warp per cluster of 8 atoms,
@@ -221,8 +222,9 @@ esp_status esp_set_positions_f32(esp_plan_t plan, const float* xyz, int where);
  * image nearest in wrapped fractional coordinates, the minimum image for
  * pairs closer than half the smallest cell height. n_pairs = 0 clears the
  * list. pairs is a host array, copied; the call first waits for the plan's
- * stream. ESP_ERR_INVALID_ARG for an index outside [0, N) or i = j;
- * ESP_ERR_UNSUPPORTED on a plan made with opts.virial. */
+ * stream. ESP_ERR_INVALID_ARG for an index outside [0, N), i = j, or a pair
+ * listed more than once (in either order); ESP_ERR_UNSUPPORTED on a plan
+ * made with opts.virial. */
 esp_status esp_set_exclusions(esp_plan_t plan, const int32_t* pairs, int64_t n_pairs);
 
 /* Spread, R2C FFT, fused influence scale + spectral energy, C2R FFT, gather,
@@ -385,6 +387,12 @@ typedef struct {
   size_t memory_budget;
   double latency_p50_ms, latency_p99_ms, latency_max_ms;
   double wall_ms;             /* first submission to last completion                  */
+  /* Overlap on the device, from events recorded on each request's stream
+   * before its first copy and after its last: every completed request's
+   * device interval [start, done]. */
+  int64_t peak_inflight;      /* most requests admitted to the device at once         */
+  int64_t peak_concurrent;    /* most device intervals that overlap at one instant    */
+  double overlap_ms;          /* device time with two or more requests in flight      */
 } esp_server_counters;
 
 void esp_server_opts_init(esp_server_opts* opts);
@@ -416,7 +424,7 @@ esp_status esp_server_destroy(esp_server_t server);
  *
  * For N charges q[N] at xyz[N*3] (both FP64, in device memory of
  * opts->device) it computes what esp_compute returns minus the spectral part:
- * the local part of Eq. localpart within r_c, the self term and, when
+ * the direct pair sum of the split within r_c, the self term and, when
  * sum q != 0 and allow_background is set, the neutralising background:
  *   potential[i] = u^l_i - q_i chi(0)/(4 pi r_c) + background,
  *   forces[i]    = F^l_i,
@@ -429,14 +437,18 @@ esp_status esp_server_destroy(esp_server_t server);
  * Working memory comes from one 6 MiB array in the library's device image,
  * which every GPU that loads the library holds until the process exits:
  * about 65k atoms in FP32 mode and 32k in FP64 mode fit; larger systems are
- * rejected with ESP_ERR_UNSUPPORTED before any device work. The first call
- * on a device looks up the array's address with that device current; make
- * that first call before any stream capture. The call reads the charges back
- * to the host (a synchronising copy) and then enqueues its kernels on the
- * stream without waiting for them. Every call shares the array, and each
- * call clears what it reads before writing it; calls whose device work
- * overlaps (on different streams or host threads) race on the array and
- * must be serialised by the caller. */
+ * rejected with ESP_ERR_UNSUPPORTED before any device work. xyz, q and every
+ * non-NULL output must be device (or managed) memory of opts->device, else
+ * ESP_ERR_INVALID_ARG before any launch. The first call on a device looks up
+ * the array's address with that device current; make that first call before
+ * any stream capture. The call reads the charges back to the host (a
+ * synchronising copy), enqueues its kernels on the stream and waits for them
+ * to read their error flag: a NaN or infinite position gives
+ * ESP_ERR_NONFINITE (the outputs are then not valid), a failed bounds check
+ * ESP_ERR_INTERNAL. Every call shares the array, and each call clears what it
+ * reads before writing it; calls whose device work overlaps (on different
+ * streams or host threads) race on the array and must be serialised by the
+ * caller. */
 esp_status esp_local_part_static(const esp_box* box, int64_t N, double tolerance,
                                  const esp_plan_opts* opts, const double* xyz,
                                  const double* q, double* energy, double* forces,
@@ -486,6 +498,8 @@ esp_status esp_md_run(esp_md_t md, int n_steps, double* energies);
 
 /* Current positions and velocities (host, N x 3; either may be NULL). */
 esp_status esp_md_state(esp_md_t md, double* xyz, double* vel);
+/* Free the MD state and clear the plan's exclusion list (the intramolecular
+ * pairs esp_md_create set), so later computes on the plan count every pair. */
 esp_status esp_md_destroy(esp_md_t md);
 
 #ifdef __cplusplus

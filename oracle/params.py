@@ -114,33 +114,42 @@ def next_grid(n: int) -> int:
     return round_grid(n + 1)
 
 
-BSPLINE_ORDER = 4          # the usual smooth-PME order; the comparator's default
-# The aliasing estimate is calibrated on the PSWF window; for the B-spline
-# window the same acceptance leaves the measured error above the tolerance
-# (order 4: 1.2e-4 at 1e-4 on 300 ions), so the comparator accepts at 0.1 eps
-# (measured <= eps at 1e-3, 1e-4, 1e-5 on ions and water). A reading:
-# parity unpinned, pinned only by the measured errors against Ewald.
-ALIAS_TARGET_BSPLINE = 0.1
+BSPLINE_ORDER = 5          # the default of both MD packages (Table 2's caption)
 
 
-def plan_bspline(eps: float, L: float, r_c: float, P: int = BSPLINE_ORDER, max_steps: int = 200):
-    """The "Default" comparator: Gaussian split (alpha = ln(1/eps), Table 2's
-    alpha_G) with the cardinal B-spline window of order P; n_f starts at
-    Eq. cemparameters and is raised to the next FFT-friendly size until the
-    relative aliasing estimate is <= ALIAS_TARGET_BSPLINE * eps.
+def default_grid_ratio(eps: float) -> float:
+    """R_default(eps)^(1/3): the per-axis grid ratio of the default PME (Gaussian
+    split, B-spline order 5, n_f raised until the error is met) to ESP, from
+    Table 2's last row, interpolated linearly in (log eps, log R) between the
+    tabulated tolerances and extrapolated along the nearest segment."""
+    tols = sorted(TABLE2)                                   # 1e-5 ... 1e-3
+    x = [math.log(t) for t in tols]
+    y = [math.log(TABLE2[t][3]) for t in tols]
+    lx = math.log(eps)
+    k = 0
+    while k < len(x) - 2 and lx > x[k + 1]:
+        k += 1
+    logR = y[k] + (y[k + 1] - y[k]) * (lx - x[k]) / (x[k + 1] - x[k])
+    return math.exp(logR / 3.0)
+
+
+def plan_bspline(eps: float, L: float, r_c: float, P: int = BSPLINE_ORDER):
+    """The "Default" comparator (Methods, classical fast Ewald methods): the
+    Gaussian split (Eq. cem, alpha = ln(1/eps), Table 2's alpha_G) with the
+    cardinal B-spline window of order P, on the grid Table 2 says the default
+    PME needs for the same error: n_f = R_default^(1/3) times ESP's
+    Eq. pswfparameters value c L / (pi r_c), at least Eq. cemparameters' value,
+    rounded up to an even FFT-friendly size. The relative aliasing estimate
+    (Eq. errorformula) at that grid is reported with it.
     Returns dict(kind, window, alpha, P, n_f, alias)."""
     from . import bspline
     if not r_c < 0.5 * L:
         raise ValueError("r_c must be smaller than L/2")
     alpha = math.log(1.0 / eps)
-    split = pswf.GaussianSplit(alpha)
-    window = bspline.BSplineWindow(P)
-    n_f = round_grid(gauss_grid_min(eps, L, r_c))
-    for _ in range(max_steps):
-        err = aliasing_error(split, 0.0, P, n_f, L, r_c, window=window)
-        if err <= ALIAS_TARGET_BSPLINE * eps or n_f >= 1024:
-            break
-        n_f = next_grid(n_f)
+    c = pswf.c_from_tolerance(eps)
+    n_min = max(gauss_grid_min(eps, L, r_c), default_grid_ratio(eps) * pswf_grid_min(c, L, r_c))
+    n_f = round_grid(n_min)
+    err = aliasing_error(pswf.GaussianSplit(alpha), 0.0, P, n_f, L, r_c, window=bspline.BSplineWindow(P))
     return dict(kind="gauss", window="bspline", alpha=alpha, P=P, n_f=n_f, alias=err)
 
 

@@ -345,6 +345,20 @@ int stencil_width(double eps) {
   return (int)std::ceil(std::log10(1.0 / eps)) + 3;
 }
 
+double default_grid_ratio(double eps) {
+  // Table 2, last row: R_default = 5.78, 7.71, 14.32, 22.42, 54.57 at
+  // eps = 1e-3, 5e-4, 1e-4, 5e-5, 1e-5; (log eps, log R) interpolated
+  // linearly, extrapolated along the nearest segment; per axis R^(1/3)
+  const double tol[5] = {1e-5, 5e-5, 1e-4, 5e-4, 1e-3};
+  const double R[5] = {54.57, 22.42, 14.32, 7.71, 5.78};
+  const double lx = std::log(eps);
+  int k = 0;
+  while (k < 3 && lx > std::log(tol[k + 1])) ++k;
+  const double x0 = std::log(tol[k]), x1 = std::log(tol[k + 1]);
+  const double y0 = std::log(R[k]), y1 = std::log(R[k + 1]);
+  return std::exp((y0 + (y1 - y0) * (lx - x0) / (x1 - x0)) / 3.0);
+}
+
 bool is_smooth(int n) {
   if (n <= 0) return false;
   for (int p : {2, 3, 5, 7}) while (n % p == 0) n /= p;

@@ -67,6 +67,9 @@ double alias_relative(const Split& s, const Window& w, int n_f, double L, double
 
 // Table 2 stencil width, smooth even grid sizes.
 int stencil_width(double eps);
+// Table 2's R_default^(1/3): per-axis grid ratio of the default PME
+// (Gaussian split, B-spline order 5) to ESP at the same error.
+double default_grid_ratio(double eps);
 bool is_smooth(int n);
 int round_grid(double n);
 

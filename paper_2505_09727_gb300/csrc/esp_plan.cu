@@ -362,8 +362,8 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   }
   const bool bspline = o.window == ESP_WINDOW_BSPLINE;
   const double c = o.c > 0 ? o.c : cached_c(tol);
-  // the B-spline comparator defaults to the usual smooth-PME order 4
-  const int P = o.P > 0 ? o.P : (bspline ? 4 : espm::stencil_width(tol));
+  // the B-spline comparator defaults to order 5, the MD packages' default
+  const int P = o.P > 0 ? o.P : (bspline ? 5 : espm::stencil_width(tol));
   if (P < espk::kMinP || P > pmax) {
     msg = "stencil width P=" + std::to_string(P) + " outside the compiled range [4, " + std::to_string(pmax) + "]";
     return ESP_ERR_UNSUPPORTED;
@@ -401,40 +401,21 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   double best_c1 = ratios[0] * c, best_alias = 1e300;
   espm::Window bwin;
   if (bspline) {
-    // B-spline window: no shape to choose; the aliasing estimate is
-    // calibrated on the PSWF window, so the comparator accepts at 0.1 eps
-    // (measured errors against Ewald stay below eps); the smallest
-    // FFT-friendly n_f that meets it is found by bisection (the estimate
-    // falls with n_f)
+    // B-spline window (the "Default" comparator): no shape to choose; unless
+    // n_f is given, the grid is the one Table 2 says the default PME needs
+    // for the same error, R_default^(1/3) times ESP's c L / (pi r_c) (and at
+    // least the Gaussian truncation minimum); the aliasing estimate at that
+    // grid is reported
     bwin = espm::make_bspline_window(P);
     best_c1 = 0.0;
-    auto alias_at = [&](int n) { return alias_from_rows(alias_rows(chi, n), bwin, n); };
-    if (o.n_f > 0) {
-      best_alias = alias_at(n_f);
-    } else {
-      std::vector<int> ladder;
-      for (int n = n_f; n <= 1024; n = espm::round_grid(n + 1)) ladder.push_back(n);
-      // the first ladder entry that meets the acceptance: probe upwards with
-      // steps that double (the estimate's cost grows as n^3, so the largest
-      // grids are evaluated only when needed), then bisect the last bracket
-      const int last = (int)ladder.size() - 1;
-      int lo = 0, hi = last, step = 1, probe = 0;
-      bool met = false;
-      while (true) {
-        if (alias_at(ladder[probe]) <= 0.1 * tol) { hi = probe; met = true; break; }
-        lo = probe + 1;
-        if (probe == last) break;
-        probe = std::min(last, probe + step);
-        step *= 2;
-      }
-      if (!met) lo = hi = last;                                 // even the largest grid does not meet it
-      while (lo < hi) {
-        const int mid = (lo + hi) / 2;
-        if (alias_at(ladder[mid]) <= 0.1 * tol) hi = mid; else lo = mid + 1;
-      }
-      n_f = ladder[lo];
-      best_alias = alias_at(n_f);
+    if (o.n_f == 0) {
+      const double c_esp = cached_c(tol);
+      const double nmin = std::max(2.0 * std::ceil(std::log(1.0 / tol) * L / (kPi * r_c)),
+                                   espm::default_grid_ratio(tol) * c_esp * L / (kPi * r_c));
+      n_f = espm::round_grid(std::max(4.0, nmin));
+      if (n_f > 1024) { msg = "grid too large (n_f > 1024): raise r_c or the tolerance"; return ESP_ERR_UNSUPPORTED; }
     }
+    best_alias = alias_from_rows(alias_rows(chi, n_f), bwin, n_f);
   } else {
     std::vector<espm::Window> windows;
     for (double r : ratios) windows.push_back(cached_window(r * c, P));

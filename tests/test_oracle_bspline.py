@@ -64,7 +64,10 @@ def test_derivative_matches_finite_difference(P):
 def test_comparator_needs_a_finer_grid_than_esp():
     b = params.plan_bspline(1e-4, 14.4129, 1.0)
     e = params.plan(1e-4, 14.4129, 1.0)
-    assert b["alias"] <= 0.1e-4 and b["n_f"] > 2 * e["n_f"]
+    assert b["P"] == 5 and b["n_f"] > 2 * e["n_f"]
+    # the grid ratio is Table 2's R_default (up to the FFT-friendly rounding)
+    R = (b["n_f"] / params.pswf_grid_min(params.TABLE2[1e-4][1], 14.4129, 1.0)) ** 3
+    assert 14.32 <= R <= 14.32 * 1.08 ** 3
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-5])
