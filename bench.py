@@ -337,7 +337,7 @@ def run_gpu(args, world, rank, local):
         extras["batched"] = batched(args, local, stream, flush)
         extras["served"] = served(args, local)
         extras["large"] = large(args, local, stream, flush)
-        # a triclinic cell (R28): the same water density in a truncated
+        # a triclinic cell: the same water density in a truncated
         # octahedron; last, and guarded, so that it cannot cost the lines above
         try:
             extras["triclinic"] = triclinic(args, local, stream, flush)

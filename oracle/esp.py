@@ -56,7 +56,7 @@ class ESPParams:
     alpha: float | None = None    # Gaussian shape (default: ln(1/eps))
     window: str = "pswf"          # SI window: "pswf" (psi_0^{c1}) or "bspline" (order P)
     diff: str = "ad"              # spectral forces: "ad" (derivatives of phi) or "ik"
-    virial_nyquist: str = "component"   # off-diagonal Nyquist products (spectral_virial)
+    virial_nyquist: str = "alias"       # off-diagonal Nyquist products (spectral_virial)
 
     def resolved(self) -> "ESPParams":
         c = self.c if self.c is not None else pswf.c_from_tolerance(self.eps)
@@ -167,18 +167,19 @@ def influence_virial(L, n_f, r_c, split, window):
     return d / den
 
 
-def spectral_virial(bh, p, pv, n_f, nyquist="component"):
+def spectral_virial(bh, p, pv, n_f, nyquist="alias"):
     """sum_k 1/2 |bh_k|^2 [p_k delta + p'_k k k^T / |k|^2] (3 x 3).
 
     A Nyquist index k_a = -n_f/2 stands for both aliases +-n_f/2 (the
     diagonal k_a^2 is the same for both). Off-diagonal products k_a k_b:
-    "component" (R27): each Nyquist component is averaged on its own, so a
-    product with any Nyquist component is zero. "alias": the mode and the
-    representative of -k, whose Nyquist components flip together (the
-    pairing the real part of the inverse transform applies to the energy of
-    a deformed cell): zero when exactly one of k_a, k_b is Nyquist, k_a k_b
-    when both are. "alias" is the exact -dE/d eps_ab; the two differ only
-    through the modes with two Nyquist components."""
+    "alias" (default): the mode and the representative of -k, whose Nyquist
+    components flip together (the pairing the real part of the inverse
+    transform applies to the energy of a deformed cell): zero when exactly
+    one of k_a, k_b is Nyquist, k_a k_b when both are. This is the exact
+    -dE/d eps_ab (pinned by shearing the cube through the triclinic oracle).
+    "component": each Nyquist component averaged on its own, so a product
+    with any Nyquist component is zero; kept for comparison, it differs from
+    the derivative only through the modes with two Nyquist components."""
     k = np.fft.fftfreq(n_f, d=1.0 / n_f)
     K = np.stack(np.meshgrid(k, k, k, indexing="ij"))         # (3, n, n, n)
     if nyquist == "alias" and n_f % 2 == 0:
@@ -199,7 +200,7 @@ def spectral_virial(bh, p, pv, n_f, nyquist="component"):
     return W
 
 
-def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad", virial=None, virial_nyquist="component"):
+def far_field(pos, q, L, n_f, r_c, split, window, targets, diff="ad", virial=None, virial_nyquist="alias"):
     """Steps 1-5: (u~ at targets, grad u~ at targets, 1/2 sum_k p_k |bh_k|^2).
     With a dict `virial`, its key "spectral" receives the spectral virial."""
     b = spread(pos, q, L, n_f, window)

@@ -136,8 +136,9 @@ def esp(pos, q, H, split, window, n_f: int, r_c: float, virial: bool = False):
     sum_k 1/2 |bh_k|^2 [p_k delta_ab + p'_k xi_a xi_b / |xi|^2] with
     p'_k = (r_c |xi| chihat'(r_c |xi|) - 2 chihat(r_c |xi|)) / (|xi|^2 V Phi^6),
     averaged over the two aliases of a mode with a component -n_f/2 (the
-    reading of the energy, R28); the local part 1/2 sum_ij F_ij d_ij^T; the
-    background E_bg delta_ab."""
+    real part of the inverse transform applies that average to the energy,
+    so its derivative carries it too); the local part 1/2 sum_ij F_ij
+    d_ij^T; the background E_bg delta_ab."""
     pos = np.asarray(pos, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     n = pos.shape[0]

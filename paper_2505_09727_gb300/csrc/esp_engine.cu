@@ -1089,12 +1089,20 @@ esp_status esp_set_exclusions(esp_plan_t p, const int32_t* pairs, int64_t n_pair
   if (!p || n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(ESP_ERR_INVALID_ARG, "NULL plan or pairs, or n_pairs < 0");
   if (p->nsys != 1) return fail(ESP_ERR_UNSUPPORTED, "exclusions belong to single-system plans");
   if (p->virial && n_pairs > 0) return fail(ESP_ERR_UNSUPPORTED, "exclusions are not combined with the virial");
+  std::vector<std::pair<int32_t, int32_t>> sorted_pairs((size_t)n_pairs);
   for (int64_t k = 0; k < n_pairs; ++k) {
     const int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
     if (i < 0 || j < 0 || i >= p->N || j >= p->N || i == j)
       return fail(ESP_ERR_INVALID_ARG, "exclusion pair " + std::to_string(k) + " = (" + std::to_string(i) + ", " +
                                            std::to_string(j) + ") is not two distinct atoms of the plan");
+    sorted_pairs[k] = std::make_pair((int32_t)std::min(i, j), (int32_t)std::max(i, j));
   }
+  // a pair listed twice, in either order, would be subtracted twice
+  std::sort(sorted_pairs.begin(), sorted_pairs.end());
+  for (size_t k = 1; k < sorted_pairs.size(); ++k)
+    if (sorted_pairs[k] == sorted_pairs[k - 1])
+      return fail(ESP_ERR_INVALID_ARG, "exclusion pair (" + std::to_string(sorted_pairs[k].first) + ", " +
+                                           std::to_string(sorted_pairs[k].second) + ") is listed more than once");
   DeviceGuard g(p->device);
   ESP_TRY(wait_stream(p, p->st));                // nothing in flight reads the old list
   if (n_pairs > p->excl_cap) {

@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(256) k_scale(
   typename Types<real>::cplx* sp = spec + S.spec0;
   const real* G = tabs + S.tab0;
   const real* W = G + S.gsize;
-  const real* H = W + (half + 1);                 // virial table (R27)
+  const real* H = W + (half + 1);                 // virial table: p'_k over the window factors
   double e = 0.0;
   double vir[6] = {0, 0, 0, 0, 0, 0};             // xx, yy, zz, xy, xz, yz
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -606,15 +606,20 @@ __global__ void __launch_bounds__(256) k_scale(
       const double a = 0.5 * wgt * (double)(__ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz))) *
                        ((double)v.x * v.x + (double)v.y * v.y);
       const double g = a * (double)__ldg(G + m), hm = a * (double)__ldg(H + m) / m;
-      // a Nyquist index stands for both aliases +-n_f/2: zero in the
-      // off-diagonal products (their average)
-      const int sx = kx == half ? 0 : kx, sy = kyi == half ? 0 : ky, sz = kzi == half ? 0 : kz;
+      // a Nyquist index stands for both aliases +-n_f/2. The exact
+      // -dE/d eps pairs the mode with the representative of -k, whose
+      // Nyquist components flip together: an off-diagonal product is zero
+      // when exactly one of its two components is Nyquist and k_a k_b (with
+      // both at -n_f/2) when both are
+      const bool even = (n & 1) == 0;
+      const bool nx = even && kx == half, ny = even && kyi == half, nz = even && kzi == half;
+      const int ax = nx ? -half : kx;               // ky, kz are already -n_f/2 there
       vir[0] += g + hm * kx * kx;
       vir[1] += g + hm * ky * ky;
       vir[2] += g + hm * kz * kz;
-      vir[3] += hm * sx * sy;
-      vir[4] += hm * sx * sz;
-      vir[5] += hm * sy * sz;
+      vir[3] += nx != ny ? 0.0 : hm * ax * ky;
+      vir[4] += nx != nz ? 0.0 : hm * ax * kz;
+      vir[5] += ny != nz ? 0.0 : hm * ky * kz;
     }
     v.x *= p;
     v.y *= p;

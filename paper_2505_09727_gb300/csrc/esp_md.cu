@@ -461,6 +461,8 @@ esp_status esp_md_destroy(esp_md_t md) {
     cudaStream_t st = espe::plan_stream(md->plan);
     if (st) cudaStreamSynchronize(st);
     md_release(md);
+    // the intramolecular exclusions belong to the MD state, not to the plan
+    esp_set_exclusions(md->plan, nullptr, 0);
   }
   delete md;
   return ESP_OK;

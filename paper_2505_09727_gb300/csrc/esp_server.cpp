@@ -105,8 +105,11 @@ struct Request {
   int64_t N = 0;
   double* buf = nullptr;     // pinned: xyz[3N] | forces[3N] | potential[N] | energy | err
   size_t cls = 0;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;      // recorded after the request's last copy
+  cudaEvent_t ev_start = nullptr;  // recorded before its first copy (device interval)
   PlanRec* plan = nullptr;
+  PlanRec* late_plan = nullptr;   // timed out with its work still on the device: the plan it holds
+  bool released = false;     // the client has taken the (timed-out) result: free once the work is done
   ReqState state = kPending;
   esp_status status = ESP_OK;
   std::string msg;
@@ -137,6 +140,7 @@ struct esp_server_s {
   uint64_t use_clock = 0;
   std::deque<Request*> pending;
   std::vector<Request*> running;
+  std::vector<Request*> late;          // timed out, work still in flight (their plans stay busy)
   std::unordered_map<int64_t, std::unique_ptr<Request>> tickets;
   int64_t next_ticket = 1;
   PinnedPool pinned;
@@ -144,6 +148,9 @@ struct esp_server_s {
   int64_t completed = 0, failed = 0, plans_created = 0, evictions = 0;
   double atoms_done = 0;
   std::vector<double> latencies;       // ms, completed requests in completion order
+  cudaEvent_t ev_ref = nullptr;        // time origin of the device intervals
+  std::vector<std::pair<double, double>> intervals;   // device [start, done] ms of completed requests
+  int64_t peak_inflight = 0;
   Clock::time_point t_first_submit{}, t_last_done{};
   bool any_submit = false;
 };
@@ -190,7 +197,9 @@ esp_status acquire_plan(esp_server_s* s, int sys, double tol, PlanRec** out, boo
   o.precision = s->opts.precision;
   o.kernel = s->opts.kernel;
   o.device = s->opts.device;
-  o.timeout_ms = s->opts.timeout_ms > 0 ? s->opts.timeout_ms : 60000.0;
+  // the plan's own synchronous waits (creation, charges) keep the default
+  // deadline; the server's deadline applies to each request's device work
+  o.timeout_ms = std::max(60000.0, s->opts.timeout_ms);
   esp_plan_params est;
   esp_status st = esp_plan_query(&S.box, S.N, tol, &o, &est);
   if (st != ESP_OK) return st;
@@ -233,6 +242,11 @@ void finish(esp_server_s* s, Request* r, esp_status st, const std::string& msg) 
     ++s->completed;
     s->atoms_done += (double)r->N;
     s->latencies.push_back(ms_since(r->t_submit, r->t_done));
+    float a = 0.f, b = 0.f;
+    if (s->ev_ref && r->ev_start && cudaEventElapsedTime(&a, s->ev_ref, r->ev_start) == cudaSuccess &&
+        cudaEventElapsedTime(&b, s->ev_ref, r->ev) == cudaSuccess)
+      s->intervals.emplace_back((double)a, (double)b);
+    cudaGetLastError();
     s->t_last_done = r->t_done;
   } else {
     ++s->failed;
@@ -256,9 +270,13 @@ void worker_loop(esp_server_s* s) {
           ++k;
           continue;
         }
-        // the plan stays busy: its stream still holds the work
+        // the plan stays busy while its stream still holds the work: the
+        // request moves to the late list, which frees the plan (and, once
+        // the client has taken the result, the buffers) when it completes
+        r->late_plan = r->plan;
         r->plan = nullptr;
         finish(s, r, ESP_ERR_TIMEOUT, "request exceeded the server deadline");
+        s->late.push_back(r);
       } else if (e != cudaSuccess) {
         finish(s, r, ESP_ERR_CUDA, std::string("request: ") + cudaGetErrorString(e));
       } else {
@@ -268,6 +286,26 @@ void worker_loop(esp_server_s* s) {
         else finish(s, r, ESP_OK, "");
       }
       s->running.erase(s->running.begin() + k);
+      progress = true;
+    }
+    // late requests whose work has now left the device give their plan back
+    for (size_t k = 0; k < s->late.size();) {
+      Request* r = s->late[k];
+      if (cudaEventQuery(r->ev) == cudaErrorNotReady) {
+        ++k;
+        continue;
+      }
+      cudaGetLastError();
+      r->late_plan->busy = false;
+      r->late_plan->last_use = ++s->use_clock;
+      r->late_plan = nullptr;
+      s->late.erase(s->late.begin() + k);
+      if (r->released) {
+        s->pinned.put(r->buf, r->cls);
+        cudaEventDestroy(r->ev);
+        if (r->ev_start) cudaEventDestroy(r->ev_start);
+        s->tickets.erase(r->ticket);
+      }
       progress = true;
     }
     if (progress) s->cv_done.notify_all();
@@ -300,6 +338,11 @@ void worker_loop(esp_server_s* s) {
         ++it;
         continue;
       }
+      if (r->ev_start && cudaEventRecord(r->ev_start, espe::plan_stream(pr->plan)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(r->ev_start);
+        r->ev_start = nullptr;
+      }
       st = espe::plan_enqueue_step(pr->plan, r->xyz(), r->forces(), r->potential(), r->energy(), r->err(), r->ev);
       if (st != ESP_OK) {
         finish(s, r, st, esp_last_error());
@@ -310,6 +353,7 @@ void worker_loop(esp_server_s* s) {
         r->state = kRunning;
         r->t_start = Clock::now();
         s->running.push_back(r);
+        s->peak_inflight = std::max<int64_t>(s->peak_inflight, (int64_t)s->running.size());
       }
       it = s->pending.erase(it);
       progress = true;
@@ -317,7 +361,7 @@ void worker_loop(esp_server_s* s) {
     if (progress) {
       last_progress = Clock::now();
     } else {
-      if (s->running.empty()) s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      if (s->running.empty()) s->cv_work.wait_for(lk, std::chrono::milliseconds(s->late.empty() ? 5 : 1));
       else {
         // requests in flight: poll their completion events with the lock
         // released (clients submit and wait meanwhile), without sleeping for
@@ -384,6 +428,20 @@ esp_status esp_server_create(const esp_server_opts* opts, esp_server_t* out) {
     budget = free_b / 10 * 8;
   }
   s->budget = budget;
+  {
+    // origin of the device intervals: recorded once, on the device's legacy
+    // stream, before any request exists
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(o.device);
+    if (cudaEventCreate(&s->ev_ref) != cudaSuccess || cudaEventRecord(s->ev_ref, 0) != cudaSuccess ||
+        cudaEventSynchronize(s->ev_ref) != cudaSuccess) {
+      cudaGetLastError();
+      if (s->ev_ref) cudaEventDestroy(s->ev_ref);
+      s->ev_ref = nullptr;
+    }
+    cudaSetDevice(prev);
+  }
   s->worker = std::thread(worker_loop, s);
   *out = s;
   return ESP_OK;
@@ -418,9 +476,19 @@ esp_status esp_server_submit(esp_server_t s, int id, double tolerance, const dou
   r->buf = static_cast<double*>(s->pinned.get(request_bytes(N), &r->cls));
   if (!r->buf) return sfail(ESP_ERR_OOM, "pinned host allocation failed");
   std::memcpy(r->xyz(), xyz, (size_t)N * 3 * sizeof(double));
-  if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
-    s->pinned.put(r->buf, r->cls);
-    return sfail(ESP_ERR_CUDA, "event creation failed");
+  {
+    // timing events: their device times give the request's device interval
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->opts.device);
+    const bool ok = cudaEventCreate(&r->ev) == cudaSuccess && cudaEventCreate(&r->ev_start) == cudaSuccess;
+    cudaSetDevice(prev);
+    if (!ok) {
+      cudaGetLastError();
+      if (r->ev) cudaEventDestroy(r->ev);
+      s->pinned.put(r->buf, r->cls);
+      return sfail(ESP_ERR_CUDA, "event creation failed");
+    }
   }
   r->t_submit = Clock::now();
   {
@@ -468,10 +536,14 @@ esp_status esp_server_wait(esp_server_t s, int64_t ticket, double timeout_ms, do
     if (potential) std::memcpy(potential, r->potential(), (size_t)r->N * sizeof(double));
     if (latency_ms) *latency_ms = ms_since(r->t_submit, r->t_done);
   }
-  // a timed-out request keeps its buffers: its copies may still land there
-  if (st != ESP_ERR_TIMEOUT) {
+  // a timed-out request whose copies may still land in its buffers keeps
+  // them until the worker sees its work finish; the ticket is released
+  if (r->late_plan) {
+    r->released = true;
+  } else {
     s->pinned.put(r->buf, r->cls);
     cudaEventDestroy(r->ev);
+    if (r->ev_start) cudaEventDestroy(r->ev_start);
     s->tickets.erase(it);
   }
   if (st != ESP_OK) return sfail(st, msg);
@@ -506,6 +578,24 @@ esp_status esp_server_stats(esp_server_t s, esp_server_counters* out) {
     out->latency_max_ms = v.back();
   }
   if (s->completed > 0) out->wall_ms = ms_since(s->t_first_submit, s->t_last_done);
+  out->peak_inflight = s->peak_inflight;
+  // sweep over the device intervals: +1 at a start, -1 at an end (ends
+  // first at equal times, so touching intervals do not count as overlap)
+  std::vector<std::pair<double, int>> ev;
+  ev.reserve(2 * s->intervals.size());
+  for (const auto& iv : s->intervals) {
+    ev.emplace_back(iv.first, +1);
+    ev.emplace_back(iv.second, -1);
+  }
+  std::sort(ev.begin(), ev.end());
+  int64_t level = 0;
+  double last = 0.0;
+  for (const auto& e : ev) {
+    if (level >= 2) out->overlap_ms += e.first - last;
+    level += e.second;
+    last = e.first;
+    out->peak_concurrent = std::max(out->peak_concurrent, level);
+  }
   return ESP_OK;
 }
 
@@ -515,6 +605,8 @@ esp_status esp_server_reset_stats(esp_server_t s) {
   s->completed = s->failed = 0;
   s->atoms_done = 0;
   s->latencies.clear();
+  s->intervals.clear();
+  s->peak_inflight = 0;
   s->any_submit = false;
   return ESP_OK;
 }
@@ -531,11 +623,14 @@ esp_status esp_server_destroy(esp_server_t s) {
   cudaGetDevice(&prev);
   cudaSetDevice(s->opts.device);
   for (Request* r : s->running) cudaEventSynchronize(r->ev);
+  for (Request* r : s->late) cudaEventSynchronize(r->ev);
   for (auto& kv : s->plans) esp_destroy(kv.second->plan);
   for (auto& kv : s->tickets) {
     s->pinned.put(kv.second->buf, kv.second->cls);
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    if (kv.second->ev_start) cudaEventDestroy(kv.second->ev_start);
   }
+  if (s->ev_ref) cudaEventDestroy(s->ev_ref);
   cudaSetDevice(prev);
   delete s;
   return ESP_OK;

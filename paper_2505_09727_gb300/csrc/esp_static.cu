@@ -134,8 +134,30 @@ esp_status run_local(const espe::HostPlan& hp, unsigned char* scratch, const dou
                   d_partials, st));
   SCU(espk::launch_energy(d_desc, 1, d_fourier, 1, d_partials, n_chunks, d_chunk_first, d_consts,
                           d_eout, energy, st));
+  // the kernels' error flag: a non-finite position (zeroed by the ingest) or
+  // a failed bounds check leaves the outputs wrong, so the call waits for its
+  // kernels and reports it
+  int flag = 0;
+  SCU(cudaMemcpyAsync(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SCU(cudaStreamSynchronize(st));
 #undef SCU
+  if (flag & 1) return sfail(ESP_ERR_NONFINITE, "a position is NaN or infinite");
+  if (flag) return sfail(ESP_ERR_INTERNAL, "a kernel bounds check failed (flag " + std::to_string(flag) + ")");
   return ESP_OK;
+}
+
+// Whether p is memory the GPU `dev` can address as a device pointer (device
+// memory of that GPU, or managed memory); host and unregistered pointers are
+// refused before any launch.
+bool device_pointer(const void* p, int dev) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Bytes of the static array one call needs.
@@ -189,6 +211,11 @@ extern "C" esp_status esp_local_part_static(const esp_box* box, int64_t N, doubl
   }
   unsigned char* scratch = nullptr;
   s = scratch_address(o.device, &scratch);
+  if (s == ESP_OK && !(device_pointer(xyz, o.device) && device_pointer(q, o.device) &&
+                       device_pointer(energy, o.device) && device_pointer(forces, o.device) &&
+                       device_pointer(potential, o.device)))
+    s = sfail(ESP_ERR_INVALID_ARG, "xyz, q and every non-NULL output must be device (or managed) memory of "
+                                   "opts->device");
   cudaStream_t st = (cudaStream_t)o.stream;
   if (s == ESP_OK && N == 0) {
     if (energy && cudaMemsetAsync(energy, 0, sizeof(double), st) != cudaSuccess)

@@ -98,6 +98,7 @@ class esp_server_counters(ctypes.Structure):
         ("plans_created", ctypes.c_int64), ("evictions", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
         ("memory_budget", ctypes.c_size_t), ("latency_p50_ms", ctypes.c_double),
         ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
+        ("peak_inflight", ctypes.c_int64), ("peak_concurrent", ctypes.c_int64), ("overlap_ms", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -465,15 +466,35 @@ def esp_local_part_static(L: float, N: int, tolerance: float, xyz, q, energy=Non
                           potential=None, opts: esp_plan_opts | None = None, **kw):
     """Local part, self term and background without device allocation.
 
-    xyz, q and the outputs are FP64 device buffers (torch CUDA tensors or raw
-    device pointers); the work is enqueued on opts.stream.
+    xyz, q and the outputs are FP64 device buffers (torch CUDA tensors of
+    3N, N, 1, 3N and N values, or raw device addresses); the work runs on
+    opts.stream and the call returns once it has finished.
     """
     if opts is None:
         opts = make_opts(**kw)
     box = esp_box((ctypes.c_double * 3)(L, L, L))
+    N = int(N)
+
+    def dev_ptr(name, x, count, required):
+        # raw device addresses (int) pass through to the library's own check
+        if x is None:
+            if required and N > 0:
+                raise ValueError(f"{name} is required")
+            return None
+        if isinstance(x, int):
+            return ctypes.c_void_p(x)
+        if not (hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)):
+            raise TypeError(f"{name} must be a CUDA tensor (device memory), got {type(x).__name__}")
+        if str(x.dtype) != "torch.float64":
+            raise TypeError(f"{name} must be float64, got {x.dtype}")
+        if x.numel() != count:
+            raise ValueError(f"{name} must hold {count} values, got {x.numel()}")
+        return _ptr(x)[0]
+
     _check(load_library().esp_local_part_static(
-        ctypes.byref(box), int(N), float(tolerance), ctypes.byref(opts), _ptr(xyz)[0], _ptr(q)[0],
-        _ptr(energy)[0], _ptr(forces)[0], _ptr(potential)[0]))
+        ctypes.byref(box), N, float(tolerance), ctypes.byref(opts), dev_ptr("xyz", xyz, 3 * N, True),
+        dev_ptr("q", q, N, True), dev_ptr("energy", energy, 1, False), dev_ptr("forces", forces, 3 * N, False),
+        dev_ptr("potential", potential, N, False)))
 
 
 def esp_autotune(L: float, tolerance: float, xyz, q, reps: int = 5, opts: esp_plan_opts | None = None,

@@ -125,3 +125,66 @@ def test_bad_requests_are_rejected(esp):
         e, f, u, _ = srv.wait(srv.submit(sid, 1e-4, s.pos))                      # still serves
         e0, f0, u0 = alone(esp, s, s.pos, 1e-4, 1.0)
         assert rel_rms(f, f0) <= FP32_PARITY
+
+
+def test_requests_submitted_while_others_run_overlap_on_the_device(esp):
+    """Continuous batching: a second thread submits while the first thread's
+    requests are on the device. The server's device intervals (events on each
+    request's stream before its first copy and after its last) must overlap,
+    and every result must equal the same request run alone."""
+    import threading
+    systems = inputs.electrolyte_batch([40000, 60000, 30000, 50000], seed=340)
+    reqs = requests_of(systems, 16, seed=341)
+    with esp.Server(1.0, max_inflight=8) as srv:
+        ids = [srv.add_system(s.L, s.q) for s in systems]
+        for i, eps, pos in reqs[:4]:                       # plans created before the timed mix
+            srv.wait(srv.submit(ids[i], eps, pos))
+        esp.esp_server_reset_stats(srv.handle)
+        first, second = reqs[:8], reqs[8:]
+        tickets_b = []
+        started = threading.Event()
+
+        def late_client():
+            started.wait()
+            for i, eps, pos in second:
+                tickets_b.append(srv.submit(ids[i], eps, pos))
+
+        th = threading.Thread(target=late_client)
+        th.start()
+        tickets_a = []
+        for k, (i, eps, pos) in enumerate(first):
+            tickets_a.append(srv.submit(ids[i], eps, pos))
+            if k == 1:
+                started.set()                              # the other client joins mid-stream
+        th.join()
+        results = [srv.wait(t) for t in tickets_a] + [srv.wait(t) for t in tickets_b]
+        st = srv.stats()
+    check(esp, systems, first + second, results, 1.0)
+    assert st["completed"] == 16 and st["failed"] == 0
+    assert st["peak_inflight"] >= 2
+    assert st["peak_concurrent"] >= 2, st
+    assert st["overlap_ms"] > 0.0
+
+
+def test_timed_out_request_releases_its_plan(esp):
+    """A request that exceeds the server deadline fails with ESP_ERR_TIMEOUT;
+    once its device work finishes its plan is free again, so the next request
+    for the same system is admitted (and, under the same short deadline,
+    times out by itself) instead of waiting forever behind a busy plan."""
+    import time
+    s = inputs.electrolyte(400_000, seed=350)
+    with esp.Server(1.0, timeout_ms=0.05, max_inflight=2) as srv:
+        sid = srv.add_system(s.L, s.q)
+        for _ in range(2):
+            with pytest.raises(esp.EspError) as exc:
+                srv.wait(srv.submit(sid, 1e-5, s.pos), timeout_ms=30000.0)
+            assert exc.value.status == 8
+            assert "server deadline" in str(exc.value)
+            for _ in range(2000):                          # the late work drains
+                st = srv.stats()
+                if st["running"] == 0 and st["pending"] == 0:
+                    break
+                time.sleep(0.005)
+        st = srv.stats()
+    assert st["failed"] == 2
+    assert st["plans_resident"] == 1

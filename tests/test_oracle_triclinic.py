@@ -162,17 +162,18 @@ def test_triclinic_virial_is_the_deformation_derivative():
 
 def test_cube_virial_readings_against_the_deformation_derivative():
     """The cube's full virial tensor pinned by shearing it (the triclinic
-    energy of the deformed cell): the "alias" Nyquist reading is the exact
-    derivative; the "component" reading (R27, the CUDA path's) differs only
-    in the off-diagonal terms of modes with two Nyquist components."""
+    energy of the deformed cell): the "alias" Nyquist reading (the oracle's
+    default, and the CUDA path's) is the exact derivative; the "component"
+    reading (each Nyquist component averaged on its own) differs only in the
+    off-diagonal terms of modes with two Nyquist components."""
     import dataclasses
     s = inputs.uniform_charges(80, 3.0, 5)
     p = oesp.default_params(1e-4, s.L, 1.1).resolved()
     H = s.L * np.eye(3)
     fd = _deformation_fd(lambda x, Hd: tr.esp(x, s.q, Hd, p.split(), p.si_window(), p.n_f, p.r_c)["energy"],
                          H, s.pos)
-    W_alias = oesp.esp(s.pos, s.q, s.L, dataclasses.replace(p, virial_nyquist="alias"))["virial"]
-    W_comp = oesp.esp(s.pos, s.q, s.L, p)["virial"]
+    W_alias = oesp.esp(s.pos, s.q, s.L, p)["virial"]
+    W_comp = oesp.esp(s.pos, s.q, s.L, dataclasses.replace(p, virial_nyquist="component"))["virial"]
     scale = np.max(np.abs(fd))
     assert np.max(np.abs(W_alias - fd)) <= 1e-7 * scale
     assert np.array_equal(np.diag(W_alias), np.diag(W_comp))

@@ -116,7 +116,8 @@ def test_triclinic_cell_with_exclusions(esp):
 def test_exclusion_arguments(esp):
     s = inputs.spce_water(50, seed=24)                       # L = 1.14 nm
     with esp.Plan(s.L, s.n, 1e-4, r_c=0.5) as p:
-        for bad in ([[0, s.n]], [[-1, 2]], [[3, 3]]):
+        # out of range, negative, self pair, and a pair listed twice (either order)
+        for bad in ([[0, s.n]], [[-1, 2]], [[3, 3]], [[1, 2], [5, 6], [2, 1]], [[4, 5], [4, 5]]):
             with pytest.raises(esp.EspError) as exc:
                 esp.esp_set_exclusions(p.handle, np.array(bad))
             assert exc.value.status == 1

@@ -88,3 +88,23 @@ def test_md_arguments(esp):
         with pytest.raises(esp.EspError) as exc:
             esp.MD(p.handle, c.pos, np.zeros_like(c.pos), lj_cutoff=0.4)
         assert exc.value.status == 10
+
+
+def test_destroy_clears_the_plan_exclusions(esp):
+    """esp_md_create sets the intramolecular exclusions on the plan; after
+    esp_md_destroy a compute on the same plan counts every pair again, as a
+    fresh plan does."""
+    s = inputs.spce_water(200, seed=35)
+    v = np.zeros_like(s.pos)
+    with esp.Plan(s.L, s.n, 1e-5, r_c=0.8, precision=esp.ESP_FP64) as p, \
+            esp.Plan(s.L, s.n, 1e-5, r_c=0.8, precision=esp.ESP_FP64) as fresh:
+        for q in (p, fresh):
+            q.set_charges(s.q)
+        with esp.MD(p.handle, s.pos, v) as sim:
+            sim.run(1)
+        p.set_positions(s.pos)
+        fresh.set_positions(s.pos)
+        e, f, u = p.compute()
+        e0, f0, u0 = fresh.compute()
+    assert abs(e - e0) <= 1e-12 * abs(e0)
+    assert np.max(np.abs(f - f0)) <= 1e-12 * np.max(np.abs(f0))

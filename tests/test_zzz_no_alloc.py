@@ -11,8 +11,8 @@ Two comparisons with the plan-based path on the same inputs:
   * Gaussian split with alpha = 1e-12: the spectral part vanishes
     identically (exp(-kappa^2/(4 alpha)) underflows to 0 for every k != 0), so
     the plan-based energy, forces and potential are the local part alone.
-This file is collected after the others but the triclinic tests (test_zz_*),
-so a run that stops at the first failure has already run the cubic paths.
+This file is collected after every other test file, so a run that stops at
+the first failure has already run the rest.
 """
 import numpy as np
 import pytest
@@ -98,3 +98,38 @@ def test_rejects_systems_beyond_the_static_size(lib):
         static_call(lib, s, 1e-4, r_c=1.0)
     assert exc.value.status == 10
     assert "static array" in lib.esp_last_error()
+
+
+def test_nonfinite_position_is_reported(lib):
+    """A NaN position is zeroed by the ingest and flagged; the call waits for
+    its kernels and returns ESP_ERR_NONFINITE instead of a wrong result."""
+    s = inputs.spce_water(500, seed=34)
+    s.pos[17, 1] = np.nan
+    with pytest.raises(lib.EspError) as exc:
+        static_call(lib, s, 1e-4, r_c=0.7)
+    assert exc.value.status == 4          # ESP_ERR_NONFINITE
+    # the shared array is usable again on the next call
+    s.pos[17, 1] = 0.5
+    e, f, u = static_call(lib, s, 1e-4, r_c=0.7)
+    assert np.isfinite(e) and np.all(np.isfinite(f)) and np.all(np.isfinite(u))
+
+
+def test_rejects_buffers_that_are_not_device_float64(lib):
+    """Host memory, a wrong dtype or a wrong length is an argument error,
+    raised before anything is launched."""
+    import torch
+    s = inputs.spce_water(200, seed=35)
+    dev = torch.device("cuda:0")
+    x = torch.tensor(s.pos, device=dev)
+    q = torch.tensor(s.q, device=dev)
+    with pytest.raises(TypeError):
+        lib.esp_local_part_static(s.L, s.n, 1e-4, torch.tensor(s.pos), q, r_c=0.7)
+    with pytest.raises(TypeError):
+        lib.esp_local_part_static(s.L, s.n, 1e-4, x.float(), q, r_c=0.7)
+    with pytest.raises(ValueError):
+        lib.esp_local_part_static(s.L, s.n, 1e-4, x[:-1], q, r_c=0.7)
+    # a raw host address reaches the C entry, which refuses it
+    host = np.ascontiguousarray(s.pos)
+    with pytest.raises(lib.EspError) as exc:
+        lib.esp_local_part_static(s.L, s.n, 1e-4, host.ctypes.data, q, r_c=0.7)
+    assert exc.value.status == 1          # ESP_ERR_INVALID_ARG
