@@ -14,6 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libesp_gb300.so")
+# throughput microbenchmarks (roofline denominators), kept out of the solver library
+PEAKS_LIB = os.path.join(OUT, "libesp_peaks.so")
+PEAKS_SOURCE = "esp_peaks.cu"
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -70,6 +73,17 @@ def build(verbose: bool = False, force: bool = False) -> str:
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("compilation failed:\n" + "\n".join(failed))
+    peaks_src = os.path.join(CSRC, PEAKS_SOURCE)
+    peaks_job = None
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(peaks_src) > os.path.getmtime(PEAKS_LIB):
+        cmd = [nvcc] + NVCC_FLAGS + ["-shared", peaks_src, "-o", PEAKS_LIB]
+        peaks_job = (cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT))
+    if peaks_job:
+        out, _ = peaks_job[1].communicate()
+        if verbose or peaks_job[1].returncode:
+            sys.stdout.write(out.decode(errors="replace"))
+        if peaks_job[1].returncode:
+            raise RuntimeError("compilation failed:\n" + " ".join(peaks_job[0]))
     if jobs or not os.path.exists(LIB):
         libdir = os.path.join(home, "lib64")
         cmd = [nvcc, ARCH, "-shared", "-o", LIB] + objs + [

@@ -40,7 +40,7 @@ static cudaError_t launch_near_cluster(const SysDesc* sys, long long n_cols, con
   const long long need = (cmap_cap + WARPS - 1) / WARPS;
   const int grid = (int)std::min<long long>(nb, std::max<long long>(1, need));
   kern<<<grid, WARPS * 32, 0, st>>>(sys, cmap, catoms, cstart + n_cols, (const float4*)rel, start,
-                                    (float4*)nearres, nc, err, vloc);
+                                    (float4*)nearres, interleave(nc), err, vloc);
   return cudaGetLastError();
 }
 

@@ -52,12 +52,27 @@ __device__ __forceinline__ float rsqrt_approx(float r2) {
   return r;
 }
 
+// The two local-part polynomials interleaved, (H_k, K_k) for k = 0 ... : one
+// packed multiply-add per Horner step advances both.
+struct NearCoefHK {
+  float2 hk[Deg<float>::nr];
+};
+
+__host__ inline NearCoefHK interleave(const NearCoef<float>& nc) {
+  NearCoefHK o;
+  for (int k = 0; k < Deg<float>::nr; ++k) o.hk[k] = make_float2(nc.h[k], nc.k[k]);
+  return o;
+}
+
 // Per-warp shared state of the cluster kernel.
 template <bool HALF>
 struct ClusterSmem {
   float4 queue[kClusterQueue];          // queued candidates (cluster frame, charge)
   int qidx[HALF ? kClusterQueue : 1];   // their atom indices (HALF)
   float4 idata[kClusterAtoms];          // the cluster's atoms
+  // the same atoms in pairs (2m, 2m + 1) for the packed pair arithmetic:
+  // ipair[2m] = (x, x', y, y'), ipair[2m + 1] = (z, z', q, q')
+  float4 ipair[kClusterAtoms];
   float4 seg_off[kSegCap];              // image offsets of each listed range
   uint32_t seg_pos[kSegCap];            // first atom of each listed range
   int seg_pre[kSegCap + 1];             // exclusive prefix counts (+ total)
@@ -84,7 +99,7 @@ template <int NC, bool HALF, bool VIR, int WARPS, bool TRI = false>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     const SysDesc* __restrict__ sys, const int2* __restrict__ cmap, const int2* __restrict__ catoms,
     const uint32_t* __restrict__ n_clusters, const float4* __restrict__ rel,
-    const uint32_t* __restrict__ start, float4* __restrict__ nearres, const NearCoef<float> nc,
+    const uint32_t* __restrict__ start, float4* __restrict__ nearres, const NearCoefHK nc,
     int* __restrict__ err, double* __restrict__ vloc = nullptr) {
   static_assert(HALF || !VIR, "the virial is formed in the half form");
   static_assert(!(TRI && VIR), "no virial on a triclinic cell");
@@ -103,18 +118,20 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
   const long long per_block = (total_clusters + gridDim.x - 1) / gridDim.x;
   const long long g_begin = (long long)blockIdx.x * per_block;
   const long long g_end = min(total_clusters, g_begin + per_block);
-  float vir[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};    // VIR: this lane's pair sums
+  float2 vir[6];                                    // VIR: this lane's pair sums (two partial sums each)
+#pragma unroll
+  for (int c = 0; c < 6; ++c) vir[c] = make_float2(0.f, 0.f);
   int vsys = -1;                                    // VIR: their system
   auto flush_virial = [&]() {
     if constexpr (VIR) {
       if (vsys >= 0) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-          float t = vir[c];
+          float t = vir[c].x + vir[c].y;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
           if (lane == 0) atomicAdd(vloc + 6 * vsys + c, (double)t * (1.0 / kFourPi));
-          vir[c] = 0.f;
+          vir[c] = make_float2(0.f, 0.f);
         }
       }
     }
@@ -187,13 +204,23 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     }
     // missing atoms (m < 8) sit far away with zero charge: every pair with
     // them is masked off, so the eight pair evaluations need no branch
-    if (lane < kClusterAtoms)
-      W.idata[lane] = mine ? ri : make_float4(far_away, far_away, far_away, 0.f);
+    if (lane < kClusterAtoms) {
+      const float4 a = mine ? ri : make_float4(far_away, far_away, far_away, 0.f);
+      W.idata[lane] = a;
+      float* pa = reinterpret_cast<float*>(&W.ipair[2 * (lane >> 1)]);
+      const int o = lane & 1;
+      pa[o] = a.x;
+      pa[2 + o] = a.y;
+      pa[4 + o] = a.z;
+      pa[6 + o] = a.w;
+    }
     __syncwarp();
 
-    float pu[kClusterAtoms], px[kClusterAtoms], py[kClusterAtoms], pz[kClusterAtoms];
+    // per-lane sums for the cluster atoms in pairs (2m, 2m + 1): potential
+    // and force components, packed two-wide
+    float2 pu[kClusterAtoms / 2], px[kClusterAtoms / 2], py[kClusterAtoms / 2], pz[kClusterAtoms / 2];
 #pragma unroll
-    for (int t = 0; t < kClusterAtoms; ++t) pu[t] = px[t] = py[t] = pz[t] = 0.f;
+    for (int m = 0; m < kClusterAtoms / 2; ++m) pu[m] = px[m] = py[m] = pz[m] = make_float2(0.f, 0.f);
 
     const float rc2 = S.rc2f, inv_rc = S.inv_rcf;
     const float inv_rc2x2 = S.inv_rc2x2f, inv_rc3 = S.inv_rc3f;
@@ -204,56 +231,76 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     int qn = 0;                                   // queued candidates
     int nseg = 0, total = 0;                      // listed ranges, their candidates
 
-    // pair work on queued candidate `jd` (atom index jx or -1)
+    // pair work on queued candidate `jd` (atom index jx or -1). The eight
+    // cluster atoms are taken two at a time with the packed f32x2 multiply-
+    // adds, so one instruction does the arithmetic of two pairs; every
+    // packed operation rounds like its scalar form, in the same order.
+    const float2 inv_rc2x2_2 = make_float2(inv_rc2x2, inv_rc2x2);
+    const float2 neg_inv_rc_2 = make_float2(-inv_rc, -inv_rc);
+    const float2 inv_rc3_2 = make_float2(inv_rc3, inv_rc3);
+    const float2 minus_one_2 = make_float2(-1.f, -1.f);
     auto evaluate = [&](const float4 jd, int jx) {
-      float uj = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f;
+      const float2 njx = make_float2(-jd.x, -jd.x), njy = make_float2(-jd.y, -jd.y),
+                   njz = make_float2(-jd.z, -jd.z);
+      float2 uj = make_float2(0.f, 0.f), fjx = uj, fjy = uj, fjz = uj;
 #pragma unroll
-      for (int t = 0; t < kClusterAtoms; ++t) {
-        const float4 ci = W.idata[t];
-        const float dx = ci.x - jd.x, dy = ci.y - jd.y, dz = ci.z - jd.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      for (int m = 0; m < kClusterAtoms / 2; ++m) {
+        const float4 A = W.ipair[2 * m], B = W.ipair[2 * m + 1];
+        const float2 dx = __fadd2_rn(make_float2(A.x, A.y), njx);
+        const float2 dy = __fadd2_rn(make_float2(A.z, A.w), njy);
+        const float2 dz = __fadd2_rn(make_float2(B.x, B.y), njz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
         // HALF never queues a cluster atom against itself, so 0 < r2 holds
         // for distinct positions; the full form meets the cluster's own atoms
-        const bool in = HALF ? r2 < rc2 : (r2 < rc2 && r2 > 0.f);
-        const float r2m = in ? r2 : rc2;
-        const float qj = in ? jd.w : 0.f;
+        const bool in0 = HALF ? r2.x < rc2 : (r2.x < rc2 && r2.x > 0.f);
+        const bool in1 = HALF ? r2.y < rc2 : (r2.y < rc2 && r2.y > 0.f);
         // masked pairs (outside r_c, or the far-away padding) are evaluated
         // at r = r_c with zero charge: every lane runs the same instructions
-        const float rinv = rsqrt_approx(r2m);
-        const float y = fmaf(r2m, inv_rc2x2, -1.f);
-        const float h = horner_f<NC>(nc.h, y);
-        const float kk = horner_f<NC>(nc.k, y);
-        const float t1 = fmaf(-h, inv_rc, rinv);
-        const float t2 = fmaf(kk, inv_rc3, rinv * rinv * rinv);
-        pu[t] = fmaf(qj, t1, pu[t]);
-        const float fs = qj * t2;
-        px[t] = fmaf(fs, dx, px[t]);
-        py[t] = fmaf(fs, dy, py[t]);
-        pz[t] = fmaf(fs, dz, pz[t]);
+        const float2 r2m = make_float2(in0 ? r2.x : rc2, in1 ? r2.y : rc2);
+        const float2 qj = make_float2(in0 ? jd.w : 0.f, in1 ? jd.w : 0.f);
+        const float2 rinv = make_float2(rsqrt_approx(r2m.x), rsqrt_approx(r2m.y));
+        const float2 y = __ffma2_rn(r2m, inv_rc2x2_2, minus_one_2);
+        // Horner for (H, K) together, one chain per atom
+        const float2 y0 = make_float2(y.x, y.x), y1 = make_float2(y.y, y.y);
+        float2 hk0 = nc.hk[NC - 1], hk1 = nc.hk[NC - 1];
+#pragma unroll
+        for (int k = NC - 2; k >= 0; --k) {
+          hk0 = __ffma2_rn(hk0, y0, nc.hk[k]);
+          hk1 = __ffma2_rn(hk1, y1, nc.hk[k]);
+        }
+        const float2 h = make_float2(hk0.x, hk1.x), kk = make_float2(hk0.y, hk1.y);
+        const float2 t1 = __ffma2_rn(h, neg_inv_rc_2, rinv);
+        const float2 t2 = __ffma2_rn(kk, inv_rc3_2, __fmul2_rn(__fmul2_rn(rinv, rinv), rinv));
+        pu[m] = __ffma2_rn(qj, t1, pu[m]);
+        const float2 fs = __fmul2_rn(qj, t2);
+        px[m] = __ffma2_rn(fs, dx, px[m]);
+        py[m] = __ffma2_rn(fs, dy, py[m]);
+        pz[m] = __ffma2_rn(fs, dz, pz[m]);
         if constexpr (HALF) {
-          const float qi = in ? ci.w : 0.f;
-          uj = fmaf(qi, t1, uj);
-          const float fsj = qi * t2;
-          fjx = fmaf(fsj, dx, fjx);
-          fjy = fmaf(fsj, dy, fjy);
-          fjz = fmaf(fsj, dz, fjz);
+          const float2 qi = make_float2(in0 ? B.z : 0.f, in1 ? B.w : 0.f);
+          uj = __ffma2_rn(qi, t1, uj);
+          const float2 fsj = __fmul2_rn(qi, t2);
+          fjx = __ffma2_rn(fsj, dx, fjx);
+          fjy = __ffma2_rn(fsj, dy, fjy);
+          fjz = __ffma2_rn(fsj, dz, fjz);
           if constexpr (VIR) {
             // pair virial q_i q_j t2 d d^T (the 1/(4 pi) at the flush)
-            const float v = fsj * jd.w;
-            const float vx = v * dx, vy = v * dy, vz = v * dz;
-            vir[0] = fmaf(vx, dx, vir[0]);
-            vir[1] = fmaf(vy, dy, vir[1]);
-            vir[2] = fmaf(vz, dz, vir[2]);
-            vir[3] = fmaf(vx, dy, vir[3]);
-            vir[4] = fmaf(vx, dz, vir[4]);
-            vir[5] = fmaf(vy, dz, vir[5]);
+            const float2 v = __fmul2_rn(fsj, make_float2(jd.w, jd.w));
+            const float2 vx = __fmul2_rn(v, dx), vy = __fmul2_rn(v, dy), vz = __fmul2_rn(v, dz);
+            vir[0] = __ffma2_rn(vx, dx, vir[0]);
+            vir[1] = __ffma2_rn(vy, dy, vir[1]);
+            vir[2] = __ffma2_rn(vz, dz, vir[2]);
+            vir[3] = __ffma2_rn(vx, dy, vir[3]);
+            vir[4] = __ffma2_rn(vx, dz, vir[4]);
+            vir[5] = __ffma2_rn(vy, dz, vir[5]);
           }
         }
       }
       if constexpr (HALF) {
         if (jx >= 0) {
           const float qk = -jd.w * k4;
-          atomicAdd(nearres + jx, make_float4(uj * k4, qk * fjx, qk * fjy, qk * fjz));
+          atomicAdd(nearres + jx, make_float4((uj.x + uj.y) * k4, qk * (fjx.x + fjx.y), qk * (fjy.x + fjy.y),
+                                              qk * (fjz.x + fjz.y)));
         }
       }
     };
@@ -465,11 +512,15 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     __syncwarp();
     float v[4 * kClusterAtoms];
 #pragma unroll
-    for (int t = 0; t < kClusterAtoms; ++t) {
-      v[t] = pu[t];
-      v[kClusterAtoms + t] = px[t];
-      v[2 * kClusterAtoms + t] = py[t];
-      v[3 * kClusterAtoms + t] = pz[t];
+    for (int m = 0; m < kClusterAtoms / 2; ++m) {
+      v[2 * m] = pu[m].x;
+      v[2 * m + 1] = pu[m].y;
+      v[kClusterAtoms + 2 * m] = px[m].x;
+      v[kClusterAtoms + 2 * m + 1] = px[m].y;
+      v[2 * kClusterAtoms + 2 * m] = py[m].x;
+      v[2 * kClusterAtoms + 2 * m + 1] = py[m].y;
+      v[3 * kClusterAtoms + 2 * m] = pz[m].x;
+      v[3 * kClusterAtoms + 2 * m + 1] = pz[m].y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -498,8 +549,10 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
         const float qe = in ? rb.w : 0.f;
         const float rinv = rsqrt_approx(r2m);
         const float y = fmaf(r2m, inv_rc2x2, -1.f);
-        const float h = horner_f<NC>(nc.h, y);
-        const float kk = horner_f<NC>(nc.k, y);
+        float2 hk = nc.hk[NC - 1];
+#pragma unroll
+        for (int k = NC - 2; k >= 0; --k) hk = __ffma2_rn(hk, make_float2(y, y), nc.hk[k]);
+        const float h = hk.x, kk = hk.y;
         su = fmaf(qe, fmaf(-h, inv_rc, rinv), su);
         const float fs = qe * fmaf(kk, inv_rc3, rinv * rinv * rinv);
         sx = fmaf(fs, dx, sx);
@@ -509,12 +562,12 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
           // ordered pairs: each unordered pair twice, half weight
           const float v = 0.5f * ra.w * fs;
           const float vx = v * dx, vy = v * dy, vz = v * dz;
-          vir[0] = fmaf(vx, dx, vir[0]);
-          vir[1] = fmaf(vy, dy, vir[1]);
-          vir[2] = fmaf(vz, dz, vir[2]);
-          vir[3] = fmaf(vx, dy, vir[3]);
-          vir[4] = fmaf(vx, dz, vir[4]);
-          vir[5] = fmaf(vy, dz, vir[5]);
+          vir[0].x = fmaf(vx, dx, vir[0].x);
+          vir[1].x = fmaf(vy, dy, vir[1].x);
+          vir[2].x = fmaf(vz, dz, vir[2].x);
+          vir[3].x = fmaf(vx, dy, vir[3].x);
+          vir[4].x = fmaf(vx, dz, vir[4].x);
+          vir[5].x = fmaf(vy, dz, vir[5].x);
         }
       }
 #pragma unroll

@@ -100,7 +100,7 @@ def test_destroy_clears_the_plan_exclusions(esp):
             esp.Plan(s.L, s.n, 1e-5, r_c=0.8, precision=esp.ESP_FP64) as fresh:
         for q in (p, fresh):
             q.set_charges(s.q)
-        with esp.MD(p.handle, s.pos, v) as sim:
+        with esp.MD(p.handle, s.pos, v, lj_cutoff=0.6) as sim:      # L = 1.82 nm
             sim.run(1)
         p.set_positions(s.pos)
         fresh.set_positions(s.pos)
