@@ -515,31 +515,48 @@ def triclinic(args, local, stream, flush):
 
 MD_LOOP = dict(workload="spce_water_1e5_molecules_md", molecules=100_000, atoms=300_000, density_per_nm3=33.4,
                r_c_nm=1.0, lj_cutoff_nm=1.0, tolerance=1e-4, dt_ps=0.0005, temperature_K=300.0, seed=2505)
+MD_DRIFT = dict(MD_LOOP, workload="spce_water_1e4_molecules_md_drift", molecules=10_000, atoms=30_000, steps=20_000)
 
 
 def md_loop(args, local, stream):
-    """ns/day and energy change of the MD loop (esp_md_*): 1e5 flexible
-    SPC/E-shaped water molecules, FP32 solve, velocity Verlet."""
+    """ns/day of the MD loop (esp_md_*: 1e5 flexible SPC/E-shaped water
+    molecules, FP32 solve, velocity Verlet, every step one CUDA graph), and
+    the energy drift over 2e4 steps (10 ps) of a 1e4-molecule box: the slope
+    of a least-squares line through the total energy, per atom."""
     import torch
     from paper_2505_09727_gb300 import esp, inputs
-    s = inputs.spce_water(MD_LOOP["molecules"], seed=MD_LOOP["seed"])
-    v = inputs.water_velocities(MD_LOOP["molecules"], MD_LOOP["temperature_K"], seed=MD_LOOP["seed"])
-    n_steps = max(10, min(args.steps, 50))
-    with esp.Plan(s.L, s.n, MD_LOOP["tolerance"], r_c=MD_LOOP["r_c_nm"], device=local, stream=stream.cuda_stream,
-                  prefactor=esp.MD_PREFACTOR) as p:
-        p.set_charges(s.q)
-        with esp.MD(p.handle, s.pos, v, dt=MD_LOOP["dt_ps"], lj_cutoff=MD_LOOP["lj_cutoff_nm"]) as sim:
-            sim.run(3)                                   # graph capture, first forces
-            torch.cuda.synchronize(torch.device("cuda", local))
-            t0 = time.perf_counter()
-            e = sim.run(n_steps)                         # ends with a device sync
-            secs = time.perf_counter() - t0
+
+    def run(cfg, n_steps):
+        s = inputs.spce_water(cfg["molecules"], seed=cfg["seed"])
+        v = inputs.water_velocities(cfg["molecules"], cfg["temperature_K"], seed=cfg["seed"])
+        with esp.Plan(s.L, s.n, cfg["tolerance"], r_c=cfg["r_c_nm"], device=local, stream=stream.cuda_stream,
+                      prefactor=esp.MD_PREFACTOR) as p:
+            p.set_charges(s.q)
+            with esp.MD(p.handle, s.pos, v, dt=cfg["dt_ps"], lj_cutoff=cfg["lj_cutoff_nm"]) as sim:
+                sim.run(3)                                   # graph capture, first forces
+                torch.cuda.synchronize(torch.device("cuda", local))
+                t0 = time.perf_counter()
+                e = sim.run(n_steps)                         # ends with a device sync
+                secs = time.perf_counter() - t0
+        return s, e, secs
+
+    n_steps = max(50, min(4 * args.steps, 200))
+    s, e, secs = run(MD_LOOP, n_steps)
     tot = e.sum(axis=1)
     ns_per_day = n_steps * MD_LOOP["dt_ps"] * 1e-3 / secs * 86400.0
-    return {"value": ns_per_day, "unit": "ns/day", "ms_per_step": 1e3 * secs / n_steps, "steps": n_steps,
-            "energy_change_kj_mol_per_atom": float(tot[-1] - tot[0]) / s.n,
-            "max_energy_excursion_over_kinetic": float(np.max(np.abs(tot - tot[0])) / np.mean(e[:, 3])),
-            "config": dict(MD_LOOP, L_nm=s.L)}
+    out = {"value": ns_per_day, "unit": "ns/day", "ms_per_step": 1e3 * secs / n_steps, "steps": n_steps,
+           "energy_change_kj_mol_per_atom": float(tot[-1] - tot[0]) / s.n,
+           "max_energy_excursion_over_kinetic": float(np.max(np.abs(tot - tot[0])) / np.mean(e[:, 3])),
+           "config": dict(MD_LOOP, L_nm=s.L)}
+    sd, ed, secs_d = run(MD_DRIFT, MD_DRIFT["steps"])
+    totd = ed.sum(axis=1)
+    t_ns = np.arange(len(totd)) * MD_DRIFT["dt_ps"] * 1e-3
+    slope = float(np.polyfit(t_ns, totd, 1)[0])
+    out["drift"] = {"kj_mol_per_ns_per_atom": slope / sd.n, "steps": MD_DRIFT["steps"],
+                    "simulated_ps": MD_DRIFT["steps"] * MD_DRIFT["dt_ps"],
+                    "max_excursion_over_kinetic": float(np.max(np.abs(totd - totd[0])) / np.mean(ed[:, 3])),
+                    "ms_per_step": 1e3 * secs_d / MD_DRIFT["steps"], "config": dict(MD_DRIFT, L_nm=sd.L)}
+    return out
 
 
 LARGE = dict(workload="spce_water_1e6_molecules", molecules=1_000_000, atoms=3_000_000, density_per_nm3=33.4,

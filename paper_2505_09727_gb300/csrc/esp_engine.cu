@@ -740,12 +740,14 @@ esp_status do_compute(esp_plan_s* p, double* energy, void* forces, void* potenti
 template <typename real>
 esp_status step_enqueue(esp_plan_s* p, const void* src, void* outF, void* outU, bool out_double, double* outE) {
   const void* key[5] = {outF, outU, out_double ? (const void*)1 : nullptr, outE, src};
-  if (p->sgexec && std::equal(key, key + 5, p->skey)) {
+  // inside a caller's stream capture (e.g. a step graph of the MD loop) the
+  // kernels are launched directly into it
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ESP_CU(cudaStreamIsCapturing(p->st, &cs));
+  if (cs == cudaStreamCaptureStatusNone && p->sgexec && std::equal(key, key + 5, p->skey)) {
     ESP_CU(cudaGraphLaunch(p->sgexec, p->st));
     return ESP_OK;
   }
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  ESP_CU(cudaStreamIsCapturing(p->st, &cs));
   if (p->s_direct_runs == 0 || cs != cudaStreamCaptureStatusNone || p->s_captures >= kMaxRecaptures) {
     ++p->s_direct_runs;
     ESP_TRY(launch_sort<real>(p, src, true));

@@ -648,6 +648,27 @@ __global__ void __launch_bounds__(256) k_scale(
   }
 }
 
+// The T^3 tile of a brick (origin ox, oy, oz, periodic) from the grid into
+// shared memory: one element per thread and step, four loads in flight per
+// thread (the element index split by FP32 reciprocals, exact for these
+// sizes: the quotients stay 1e-4 away from integers and below 2^24).
+template <typename real>
+__device__ __forceinline__ void load_tile(real* __restrict__ tile, const real* __restrict__ grid, int T, int PY,
+                                          int PZ, int ox, int oy, int oz, int n_f) {
+  const int T2 = T * T, T3 = T2 * T;
+  const float inv_T = 1.f / (float)T, inv_T2 = 1.f / (float)T2;
+  const long long plane = (long long)n_f * n_f;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < T3; e += blockDim.x) {
+    const int jz = __float2int_rd(((float)e + 0.5f) * inv_T2);
+    const int r = e - jz * T2;
+    const int jy = __float2int_rd(((float)r + 0.5f) * inv_T);
+    const int jx = r - jy * T;
+    tile[jz * PZ + jy * PY + jx] = __ldg(grid + (long long)wrap_near(oz + jz, n_f) * plane +
+                                         (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f));
+  }
+}
+
 // A6 (ik method): gather the potential and the three gradient grids with the
 // SI weights alone; the gradients are already derivatives in physical units.
 template <typename real, int P>
@@ -670,13 +691,7 @@ __global__ void __launch_bounds__(256) k_gather_ik(
   real* tile = reinterpret_cast<real*>(smem_raw);           // [4][tsz]: u, du/dx, du/dy, du/dz
   for (int g = 0; g < 4; ++g) {
     const real* grid = (g == 0 ? grids : grids_ik + (g - 1) * grid_total) + S.grid0;
-    real* t = tile + g * tsz;
-    for (int jyx = threadIdx.x; jyx < T * T; jyx += blockDim.x) {
-      const int jy = jyx / T, jx = jyx - jy * T;
-      const long long gyx = (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f);
-      for (int jz = 0; jz < T; ++jz)
-        t[jz * PZ + jy * PY + jx] = __ldg(grid + (long long)wrap_near(oz + jz, n_f) * n_f * n_f + gyx);
-    }
+    load_tile(tile + g * tsz, grid, T, PY, PZ, ox, oy, oz, n_f);
   }
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
@@ -745,12 +760,7 @@ __global__ void __launch_bounds__(256) k_gather(
             oz = tile_origin(S, bz, P, real());
   const int PY = S.tpy, PZ = S.tpz;
   const real* grid = grids + S.grid0;
-  for (int jyx = threadIdx.x; jyx < T * T; jyx += blockDim.x) {
-    const int jy = jyx / T, jx = jyx - jy * T;
-    const long long gyx = (long long)wrap_near(oy + jy, n_f) * n_f + wrap_near(ox + jx, n_f);
-    for (int jz = 0; jz < T; ++jz)
-      tile[jz * PZ + jy * PY + jx] = __ldg(grid + (long long)wrap_near(oz + jz, n_f) * n_f * n_f + gyx);
-  }
+  load_tile(tile, grid, T, PY, PZ, ox, oy, oz, n_f);
   __syncthreads();
   const long long k0 = S.cell0 + (long long)b * bc * bc * bc * kSub;
   const uint32_t a_begin = start[k0], a_end = start[k0 + bc * bc * bc * kSub];

@@ -32,11 +32,16 @@ struct esp_md_s {
   double* d_v = nullptr;
   double* d_f = nullptr;
   double* d_e = nullptr;           // energies [(capacity) x 4]
-  double* d_ec = nullptr;          // the solve's energy (a fixed address: the step graph replays)
+  double* d_ecur = nullptr;        // energies of the step in progress (Coulomb, bonded, LJ, kinetic)
+  int* d_row = nullptr;            // next row of d_e the step writes
   long long e_cap = 0;
+  cudaGraph_t graph = nullptr;     // one velocity-Verlet step, replayed n times
+  cudaGraphExec_t gexec = nullptr;
+  const double* graph_e = nullptr; // the d_e the graph was captured with
   double e_now[4] = {0, 0, 0, 0};  // energies at the current positions
   uint32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_tiles = nullptr, *d_cursor = nullptr,
            *d_sorted = nullptr;
+  double* d_opos = nullptr;        // packed O positions (4 values of the plan's precision per O)
   std::vector<void*> allocs;
 };
 
@@ -113,6 +118,18 @@ __global__ void k_kick(double* __restrict__ v, const double* __restrict__ f, MdC
   block_add(e, ek);
 }
 
+// End of a step: the step's energies become row *row of e (when it exists),
+// the accumulators are cleared and the row advances.
+__global__ void k_commit(double* __restrict__ ecur, double* __restrict__ e, int* __restrict__ row, long long cap) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int r = *row;
+    if (r < cap)
+      for (int c = 0; c < 4; ++c) e[4ll * r + c] = ecur[c];
+    for (int c = 0; c < 4; ++c) ecur[c] = 0.0;
+    *row = r + 1;
+  }
+}
+
 // Bonds and angle of one molecule per thread, added to f; energy to *eb.
 __global__ void k_bonded(const double* __restrict__ x, double* __restrict__ f, MdConst C, double* __restrict__ eb) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,14 +195,29 @@ __global__ void k_lj_fill(const uint32_t* __restrict__ cell, const uint32_t* __r
   sorted[start[k] + atomicAdd(cursor + k, 1u)] = (uint32_t)m;
 }
 
+// O positions in cell order (cells) or molecule order (no cells), packed
+// as (x, y, z, molecule) in the precision of the plan, for coalesced reads.
+template <typename real> struct OPos { real x, y, z, m; };
+
+template <typename real>
+__global__ void k_lj_pack(const double* __restrict__ x, const uint32_t* __restrict__ sorted, int use_cells,
+                          int n_mol, OPos<real>* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_mol) return;
+  const int m = use_cells ? (int)sorted[s] : s;
+  const double* o = x + 9ll * m;
+  out[s] = OPos<real>{(real)o[0], (real)o[1], (real)o[2], (real)m};
+}
+
 // One O-O pair seen from i, in the precision of the plan (FP32 plans: FP32
 // coordinates and arithmetic, as the solve's own pair terms).
 template <typename real>
-__device__ __forceinline__ void lj_pair(const real* xi, const double* xj, const MdConst& C, real* fi, real& e) {
+__device__ __forceinline__ void lj_pair(const real* xi, const OPos<real>& pj, const MdConst& C, real* fi, real& e) {
   const real L = (real)C.L, inv_L = (real)C.inv_L;
+  const real xj[3] = {pj.x, pj.y, pj.z};
   real d[3];
   for (int a = 0; a < 3; ++a) {
-    const real t = xi[a] - (real)xj[a];
+    const real t = xi[a] - xj[a];
     d[a] = t - L * rint(t * inv_L);
   }
   const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -198,19 +230,21 @@ __device__ __forceinline__ void lj_pair(const real* xi, const double* xj, const 
   fi[2] += fm * d[2];
 }
 
-// O-O Lennard-Jones, one O per thread: the 27 neighbouring cells (cell edge
-// >= cutoff), or every O when there are fewer than 3 cells per axis.
+// O-O Lennard-Jones, one warp per O (taken in cell order, so the warps of a
+// block read the same neighbouring cells): the lanes stride over the
+// candidates of the 27 neighbouring cells (cell edge >= cutoff), or of every
+// O when there are fewer than 3 cells per axis; sums over the warp.
 template <typename real>
-__global__ void k_lj(const double* __restrict__ x, const uint32_t* __restrict__ cell,
-                     const uint32_t* __restrict__ start, const uint32_t* __restrict__ sorted, MdConst C,
-                     double* __restrict__ f, double* __restrict__ el) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restrict__ cell,
+                     const uint32_t* __restrict__ start, MdConst C, double* __restrict__ f,
+                     double* __restrict__ el) {
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   real e = 0;
-  if (m < C.n_mol) {
-    // with cells, threads take the O atoms in cell order: the lanes of a
-    // warp then read the same neighbouring cells
-    if (C.nc >= 3) m = (int)sorted[m];
-    const real xi[3] = {(real)x[9ll * m], (real)x[9ll * m + 1], (real)x[9ll * m + 2]};
+  if (w < C.n_mol) {
+    const OPos<real> pi = op[w];
+    const int m = (int)pi.m;
+    const real xi[3] = {pi.x, pi.y, pi.z};
     real fi[3] = {0, 0, 0};
     if (C.nc >= 3) {
       const int k = (int)cell[m];
@@ -220,19 +254,25 @@ __global__ void k_lj(const double* __restrict__ x, const uint32_t* __restrict__ 
           for (int oz = -1; oz <= 1; ++oz) {
             const int nx = (cx + ox + C.nc) % C.nc, ny = (cy + oy + C.nc) % C.nc, nz = (cz + oz + C.nc) % C.nc;
             const int kk = (nx * C.nc + ny) * C.nc + nz;
-            for (uint32_t s = start[kk]; s < start[kk + 1]; ++s) {
-              const uint32_t j = sorted[s];
-              if ((int)j != m) lj_pair(xi, x + 9ll * j, C, fi, e);
-            }
+            const uint32_t s1 = start[kk + 1];
+            for (uint32_t s = start[kk] + lane; s < s1; s += 32)
+              if (s != (uint32_t)w) lj_pair(xi, op[s], C, fi, e);
           }
     } else {
-      for (int j = 0; j < C.n_mol; ++j)
-        if (j != m) lj_pair(xi, x + 9ll * j, C, fi, e);
+      for (int s = lane; s < C.n_mol; s += 32)
+        if (s != w) lj_pair(xi, op[s], C, fi, e);
     }
-    double* fo = f + 9ll * m;
-    fo[0] += (double)fi[0];
-    fo[1] += (double)fi[1];
-    fo[2] += (double)fi[2];
+    for (int o = 16; o > 0; o >>= 1) {
+      fi[0] += __shfl_xor_sync(0xffffffffu, fi[0], o);
+      fi[1] += __shfl_xor_sync(0xffffffffu, fi[1], o);
+      fi[2] += __shfl_xor_sync(0xffffffffu, fi[2], o);
+    }
+    if (lane == 0) {
+      double* fo = f + 9ll * m;
+      fo[0] += (double)fi[0];
+      fo[1] += (double)fi[1];
+      fo[2] += (double)fi[2];
+    }
   }
   block_add((double)e, el);
 }
@@ -263,10 +303,11 @@ int blocks_of(long long n) { return (int)std::max<long long>(1, (n + 255) / 256)
 
 // Forces and potential energies at the current positions into d_f and
 // e[0..2] (Coulomb, bonded, Lennard-Jones; e zeroed by the caller).
+// Forces at the current positions; energies to e[0] (Coulomb, written), e[1]
+// (bonded) and e[2] (Lennard-Jones), both added.
 esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st) {
-  esp_status s = esp_step(md->plan, md->d_x, md->d_ec, md->d_f, nullptr, ESP_DEVICE);
+  esp_status s = esp_step(md->plan, md->d_x, e, md->d_f, nullptr, ESP_DEVICE);
   if (s != ESP_OK) return s;
-  MD_CU(cudaMemcpyAsync(e, md->d_ec, sizeof(double), cudaMemcpyDeviceToDevice, st));
   const MdConst C = make_const(md);
   k_bonded<<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_f, C, e + 1);
   if (md->nc >= 3) {
@@ -277,12 +318,17 @@ esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st) {
     MD_CU(espk::launch_scan(md->d_count, md->d_start, md->d_tiles, ncell, st));
     k_lj_fill<<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_cell, md->d_start, md->d_cursor, md->d_sorted, md->n_mol);
   }
-  if (md->fp32)
-    k_lj<float><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_cell, md->d_start, md->d_sorted, C, md->d_f,
-                                                     e + 2);
-  else
-    k_lj<double><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_cell, md->d_start, md->d_sorted, C, md->d_f,
-                                                      e + 2);
+  const int use_cells = md->nc >= 3;
+  const int wb = blocks_of(32ll * md->n_mol);                   // one warp per O
+  if (md->fp32) {
+    auto* op = reinterpret_cast<OPos<float>*>(md->d_opos);
+    k_lj_pack<float><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, op);
+    k_lj<float><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f, e + 2);
+  } else {
+    auto* op = reinterpret_cast<OPos<double>*>(md->d_opos);
+    k_lj_pack<double><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, op);
+    k_lj<double><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f, e + 2);
+  }
   MD_CU(cudaGetLastError());
   return ESP_OK;
 }
@@ -311,6 +357,47 @@ struct MdDevice {
   }
   ~MdDevice() { cudaSetDevice(prev); }
 };
+
+// One velocity-Verlet step: kick + drift, forces, kick, commit of its energies.
+esp_status md_step(esp_md_s* md, cudaStream_t st) {
+  const MdConst C = make_const(md);
+  const int nb = blocks_of(md->n_atoms);
+  k_kick_drift<<<nb, 256, 0, st>>>(md->d_x, md->d_v, md->d_f, C, md->n_atoms);
+  esp_status s = md_forces(md, md->d_ecur, st);
+  if (s != ESP_OK) return s;
+  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 1.0, md->d_ecur + 3);
+  k_commit<<<1, 32, 0, st>>>(md->d_ecur, md->d_e, md->d_row, md->e_cap);
+  MD_CU(cudaGetLastError());
+  return ESP_OK;
+}
+
+void drop_graph(esp_md_s* md) {
+  if (md->gexec) cudaGraphExecDestroy(md->gexec);
+  if (md->graph) cudaGraphDestroy(md->graph);
+  md->gexec = nullptr;
+  md->graph = nullptr;
+  md->graph_e = nullptr;
+}
+
+// The step as a CUDA graph on the plan's stream (captured once per energy
+// buffer; the solve inside is launched directly into the capture).
+esp_status md_graph(esp_md_s* md, cudaStream_t st) {
+  if (md->gexec && md->graph_e == md->d_e) return ESP_OK;
+  drop_graph(md);
+  MD_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  esp_status s = md_step(md, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (s != ESP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return md_fail(ESP_ERR_CUDA, std::string("MD step capture: ") + cudaGetErrorString(e));
+  md->graph = g;
+  MD_CU(cudaGraphInstantiate(&md->gexec, g, 0));
+  md->graph_e = md->d_e;
+  return ESP_OK;
+}
 
 }  // namespace
 
@@ -359,9 +446,11 @@ esp_status esp_md_create(esp_plan_t plan, const esp_md_params* params, const dou
   const size_t n3 = (size_t)md->n_atoms * 3;
   esp_status st = ESP_OK;
   if ((st = md_alloc(md, &md->d_x, n3)) != ESP_OK || (st = md_alloc(md, &md->d_v, n3)) != ESP_OK ||
-      (st = md_alloc(md, &md->d_f, n3)) != ESP_OK || (st = md_alloc(md, &md->d_ec, 1)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_f, n3)) != ESP_OK || (st = md_alloc(md, &md->d_ecur, 4)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_row, 1)) != ESP_OK ||
       (st = md_alloc(md, &md->d_cell, (size_t)md->n_mol)) != ESP_OK ||
-      (st = md_alloc(md, &md->d_sorted, (size_t)md->n_mol)) != ESP_OK) {
+      (st = md_alloc(md, &md->d_sorted, (size_t)md->n_mol)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_opos, (size_t)md->n_mol * 4)) != ESP_OK) {
     md_release(md);
     delete md;
     return st;
@@ -416,25 +505,26 @@ esp_status esp_md_run(esp_md_t md, int n_steps, double* energies) {
     md->e_cap = rows;
   }
   MD_CU(cudaMemsetAsync(md->d_e, 0, (size_t)rows * 4 * sizeof(double), st));
+  MD_CU(cudaMemsetAsync(md->d_ecur, 0, 4 * sizeof(double), st));
+  MD_CU(cudaMemsetAsync(md->d_row, 0, sizeof(int), st));
   const MdConst C = make_const(md);
   const int nb = blocks_of(md->n_atoms);
   // row 0: the current state (forces computed once, then carried over)
   if (!md->have_forces) {
-    esp_status s = md_forces(md, md->d_e, st);
+    esp_status s = md_forces(md, md->d_ecur, st);
     if (s != ESP_OK) return s;
     md->have_forces = true;
   } else {
-    MD_CU(cudaMemcpyAsync(md->d_e, md->e_now, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    MD_CU(cudaMemcpyAsync(md->d_ecur, md->e_now, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
   }
-  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 0.0, md->d_e + 3);
-  for (int k = 1; k <= n_steps; ++k) {
-    double* e = md->d_e + 4ll * k;
-    k_kick_drift<<<nb, 256, 0, st>>>(md->d_x, md->d_v, md->d_f, C, md->n_atoms);
-    esp_status s = md_forces(md, e, st);
-    if (s != ESP_OK) return s;
-    k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 1.0, e + 3);
-  }
+  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 0.0, md->d_ecur + 3);
+  k_commit<<<1, 32, 0, st>>>(md->d_ecur, md->d_e, md->d_row, md->e_cap);
   MD_CU(cudaGetLastError());
+  if (n_steps > 0) {
+    esp_status s = md_graph(md, st);
+    if (s != ESP_OK) return s;
+    for (int k = 1; k <= n_steps; ++k) MD_CU(cudaGraphLaunch(md->gexec, st));
+  }
   std::vector<double> h((size_t)rows * 4);
   MD_CU(cudaMemcpyAsync(h.data(), md->d_e, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   MD_CU(cudaStreamSynchronize(st));
@@ -460,6 +550,7 @@ esp_status esp_md_destroy(esp_md_t md) {
     MdDevice g(md->device);
     cudaStream_t st = espe::plan_stream(md->plan);
     if (st) cudaStreamSynchronize(st);
+    drop_graph(md);
     md_release(md);
     // the intramolecular exclusions belong to the MD state, not to the plan
     esp_set_exclusions(md->plan, nullptr, 0);
