@@ -1267,6 +1267,33 @@ esp_status batch_plans(const esp_box* boxes, const int64_t* N, int nsys, double 
     }
     if (st != ESP_OK) return fail(st, "system " + std::to_string(s) + ": " + msg);
   }
+  // One spread launch serves every system with the batch's largest tile, so
+  // a system whose brick shape gives an outlying tile (a single brick across
+  // a small box, say) shrinks every CTA's warp count: such systems are
+  // re-planned with the largest smaller brick whose tile is within two
+  // points of the batch's median tile.
+  if (o.brick_cells <= 0 && nsys > 2) {
+    std::vector<int> tiles(nsys);
+    for (int s = 0; s < nsys; ++s) tiles[s] = hps[s].desc.T;
+    std::nth_element(tiles.begin(), tiles.begin() + nsys / 2, tiles.end());
+    const int t_cap = tiles[nsys / 2] + 2;
+    for (int s = 0; s < nsys; ++s) {
+      if (hps[s].desc.T <= t_cap) continue;
+      for (int b = hps[s].desc.bc - 1; b >= 1; --b) {
+        esp_plan_opts oo = o;
+        oo.c = hps[s].info.c;
+        oo.c1 = hps[s].info.c1;
+        oo.n_f = hps[s].info.n_f;
+        oo.brick_cells = b;
+        espe::HostPlan tmp;
+        if (espe::make_host_plan(boxes[s].L[0], N[s], tol, oo, tmp, msg) != ESP_OK) continue;
+        if (tmp.desc.T <= t_cap) {
+          hps[s] = tmp;
+          break;
+        }
+      }
+    }
+  }
   return ESP_OK;
 }
 
