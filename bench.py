@@ -689,12 +689,25 @@ def served(args, local):
     t_plans = time.perf_counter() - t0
     pos_cache = {}
 
-    def run(rate):
-        """rate None: closed loop with 64 requests outstanding; else Poisson."""
+    def run(rate, clients=4):
+        """rate None: closed loop with 64 requests outstanding; else Poisson
+        arrivals. Requests are handed to `clients` submitting threads (each
+        submission copies the request's positions into the server's pinned
+        buffers, so one thread caps the request rate); one thread collects."""
         import queue
         esp.esp_server_reset_stats(srv.handle)
         window = threading.Semaphore(64 if rate is None else 512)
+        arrivals = queue.Queue()
         pending = queue.Queue()
+
+        def client():
+            while True:
+                item = arrivals.get()
+                if item is None:
+                    return
+                i, eps, k = item
+                window.acquire()
+                pending.put(srv.submit(ids[i], eps, pos_cache[(i, k)]))
 
         def waiter():
             while True:
@@ -704,18 +717,24 @@ def served(args, local):
                 srv.wait(t, forces=False, potential=False)
                 window.release()
 
+        subs = [threading.Thread(target=client) for _ in range(clients)]
         th = threading.Thread(target=waiter)
+        for t in subs:
+            t.start()
         th.start()
         t_start = time.perf_counter()
         next_t = t_start
-        for i, eps, k in reqs:
+        for item in reqs:
             if rate:
                 next_t += rng.exponential(1.0 / rate)
                 d = next_t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-            window.acquire()
-            pending.put(srv.submit(ids[i], eps, pos_cache[(i, k)]))
+            arrivals.put(item)
+        for _ in subs:
+            arrivals.put(None)
+        for t in subs:
+            t.join()
         pending.put(None)
         th.join()
         wall = time.perf_counter() - t_start

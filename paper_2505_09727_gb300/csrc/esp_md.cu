@@ -197,34 +197,54 @@ __global__ void k_lj_fill(const uint32_t* __restrict__ cell, const uint32_t* __r
 
 // O positions in cell order (cells) or molecule order (no cells), packed
 // as (x, y, z, molecule) in the precision of the plan, for coalesced reads.
-template <typename real> struct OPos { real x, y, z, m; };
+template <typename real> struct __align__(4 * sizeof(real)) OPos { real x, y, z, m; };
 
 template <typename real>
 __global__ void k_lj_pack(const double* __restrict__ x, const uint32_t* __restrict__ sorted, int use_cells,
-                          int n_mol, OPos<real>* __restrict__ out) {
+                          int n_mol, MdConst C, OPos<real>* __restrict__ out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_mol) return;
   const int m = use_cells ? (int)sorted[s] : s;
   const double* o = x + 9ll * m;
-  out[s] = OPos<real>{(real)o[0], (real)o[1], (real)o[2], (real)m};
+  // wrapped into [0, L): with cells, a neighbouring cell's image shift is
+  // then +-L or 0 along each axis
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    w[a] = o[a] - C.L * floor(o[a] * C.inv_L);
+    if (w[a] >= C.L) w[a] -= C.L;
+  }
+  out[s] = OPos<real>{(real)w[0], (real)w[1], (real)w[2], (real)m};
 }
 
 // One O-O pair seen from i, in the precision of the plan (FP32 plans: FP32
-// coordinates and arithmetic, as the solve's own pair terms).
-template <typename real>
-__device__ __forceinline__ void lj_pair(const real* xi, const OPos<real>& pj, const MdConst& C, real* fi, real& e) {
-  const real L = (real)C.L, inv_L = (real)C.inv_L;
+// coordinates and arithmetic, as the solve's own pair terms). d = x_i - x_j
+// with the minimum image taken by `rint` (no cells) or by the neighbouring
+// cell's shift sh (cells; wrapped positions).
+// The Lennard-Jones constants in the plan's precision, converted once per
+// thread (FP64 conversions are slow on this GPU).
+template <typename real> struct LjC {
+  real L, inv_L, rc2, sigma2, eps4, shift;
+  __device__ explicit LjC(const MdConst& C)
+      : L((real)C.L), inv_L((real)C.inv_L), rc2((real)C.rc2), sigma2((real)C.sigma2), eps4((real)C.eps4),
+        shift((real)C.shift) {}
+};
+
+template <typename real, bool CELLS>
+__device__ __forceinline__ void lj_pair(const real* xi, const OPos<real>& pj, const real* sh, const LjC<real>& C,
+                                        real* fi, real& e) {
   const real xj[3] = {pj.x, pj.y, pj.z};
   real d[3];
   for (int a = 0; a < 3; ++a) {
     const real t = xi[a] - xj[a];
-    d[a] = t - L * rint(t * inv_L);
+    if constexpr (CELLS) d[a] = t + sh[a];
+    else d[a] = t - C.L * rint(t * C.inv_L);
   }
   const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  if (r2 >= (real)C.rc2 || r2 <= real(0)) return;
-  const real s2 = (real)C.sigma2 / r2, s6 = s2 * s2 * s2;
-  e += real(0.5) * ((real)C.eps4 * (s6 * s6 - s6) - (real)C.shift);   // every pair is met from both sides
-  const real fm = real(6) * (real)C.eps4 * (real(2) * s6 * s6 - s6) / r2;
+  if (r2 >= C.rc2 || r2 <= real(0)) return;
+  const real inv_r2 = real(1) / r2;
+  const real s2 = C.sigma2 * inv_r2, s6 = s2 * s2 * s2;
+  e += real(0.5) * (C.eps4 * (s6 * s6 - s6) - C.shift);   // every pair is met from both sides
+  const real fm = real(6) * C.eps4 * (real(2) * s6 * s6 - s6) * inv_r2;
   fi[0] += fm * d[0];
   fi[1] += fm * d[1];
   fi[2] += fm * d[2];
@@ -240,6 +260,7 @@ __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restri
                      double* __restrict__ el) {
   const int lane = threadIdx.x & 31;
   const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const LjC<real> LC(C);
   real e = 0;
   if (w < C.n_mol) {
     const OPos<real> pi = op[w];
@@ -247,20 +268,37 @@ __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restri
     const real xi[3] = {pi.x, pi.y, pi.z};
     real fi[3] = {0, 0, 0};
     if (C.nc >= 3) {
+      const int nc = C.nc;
       const int k = (int)cell[m];
-      const int cz = k % C.nc, cy = (k / C.nc) % C.nc, cx = k / (C.nc * C.nc);
+      const int cz = k % nc, cy = (k / nc) % nc, cx = k / (nc * nc);
+      auto wrap = [&](int u) { return u < 0 ? u + nc : (u >= nc ? u - nc : u); };
+      auto shift = [&](int u) { return u < 0 ? LC.L : (u >= nc ? -LC.L : real(0)); };
+      // the three z-neighbouring cells of a column (nx, ny) are consecutive in
+      // cell order: one range, or two where the column wraps in z
+      auto sweep = [&](uint32_t b, uint32_t e2, const real* sh) {
+        for (uint32_t s = b + lane; s < e2; s += 32)
+          if (s != (uint32_t)w) lj_pair<real, true>(xi, op[s], sh, LC, fi, e);
+      };
       for (int ox = -1; ox <= 1; ++ox)
-        for (int oy = -1; oy <= 1; ++oy)
-          for (int oz = -1; oz <= 1; ++oz) {
-            const int nx = (cx + ox + C.nc) % C.nc, ny = (cy + oy + C.nc) % C.nc, nz = (cz + oz + C.nc) % C.nc;
-            const int kk = (nx * C.nc + ny) * C.nc + nz;
-            const uint32_t s1 = start[kk + 1];
-            for (uint32_t s = start[kk] + lane; s < s1; s += 32)
-              if (s != (uint32_t)w) lj_pair(xi, op[s], C, fi, e);
+        for (int oy = -1; oy <= 1; ++oy) {
+          const int ux = cx + ox, uy = cy + oy;
+          const int col = (wrap(ux) * nc + wrap(uy)) * nc;
+          real sh[3] = {shift(ux), shift(uy), real(0)};
+          if (cz == 0) {
+            sweep(start[col], start[col + 2], sh);                 // cells 0, 1
+            sh[2] = LC.L;
+            sweep(start[col + nc - 1], start[col + nc], sh);       // cell nc - 1, one period down
+          } else if (cz == nc - 1) {
+            sweep(start[col + nc - 2], start[col + nc], sh);       // cells nc - 2, nc - 1
+            sh[2] = -LC.L;
+            sweep(start[col], start[col + 1], sh);                 // cell 0, one period up
+          } else {
+            sweep(start[col + cz - 1], start[col + cz + 2], sh);   // cells cz - 1 ... cz + 1
           }
+        }
     } else {
       for (int s = lane; s < C.n_mol; s += 32)
-        if (s != w) lj_pair(xi, op[s], C, fi, e);
+        if (s != w) lj_pair<real, false>(xi, op[s], nullptr, LC, fi, e);
     }
     for (int o = 16; o > 0; o >>= 1) {
       fi[0] += __shfl_xor_sync(0xffffffffu, fi[0], o);
@@ -322,11 +360,11 @@ esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st) {
   const int wb = blocks_of(32ll * md->n_mol);                   // one warp per O
   if (md->fp32) {
     auto* op = reinterpret_cast<OPos<float>*>(md->d_opos);
-    k_lj_pack<float><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, op);
+    k_lj_pack<float><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, C, op);
     k_lj<float><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f, e + 2);
   } else {
     auto* op = reinterpret_cast<OPos<double>*>(md->d_opos);
-    k_lj_pack<double><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, op);
+    k_lj_pack<double><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, C, op);
     k_lj<double><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f, e + 2);
   }
   MD_CU(cudaGetLastError());

@@ -43,7 +43,7 @@ def requests_of(systems, n_req, seed):
     out = []
     for k in range(n_req):
         i = int(rng.integers(len(systems)))
-        eps = float(rng.choice([1e-3, 1e-4]))
+        eps = float(rng.choice([1e-3, 1e-4, 1e-5]))
         out.append((i, eps, inputs.perturb(systems[i], 0.01, seed=seed * 1000 + k).pos))
     return out
 
@@ -62,8 +62,10 @@ def check(esp, systems, reqs, results, r_c):
 
 
 def test_mix_and_alone_match_single_plans(esp):
-    systems = inputs.electrolyte_batch([3000, 5200, 8000, 3600, 12000], seed=300)
+    # tolerances 1e-3, 1e-4 and 1e-5; one system of 2e5 atoms in the mix
+    systems = inputs.electrolyte_batch([3000, 5200, 8000, 3600, 12000, 200_000], seed=300)
     reqs = requests_of(systems, 24, seed=301)
+    assert {eps for _, eps, _ in reqs} == {1e-3, 1e-4, 1e-5} and any(i == 5 for i, _, _ in reqs)
     with esp.Server(1.0, max_inflight=6) as srv:
         ids = [srv.add_system(s.L, s.q) for s in systems]
         tickets = [srv.submit(ids[i], eps, pos) for i, eps, pos in reqs]       # the mix
@@ -77,7 +79,7 @@ def test_mix_and_alone_match_single_plans(esp):
     for a, b in zip(mixed, single):
         assert rel_rms(a[1], b[1]) <= FP32_PARITY
     assert st["completed"] == 48 and st["failed"] == 0
-    assert st["plans_resident"] == st["plans_created"] <= 10
+    assert st["plans_resident"] == st["plans_created"] <= 18
     assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
 
 
