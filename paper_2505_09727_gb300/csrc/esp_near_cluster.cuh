@@ -93,8 +93,9 @@ struct ClusterSmem {
 // (ox, oy) away sits at ox a/n_c + oy b/n_c and a brick up the column at
 // bc c/n_c (Cartesian offsets), and the records hold Cartesian positions
 // relative to their brick corner. The z window is the cutoff around the box
-// in Cartesian z (z depends on the fractional z alone); columns are not
-// culled by their xy gap, every candidate passes the box filter.
+// in Cartesian z (z depends on the fractional z alone); a column is culled
+// when the xy extent it can reach over the cutoff's z window (its sheared
+// cross-section) lies r_c or more from the cluster's box.
 template <int NC, bool HALF, bool VIR, int WARPS, bool TRI = false>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     const SysDesc* __restrict__ sys, const int2* __restrict__ cmap, const int2* __restrict__ catoms,
@@ -340,6 +341,23 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
           if constexpr (!TRI) {
             const float gx = fmax3(0.f, (float)ox * w - bx_hi, bx_lo - (float)(ox + 1) * w);
             const float gy = fmax3(0.f, (float)oy * w - by_hi, by_lo - (float)(oy + 1) * w);
+            d2 = gx * gx + gy * gy;
+          } else {
+            // triclinic: a point of the column at Cartesian height z (cluster
+            // frame) has x = (f_x a_x + f_y b_x) / n_c + z c_x / c_z and
+            // y = f_y b_y / n_c + z c_y / c_z with f_x in [ox, ox + 1),
+            // f_y in [oy, oy + 1). Over the z window of the full cutoff that
+            // bounds the column's xy extent, whose gap to the cluster's box
+            // bounds every candidate's xy distance from below
+            const float z1 = bz_lo - S.r_cf - margin, z2 = bz_hi + S.r_cf + margin;
+            const float sx = S.tbrick[0] / S.tbrick[2], sy = S.tbrick[1] / S.tbrick[2];
+            const float xb0 = (float)oy * S.tcol[1], xb1 = (float)(oy + 1) * S.tcol[1];
+            const float x_lo = fmaf((float)ox, S.tcol[0], fminf(xb0, xb1)) + fminf(z1 * sx, z2 * sx);
+            const float x_hi = fmaf((float)(ox + 1), S.tcol[0], fmaxf(xb0, xb1)) + fmaxf(z1 * sx, z2 * sx);
+            const float y_lo = (float)oy * S.tcol[2] + fminf(z1 * sy, z2 * sy);
+            const float y_hi = (float)(oy + 1) * S.tcol[2] + fmaxf(z1 * sy, z2 * sy);
+            const float gx = fmax3(0.f, x_lo - bx_hi, bx_lo - x_hi);
+            const float gy = fmax3(0.f, y_lo - by_hi, by_lo - y_hi);
             d2 = gx * gx + gy * gy;
           }
           const bool col_on = use && d2 < cull2;
