@@ -257,8 +257,10 @@ esp_status esp_phase_times(esp_plan_t plan, float* ms, int n);
 esp_status esp_last_spectral_energy(esp_plan_t plan, double* e_fourier, double* e_gather);
 
 /* One step: esp_set_positions(xyz) followed by esp_compute, in one call.
- * With host buffers the call copies the positions in, computes, copies the
- * results out and waits once; after its first run the sort and the compute
+ * With host buffers the call copies the positions in (positions in
+ * page-locked host memory mapped into the device's address space, e.g. from
+ * cudaHostAlloc, are read in place by the ingest kernel instead), computes,
+ * copies the results out and waits once; after its first run the sort and the compute
  * replay as one captured CUDA graph (per position source and output
  * pointers, as for esp_compute). Errors as for the two calls (a non-finite
  * position is reported as ESP_ERR_NONFINITE by this call with host

@@ -655,6 +655,18 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
 
 // Host tail of a compute with host outputs: copies, bounded wait, energies,
 // device error flag.
+// The device address of a page-locked host buffer mapped into the device's
+// address space (nullptr for any other pointer).
+void* mapped_host(const void* h) {
+  if (!h) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 esp_status finish_host(esp_plan_s* p, double* energy, void* forces, void* potential, bool out_double) {
   const long long N = p->N;
   const size_t ob = out_double ? sizeof(double) : sizeof(float);
@@ -788,8 +800,18 @@ esp_status do_step(esp_plan_s* p, const double* xyz, double* energy, void* force
   void* outU = potential;
   double* outE = energy;
   if (where == ESP_HOST) {
-    ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, p->N * 3 * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    src = p->d_pos;
+    // positions in a page-locked host buffer mapped into the device's
+    // address space are read in place by the ingest (coalesced, over the
+    // CPU-GPU link): no staging copy. Results go back by copies: the
+    // finalize writes them in caller order, scattered, which the link
+    // serves worse than one bulk copy
+    const void* xyz_dev = mapped_host(xyz);
+    if (xyz_dev) {
+      src = xyz_dev;
+    } else {
+      ESP_CU(cudaMemcpyAsync(p->d_pos, xyz, p->N * 3 * sizeof(double), cudaMemcpyHostToDevice, p->st));
+      src = p->d_pos;
+    }
     outF = forces ? p->d_outF : nullptr;
     outU = potential ? p->d_outU : nullptr;
     outE = nullptr;
