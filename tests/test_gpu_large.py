@@ -10,6 +10,9 @@ states its errors against.
   method at raised parameters).
 * That reference: the FP64 solve at eps = 1e-10 parameters matches
   converged classical Ewald to 1e-9 on a water box small enough for Ewald.
+* The batched workload at full size (64 electrolyte boxes, 3.24e6 atoms):
+  sampled atoms of three systems against the oracle at their batch
+  parameters, every system against an FP64 batch at 1e-10 parameters.
 """
 import numpy as np
 import pytest
@@ -65,3 +68,39 @@ def test_large_water_box_at_full_size(esp):
     delta = metrics.relative_rms_force_error(f, f_ref)
     assert delta <= 1e-5, delta
     assert abs(e - e_ref) <= 1e-5 * abs(e_ref)
+
+
+def test_batched_workload_at_full_size(esp):
+    """The 64-box electrolyte batch of the benchmark (3.24e6 atoms, sizes
+    log-uniform in [3e3, 2e5], seed 9727, one launch per kernel, graph
+    replay): sampled atoms of the smallest, a middle and the largest system
+    against the oracle at that system's batch parameters (FP32 parity bound),
+    and every system's force error over all atoms against an FP64 batch at
+    eps = 1e-10 parameters within the tolerance."""
+    sizes = inputs.batch_sizes(64, 3000, 200_000, seed=9727)
+    systems = inputs.electrolyte_batch(sizes, seed=9727)
+    pos, q = inputs.concat(systems)
+    with esp.Batch([s.L for s in systems], [s.n for s in systems], 1e-4, r_c=1.0) as b:
+        b.set_charges(q)
+        for _ in range(2):                                  # direct run, then the captured graph
+            e, f, u = b.compute(pos)
+        infos = [b.info(i) for i in range(len(systems))]
+        off = b.offsets
+    assert np.all(np.isfinite(f)) and np.all(np.isfinite(e))
+    order = np.argsort(sizes)
+    rng = np.random.default_rng(5)
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        s, info = systems[i], infos[i]
+        idx = np.sort(rng.choice(s.n, size=min(48, s.n), replace=False))
+        p = oesp.ESPParams(1e-4, info["r_c"], info["P"], info["n_f"], c=info["c"], c1=info["c1"])
+        ref = oesp.esp(s.pos, s.q, s.L, p, idx)
+        fs = f[off[i]:off[i + 1]][idx]
+        us = u[off[i]:off[i + 1]][idx]
+        assert metrics.relative_rms_force_error(fs, ref["forces"]) <= FP32_PARITY, i
+        assert float(np.sqrt(np.sum((us - ref["potential"]) ** 2) / np.sum(ref["potential"] ** 2))) <= FP32_PARITY
+    with esp.Batch([s.L for s in systems], [s.n for s in systems], 1e-10, r_c=1.0, precision=esp.ESP_FP64) as rb:
+        rb.set_charges(q)
+        _, f_ref, _ = rb.compute(pos)
+    for i in range(len(systems)):
+        sl = slice(off[i], off[i + 1])
+        assert metrics.relative_rms_force_error(f[sl], f_ref[sl]) <= 1e-4, i
