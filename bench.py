@@ -66,16 +66,73 @@ def dist_env():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """SM clocks and clock-event reasons while the timed steps run.
+
+    NVML read-only queries (through ctypes, from a thread) every 5 ms, so a
+    timed region of a few tens of milliseconds still holds several samples;
+    without NVML, nvidia-smi every 200 ms. Nothing is ever set.
+    """
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of NVML
+    NVML_REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+                    (0x40, "hw_thermal_slowdown"))
+    NVML_CLOCK_SM = 1
+    PERIOD_S = 0.005
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.thread = None
         self.path = os.path.join(tempfile.gettempdir(), f"esp_bench_clocks_rank{index}.csv")
 
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        handle = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(handle)) == 0
+        except (AttributeError, RuntimeError, ImportError):
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(handle)) != 0:
+            return None
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, handle, reasons
+
+    def _poll(self, lib, handle, reasons_fn):
+        import ctypes
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if lib.nvmlDeviceGetClockInfo(handle, self.NVML_CLOCK_SM, ctypes.byref(clk)) == 0 and \
+                    reasons_fn(handle, ctypes.byref(rs)) == 0:
+                self.samples.append((clk.value, rs.value))
+            time.sleep(self.PERIOD_S)
+
     def start(self):
+        import threading
+        try:
+            nv = self._nvml_handle()
+        except (OSError, AttributeError):
+            nv = None
+        if nv is not None:
+            import ctypes
+            lib, handle, reasons_fn = nv
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(
+                handle, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 else None
+            self.samples = []
+            self.stop_flag = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=nv, daemon=True)
+            self.thread.start()
+            return
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -87,6 +144,16 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            if not self.samples:
+                return None
+            sm = [float(c) for c, _ in self.samples]
+            reasons = {name for c, r in self.samples for bit, name in self.NVML_REASONS if r & bit}
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz or max(sm),
+                    "sm_min_mhz": min(sm), "reasons": sorted(reasons), "samples": len(sm),
+                    "source": "NVML every 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -112,7 +179,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi every 200 ms"}
 
 
 # ------------------------------------------------------------------ roofline

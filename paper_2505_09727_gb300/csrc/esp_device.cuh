@@ -77,6 +77,10 @@ struct SysDesc {
   double w;          // cell edge L / n_c
   double fix_scale;  // L / 2^32
   double to_fixed;   // 2^32 / L
+  // 2^32 / L as fix_m 2^fix_e (fix_m: 64 bits, top bit set, rounded down):
+  // the FP32 ingest's exact integer conversion to fixed point
+  unsigned long long fix_m;
+  int fix_e;
   double w32;        // w / 2^32
   double self_coef;  // chi(0) / (4 pi r_c)
   double bg_shift;   // -(Q/V) (r_c^2/2) int_0^1 x^2 chi
@@ -113,6 +117,38 @@ __host__ __device__ inline void tile_pitches(int T, int P, int& py, int& pz) {
 // FP32 mode stores coordinates as 32-bit fixed-point fractions of L: the grid
 // index of the stencil origin is then exact integer arithmetic and pair
 // differences are exact integer differences (minimum image = int32 wrap).
+// u = floor(x S) mod 2^32 for S = fix_m 2^fix_e, in integer arithmetic on the
+// bits of the double x = m 2^E (m the 53-bit significand): x S = (m fix_m)
+// 2^(E + fix_e), the 117-bit product formed exactly and shifted; a negative x
+// rounds down (one less when a fraction remains). No FP64 instruction: FP64
+// units are scarce on this GPU. x must be finite.
+__device__ __forceinline__ uint32_t fixed_from_double(double x, unsigned long long fix_m, int fix_e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull);
+  const int sh = (ex ? ex : 1) - 1075 + fix_e;         // x S = (hi:lo) 2^sh
+  const unsigned long long lo = m * fix_m, hi = __umul64hi(m, fix_m);
+  uint32_t ip;                                          // floor(|x| S) mod 2^32
+  bool frac;                                            // |x| S is not an integer
+  if (sh >= 0) {
+    ip = sh >= 32 ? 0u : (uint32_t)(lo << sh);
+    frac = false;
+  } else {
+    const int r = -sh;
+    if (r >= 128) {
+      ip = 0u;
+      frac = (hi | lo) != 0ull;
+    } else if (r >= 64) {
+      ip = (uint32_t)(hi >> (r - 64));
+      frac = lo != 0ull || (r > 64 && (hi << (128 - r)) != 0ull);
+    } else {
+      ip = (uint32_t)((lo >> r) | (hi << (64 - r)));
+      frac = (lo << (64 - r)) != 0ull;
+    }
+  }
+  return (bits >> 63) ? 0u - ip - (frac ? 1u : 0u) : ip;
+}
+
 __host__ __device__ inline void stencil_fixed(uint32_t u, int n_f, int P, int& l0, int64_t& r) {
   // t = u n_f / 2^32 (32.32 fixed point); l0 = ceil(t - P/2);
   // r = (t - l0 - P/2 + 1) * 2^32 in (0, 2^32]

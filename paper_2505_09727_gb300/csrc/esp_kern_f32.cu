@@ -25,7 +25,6 @@ cudaError_t launch_scan(const uint32_t* count, uint32_t* start, uint32_t* tile_s
     return cudaGetLastError();
   }
   k_scan_tiles<<<tiles, kScanThreads, 0, st>>>(count, start, tile_sum, n);
-  k_scan_totals<<<1, kScanThreads, 0, st>>>(tile_sum, tiles, start, n);
   k_scan_add<<<tiles, kScanThreads, 0, st>>>(start, tile_sum, n);
   return cudaGetLastError();
 }

@@ -175,16 +175,9 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
     } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      // u = floor(x 2^32 / L) mod 2^32: one FP64 product rounded down to a
-      // 64-bit integer whose low word is the periodic wrap (FP64 division
-      // and floor are slow on this GPU); only |x| beyond 2^31 L wraps in FP64
-      long long v = __double2ll_rd(p[a] * S.to_fixed);
-      if (v == LLONG_MAX || v == LLONG_MIN) {   // saturated: |x| beyond 2^31 L
-        double f = p[a] * S.inv_L;
-        f -= floor(f);
-        v = (long long)(f * 4294967296.0);
-      }
-      u[a] = (uint32_t)(unsigned long long)v;
+      // u = floor(x 2^32 / L) mod 2^32 (the periodic wrap is the mod), in
+      // integer arithmetic: exact for every finite x
+      u[a] = fixed_from_double(p[a], S.fix_m, S.fix_e);
       c[a] = (int)(((uint64_t)u[a] * (uint64_t)S.n_c) >> 32);
     }
     }
@@ -223,9 +216,9 @@ __global__ void __launch_bounds__(kChunk) k_ingest(
   rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-// A1a: exclusive scan of the pooled cell-list counts in three passes: each
-// block scans kScanTile entries and records its total; one block scans the
-// totals; every block adds its offset. start[n] receives the grand total.
+// A1a: exclusive scan of the pooled cell-list counts in two passes: each
+// block scans kScanTile entries and records its total; then every block adds
+// the sum of the totals before it. start[n] receives the grand total.
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 constexpr int kScanTile = kScanThreads * kScanPer;
@@ -277,24 +270,6 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
   if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
 }
 
-static __global__ void __launch_bounds__(kScanThreads) k_scan_totals(
-    uint32_t* __restrict__ tile_sum, int n_tiles, uint32_t* __restrict__ start, long long n) {
-  __shared__ uint32_t wsum[33];
-  const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
-  const int b = per * threadIdx.x;
-  const int e = b + per < n_tiles ? b + per : n_tiles;
-  uint32_t s = 0;
-  for (int j = b; j < e; ++j) s += tile_sum[j];
-  uint32_t total;
-  uint32_t run = block_exclusive_scan(s, wsum, &total);
-  for (int j = b; j < e; ++j) {
-    const uint32_t t = tile_sum[j];
-    tile_sum[j] = run;
-    run += t;
-  }
-  if (threadIdx.x == 0) start[n] = total;
-}
-
 // Whole scan in one CTA for short arrays (one launch instead of three): each
 // thread sums a contiguous run of entries, the CTA scans the run sums, and
 // each thread writes its run.
@@ -318,10 +293,37 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_small(
   if (threadIdx.x == 0) start[n] = total;
 }
 
+// Sum of v over the CTA (every thread gets it); wsum holds 32 words.
+__device__ inline uint32_t block_sum_u32(uint32_t v, uint32_t* wsum) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();                                  // wsum is free again
+  if (lane == 0) wsum[wid] = v;
+  __syncthreads();
+  uint32_t t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+  return t;
+}
+
+// Second pass: each tile adds the sum of the tile totals before it (a CTA
+// reduction over the totals); the last tile also writes the grand total to
+// start[n].
 static __global__ void __launch_bounds__(kScanThreads) k_scan_add(
     uint32_t* __restrict__ start, const uint32_t* __restrict__ tile_sum, long long n) {
-  const uint32_t off = tile_sum[blockIdx.x];
-  const long long b = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+  __shared__ uint32_t wsum[32];
+  const int tb = (int)blockIdx.x;
+  uint32_t before = 0, through = 0;
+  for (int j = threadIdx.x; j <= tb; j += blockDim.x) {
+    const uint32_t t = tile_sum[j];
+    through += t;
+    if (j < tb) before += t;
+  }
+  const uint32_t off = block_sum_u32(before, wsum);
+  if (tb == (int)gridDim.x - 1) {
+    const uint32_t tot = block_sum_u32(through, wsum);
+    if (threadIdx.x == 0) start[n] = tot;
+  }
+  const long long b = (long long)tb * kScanTile + (long long)threadIdx.x * kScanPer;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k)
     if (b + k < n) start[b + k] += off;
@@ -458,8 +460,9 @@ __global__ void __launch_bounds__(256) k_spread(
 }
 
 // A2 (FP32): spread with one private tile per warp and no atomics inside the
-// block. The warps of a CTA take the brick's atoms in chunks of 32: lane l
-// evaluates the 3P one-dimensional weights of the chunk's atom l (charge
+// block. Every warp of the brick's CTAs takes an equal contiguous share of
+// the brick's atoms, in chunks of 32: lane l evaluates the 3P
+// one-dimensional weights of the chunk's atom l (charge
 // folded into the z weights) and its tile offset into the warp's scratch;
 // then the chunk's atoms follow each other, every lane taking whole stencil
 // rows (b, c) of the atom. The row points of one atom are distinct, so plain
@@ -508,11 +511,13 @@ __global__ void __launch_bounds__(256) k_spread_warps(
       wy_at[k] = P + r % P;
       wz_at[k] = 2 * P + r / P;
     }
+    // the brick's atoms in equal contiguous shares, one per warp of its CTAs
     const int n_here = (int)(a_end - a_begin);
-    const int n_chunks = (n_here + 31) / 32;
-    for (int ch = split * nwarps + wid; ch < n_chunks; ch += nwarps * splits) {
-      const int a0 = ch * 32;
-      const int cnt = min(32, n_here - a0);
+    const int parts = nwarps * splits, part = split * nwarps + wid;
+    const int p_lo = (int)((long long)n_here * part / parts);
+    const int p_hi = (int)((long long)n_here * (part + 1) / parts);
+    for (int a0 = p_lo; a0 < p_hi; a0 += 32) {
+      const int cnt = min(32, p_hi - a0);
       bool sok = false;
       if (lane < cnt) {
         const uint4 at = atoms[a_begin + a0 + lane];

@@ -341,6 +341,21 @@ static esp_status choose_bricks(int n_f, int nc_max, double L, int P, const esp_
   return ESP_OK;
 }
 
+// 2^32 / L as m 2^e with m a 64-bit integer (top bit set), rounded down: L =
+// Lm 2^LE with Lm the 53-bit significand, so 2^32 / L = (2^k / Lm) 2^(32 - LE
+// - k); the quotient is an exact 128-bit integer division (the same on every
+// host).
+static void fixed_scale(double L, unsigned long long& m, int& e) {
+  int le = 0;
+  const double f = std::frexp(L, &le);                   // L = f 2^le, f in [0.5, 1)
+  const unsigned long long lm = (unsigned long long)std::ldexp(f, 53);   // exact
+  int k = 116;
+  if (lm == (1ull << 52)) k = 115;                      // 2^116 / 2^52 would need 65 bits
+  const unsigned __int128 q = ((unsigned __int128)1 << k) / lm;
+  m = (unsigned long long)q;
+  e = 32 - (le - 53) - k;
+}
+
 esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts& o, HostPlan& hp,
                           std::string& msg) {
   if (!(L > 0.0) || !std::isfinite(L)) { msg = "box edge must be positive and finite"; return ESP_ERR_INVALID_ARG; }
@@ -469,6 +484,7 @@ esp_status make_host_plan(double L, long long N, double tol, const esp_plan_opts
   d.w = L / n_c;
   d.fix_scale = L / 4294967296.0;
   d.to_fixed = 4294967296.0 / L;
+  fixed_scale(L, d.fix_m, d.fix_e);
   d.w32 = d.w / 4294967296.0;
   d.wf = (float)d.w;
   d.w32f = d.wf * 2.3283064365386962890625e-10f;
