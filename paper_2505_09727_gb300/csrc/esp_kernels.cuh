@@ -461,15 +461,15 @@ __global__ void __launch_bounds__(256) k_spread(
 
 // A2 (FP32): spread with one private tile per warp and no atomics inside the
 // block. Every warp of the brick's CTAs takes an equal contiguous share of
-// the brick's atoms, in chunks of 32: lane l evaluates the 3P
-// one-dimensional weights of the chunk's atom l (charge
-// folded into the z weights) and its tile offset into the warp's scratch;
-// then the chunk's atoms follow each other, every lane taking whole stencil
-// rows (b, c) of the atom. The row points of one atom are distinct, so plain
-// read-add-write needs no atomics, and the padded tile pitches put the rows
-// of one atom on distinct banks. The private tiles are summed point by point
-// and flushed to the grid with global atomics (bricks overlap by P - 1
-// points).
+// the brick's atoms, in chunks of 32: lane l evaluates the 3P one-dimensional
+// weights of the chunk's atom l (charge folded into the z weights) and its
+// tile offset into the warp's scratch; then the chunk's atoms follow each
+// other, every lane taking whole stencil rows (b, c) of the atom (the rows
+// beyond the last full pass of 32, when their points fit one pass, one point
+// per lane). The points of one atom are distinct, so plain read-add-write
+// needs no atomics, and the padded tile pitches put the rows of one atom on
+// distinct banks. The private tiles are summed point by point and flushed to
+// the grid with global atomics (bricks overlap by P - 1 points).
 template <int P>
 struct SpreadScratch {
   static constexpr int kW = 3 * P | 1;            // weights per atom; odd: lane stores hit distinct banks
@@ -502,7 +502,12 @@ __global__ void __launch_bounds__(256) k_spread_warps(
     float* wts = tiles + (size_t)nwarps * tile_stride + (size_t)wid * SpreadScratch<P>::kFloats;
     int* offs = reinterpret_cast<int*>(wts + 32 * kW);
     constexpr int kRows = P * P;
-    constexpr int kPass = (kRows + 31) / 32;
+    // rows left after the full passes of 32; when their points fit one pass
+    // (P = 6: 4 rows, 24 points) they go one point per lane instead of a
+    // row pass with few lanes busy
+    constexpr int kLeftRows = kRows % 32;
+    constexpr bool kPointTail = kRows > 32 && kLeftRows > 0 && kLeftRows * P <= 32;
+    constexpr int kPass = kPointTail ? kRows / 32 : (kRows + 31) / 32;
     int row_off[kPass], wy_at[kPass], wz_at[kPass];
 #pragma unroll
     for (int k = 0; k < kPass; ++k) {
@@ -510,6 +515,15 @@ __global__ void __launch_bounds__(256) k_spread_warps(
       row_off[k] = (r / P) * PZ + (r % P) * PY;
       wy_at[k] = P + r % P;
       wz_at[k] = 2 * P + r / P;
+    }
+    int pt_off = 0, pt_wx = 0, pt_wy = 0, pt_wz = 0;   // kPointTail: this lane's point
+    if constexpr (kPointTail) {
+      const int pnt = min(lane, kLeftRows * P - 1);
+      const int r = kRows - kLeftRows + pnt / P;
+      pt_wx = pnt % P;
+      pt_off = (r / P) * PZ + (r % P) * PY + pt_wx;
+      pt_wy = P + r % P;
+      pt_wz = 2 * P + r / P;
     }
     // the brick's atoms in equal contiguous shares, one per warp of its CTAs
     const int n_here = (int)(a_end - a_begin);
@@ -554,6 +568,13 @@ __global__ void __launch_bounds__(256) k_spread_warps(
             float* row = tile + off + row_off[k];
 #pragma unroll
             for (int a = 0; a < P; ++a) row[a] = fmaf(wyz, wx[a], row[a]);
+          }
+        }
+        if constexpr (kPointTail) {
+          // the same product and rounding as the row form
+          if (lane < kLeftRows * P) {
+            float* pt = tile + off + pt_off;
+            *pt = fmaf(wt[pt_wy] * wt[pt_wz], wt[pt_wx], *pt);
           }
         }
         __syncwarp();
