@@ -199,6 +199,23 @@ __host__ __device__ inline int wrap_near(int v, int n) {
   return v;
 }
 
+// Arguments of the per-system energy combination (the four energy parts,
+// optional virial): see launch_energy. ticket: a counter that is zero between
+// launches; when set, the finalize kernel's last CTA does the combination.
+struct EnergyArgs {
+  int nsys = 0;
+  const double* fourier = nullptr;
+  int n_fourier_blocks = 0;
+  const int* chunk_first = nullptr;
+  const double* consts = nullptr;
+  double* out = nullptr;
+  double* user_energy = nullptr;
+  const double* vpart = nullptr;
+  const double* vloc = nullptr;
+  double* vout = nullptr;
+  unsigned* ticket = nullptr;
+};
+
 // --------------------------------------------------------------- reductions
 __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

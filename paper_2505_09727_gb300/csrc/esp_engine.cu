@@ -128,6 +128,7 @@ struct esp_plan_s {
   void* d_near = nullptr;
   double* d_fourier = nullptr;
   double* d_partials = nullptr;
+  unsigned* d_ticket = nullptr;        // finalize's CTA ticket (zero between launches)
   double* d_consts = nullptr;
   double* d_eout = nullptr;      // per system: E, E_fourier, E_gather
   double* d_vpart = nullptr;     // virial: spectral partials [nsys][F][6]
@@ -384,6 +385,7 @@ esp_status build_buffers(esp_plan_s* p) {
   ESP_TRY(dev_alloc(p, &p->d_near, (size_t)N * L::res_bytes()));
   ESP_TRY(dev_alloc_t(p, &p->d_fourier, (size_t)p->F * n));
   ESP_TRY(dev_alloc_t(p, &p->d_partials, 2 * std::max(1, p->n_chunks)));
+  ESP_TRY(dev_alloc_t(p, &p->d_ticket, 1));
   ESP_TRY(dev_alloc_t(p, &p->d_consts, 2 * n));
   ESP_TRY(dev_alloc_t(p, &p->d_eout, 3 * n));
   p->virial = p->hps[0].info.virial != 0;
@@ -420,6 +422,7 @@ esp_status build_buffers(esp_plan_s* p) {
     ESP_CU(cudaMemcpyAsync(p->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, p->st));
   ESP_CU(cudaMemcpyAsync(p->d_tabs, tabs.data(), p->tab_total * rb, cudaMemcpyHostToDevice, p->st));
   ESP_CU(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->st));
+  ESP_CU(cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned), p->st));
   ESP_CU(cudaMemsetAsync(p->d_consts, 0, 2 * n * sizeof(double), p->st));
 
   const bool f32 = sizeof(real) == 4;
@@ -642,12 +645,22 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   rec(p, 8, st);
   // join and finish
   if (!serial) ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
+  // per-atom totals; the finalize kernel's last CTA combines the energies
+  espk::EnergyArgs ea;
+  ea.nsys = p->nsys;
+  ea.fourier = p->d_fourier;
+  ea.n_fourier_blocks = p->F;
+  ea.chunk_first = p->d_chunk_first;
+  ea.consts = p->d_consts;
+  ea.out = p->d_eout;
+  ea.user_energy = outE;
+  ea.vpart = p->d_vpart;
+  ea.vloc = p->d_vloc;
+  ea.vout = p->d_vout;
+  ea.ticket = p->d_ticket;
   ESP_CU(L::finalize(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_perm,
                      atom_outputs ? p->d_far : nullptr, p->d_near,
-                     outF, outU, out_double, p->d_partials, st));
-  ESP_CU(espk::launch_energy(p->d_desc, p->nsys, p->d_fourier, p->F, p->d_partials, p->n_chunks,
-                             p->d_chunk_first, p->d_consts, p->d_eout, outE, st, p->d_vpart, p->d_vloc,
-                             p->d_vout));
+                     outF, outU, out_double, p->d_partials, st, ea));
   p->computed = true;
   rec(p, 11, st);
   return ESP_OK;

@@ -33,8 +33,18 @@ cudaError_t launch_energy(const SysDesc* sys, int nsys, const double* fourier, i
                           const double* partials, int n_chunks, const int* chunk_first,
                           const double* consts, double* out, double* user_energy, cudaStream_t st,
                           const double* vpart, const double* vloc, double* vout) {
-  k_energy<<<nsys, 1024, 0, st>>>(sys, fourier, n_fourier_blocks, partials, n_chunks, chunk_first,
-                                 consts, out, user_energy, vpart, vloc, vout);
+  EnergyArgs ea;
+  ea.nsys = nsys;
+  ea.fourier = fourier;
+  ea.n_fourier_blocks = n_fourier_blocks;
+  ea.chunk_first = chunk_first;
+  ea.consts = consts;
+  ea.out = out;
+  ea.user_energy = user_energy;
+  ea.vpart = vpart;
+  ea.vloc = vloc;
+  ea.vout = vout;
+  k_energy<<<nsys, 1024, 0, st>>>(sys, ea, partials, n_chunks);
   return cudaGetLastError();
 }
 

@@ -225,18 +225,19 @@ template <>
 cudaError_t Launch<ESP_REAL>::finalize(const SysDesc* sys, const int2* chunks, int n_chunks,
                                        const void* atoms, const uint32_t* perm, const void* far,
                                        const void* nearres, void* forces, void* pot,
-                                       bool out_double, double* partials, cudaStream_t st) {
+                                       bool out_double, double* partials, cudaStream_t st,
+                                       const EnergyArgs& ea) {
   using A = typename Types<ESP_REAL>::atom;
   using R = typename Types<ESP_REAL>::res;
   if (n_chunks == 0) return cudaSuccess;
   if (out_double)
     k_finalize<ESP_REAL, double><<<n_chunks, kChunk, 0, st>>>(
         sys, chunks, (const A*)atoms, perm, (const R*)far, (const R*)nearres, (double*)forces,
-        (double*)pot, partials, n_chunks);
+        (double*)pot, partials, n_chunks, ea);
   else
     k_finalize<ESP_REAL, float><<<n_chunks, kChunk, 0, st>>>(
         sys, chunks, (const A*)atoms, perm, (const R*)far, (const R*)nearres, (float*)forces,
-        (float*)pot, partials, n_chunks);
+        (float*)pot, partials, n_chunks, ea);
   return cudaGetLastError();
 }
 

@@ -1107,7 +1107,39 @@ __global__ void __launch_bounds__(kChunk) k_near(
   nearres[i] = out;
 }
 
-// A8: per-atom totals in the caller's order and energy partials.
+// Exact float -> double by bit manipulation (the double has the float's
+// value: sign, exponent rebiased, significand widened; a subnormal float
+// becomes a normal double), without an FP64 conversion instruction (FP64
+// units are scarce on this GPU).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  unsigned long long r;
+  if (e == 0xffu) {
+    r = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);            // inf, NaN
+  } else if (e != 0u) {
+    r = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0u) {
+    r = sign;                                                                 // +-0
+  } else {
+    const int lz = __clz((int)m) - 8;                   // top bit of m moves to bit 23
+    const unsigned long long mm = (unsigned long long)((m << lz) & 0x7fffffu);
+    r = sign | ((unsigned long long)(897 - lz) << 52) | (mm << 29);
+  }
+  return __longlong_as_double((long long)r);
+}
+template <typename Out> __device__ __forceinline__ Out out_cast(float v) {
+  if constexpr (sizeof(Out) == 8) return f32_to_f64(v);
+  else return (Out)v;
+}
+
+static __device__ void energy_of_system(int s, const SysDesc* __restrict__ sys, const EnergyArgs& ea,
+                                        const double* __restrict__ partials, int n_chunks, double* red);
+
+// A8: per-atom totals in the caller's order and energy partials; with
+// ea.ticket set, the last CTA to finish (a ticket taken after its partials
+// are written and fenced) also combines every system's energy.
 // partials layout: [near chunk partials][gather chunk partials].
 // (hi, lo) += (bh, bl) with the rounding error of hi + bh kept in lo
 // (Knuth's TwoSum; exact for FP32 round-to-nearest without reassociation).
@@ -1124,8 +1156,10 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
     const SysDesc* __restrict__ sys, const int2* __restrict__ chunks,
     const typename Types<real>::atom* __restrict__ atoms, const uint32_t* __restrict__ perm,
     const typename Types<real>::res* __restrict__ far, const typename Types<real>::res* __restrict__ nearres,
-    Out* __restrict__ forces, Out* __restrict__ pot, double* __restrict__ partials, int n_chunks) {
+    Out* __restrict__ forces, Out* __restrict__ pot, double* __restrict__ partials, int n_chunks,
+    const EnergyArgs ea) {
   __shared__ double red[32];
+  __shared__ unsigned last_cta;
   const int2 ch = chunks[blockIdx.x];
   const SysDesc& S = sys[ch.x];
   const int local = ch.y + threadIdx.x;
@@ -1143,11 +1177,11 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
       const uint32_t o = perm[i];
       const float pre = S.prefactor_f;
       if (forces) {
-        forces[3ll * o + 0] = (Out)(pre * fmaf(-q, f.y, nr.y));
-        forces[3ll * o + 1] = (Out)(pre * fmaf(-q, f.z, nr.z));
-        forces[3ll * o + 2] = (Out)(pre * fmaf(-q, f.w, nr.w));
+        forces[3ll * o + 0] = out_cast<Out>(pre * fmaf(-q, f.y, nr.y));
+        forces[3ll * o + 1] = out_cast<Out>(pre * fmaf(-q, f.z, nr.z));
+        forces[3ll * o + 2] = out_cast<Out>(pre * fmaf(-q, f.w, nr.w));
       }
-      if (pot) pot[o] = (Out)(pre * (fmaf(-q, S.self_coef_f, f.x + nr.x) + S.bg_shift_f));
+      if (pot) pot[o] = out_cast<Out>(pre * (fmaf(-q, S.self_coef_f, f.x + nr.x) + S.bg_shift_f));
       en_hi = 0.5f * q * nr.x;
       eg_hi = 0.5f * q * f.x;
     }
@@ -1171,8 +1205,7 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
       partials[blockIdx.x] = a;
       partials[n_chunks + blockIdx.x] = b;
     }
-    return;
-  }
+  } else {
   double en = 0.0, eg = 0.0;
   if (local < S.n_atoms) {
     const long long i = S.atom0 + local;
@@ -1197,6 +1230,19 @@ __global__ void __launch_bounds__(kChunk) k_finalize(
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = en;
     partials[n_chunks + blockIdx.x] = eg;
+  }
+  }
+  if (ea.ticket) {
+    if (threadIdx.x == 0) {
+      __threadfence();                               // this CTA's partials before its ticket
+      last_cta = atomicAdd(ea.ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (last_cta) {
+      __threadfence();
+      for (int sy = 0; sy < ea.nsys; ++sy) energy_of_system(sy, sys, ea, partials, n_chunks, red);
+      if (threadIdx.x == 0) *ea.ticket = 0u;         // ready for the next launch
+    }
   }
 }
 
@@ -1272,23 +1318,21 @@ __device__ inline void neumaier_add(double& s, double& c, double v) {
 
 // Per-system energy: E = prefactor (E_fourier + E_near + E_self + E_bg).
 // One block of 1024 threads per system. out[3 s + 0] = E, [1] = E_fourier, [2] = E_gather.
-static __global__ void __launch_bounds__(1024) k_energy(
-    const SysDesc* __restrict__ sys, const double* __restrict__ fourier, int n_fourier_blocks,
-    const double* __restrict__ partials, int n_chunks, const int* __restrict__ chunk_first,
-    const double* __restrict__ consts, double* __restrict__ out, double* __restrict__ user_energy,
-    const double* __restrict__ vpart, const double* __restrict__ vloc, double* __restrict__ vout) {
-  __shared__ double red[32];
-  const int s = blockIdx.x;
-  // a few plain FP64 additions per thread, then a pairwise tree over the
-  // block: the rounding error stays near log2(terms) ulp, and the FP64 work
-  // of this single block is kept small (FP64 is scarce on this GPU);
-  // the four parts are combined with compensation below
+// The energy of system s from the partials of the scale and finalize
+// kernels (and its virial), by the calling CTA: a few plain FP64 additions
+// per thread, then a pairwise tree over the CTA (the rounding error stays
+// near log2(terms) ulp, and the FP64 work is small: FP64 is scarce on this
+// GPU); the four parts are combined with compensation. The partials are
+// read through L2 (the finalize kernel's own CTAs may have just written
+// them).
+static __device__ void energy_of_system(int s, const SysDesc* __restrict__ sys, const EnergyArgs& ea,
+                                        const double* __restrict__ partials, int n_chunks, double* red) {
   double vs[3] = {0, 0, 0};
-  for (int j = threadIdx.x; j < n_fourier_blocks; j += blockDim.x)
-    vs[0] += fourier[(long long)s * n_fourier_blocks + j];
-  for (int j = chunk_first[s] + threadIdx.x; j < chunk_first[s + 1]; j += blockDim.x) {
-    vs[1] += partials[j];
-    vs[2] += partials[n_chunks + j];
+  for (int j = threadIdx.x; j < ea.n_fourier_blocks; j += blockDim.x)
+    vs[0] += ea.fourier[(long long)s * ea.n_fourier_blocks + j];
+  for (int j = ea.chunk_first[s] + threadIdx.x; j < ea.chunk_first[s + 1]; j += blockDim.x) {
+    vs[1] += __ldcg(partials + j);
+    vs[2] += __ldcg(partials + n_chunks + j);
   }
   double tot[3];
   for (int a = 0; a < 3; ++a) tot[a] = block_sum(vs[a], red);
@@ -1298,25 +1342,32 @@ static __global__ void __launch_bounds__(1024) k_energy(
     double acc = 0.0, cc = 0.0;
     neumaier_add(acc, cc, tot[0]);
     neumaier_add(acc, cc, tot[1]);
-    neumaier_add(acc, cc, consts[2 * s]);
-    neumaier_add(acc, cc, consts[2 * s + 1]);
+    neumaier_add(acc, cc, ea.consts[2 * s]);
+    neumaier_add(acc, cc, ea.consts[2 * s + 1]);
     const double e = pre * (acc + cc);
-    out[3 * s + 0] = e;
-    out[3 * s + 1] = pre * tot[0];
-    out[3 * s + 2] = pre * tot[2];
-    if (user_energy) user_energy[s] = e;
+    ea.out[3 * s + 0] = e;
+    ea.out[3 * s + 1] = pre * tot[0];
+    ea.out[3 * s + 2] = pre * tot[2];
+    if (ea.user_energy) ea.user_energy[s] = e;
   }
-  if (vout) {
+  if (ea.vout) {
     // virial: spectral partials, local sums, background energy on the diagonal
     for (int c = 0; c < 6; ++c) {
       double v = 0.0;
-      for (int j = threadIdx.x; j < n_fourier_blocks; j += blockDim.x)
-        v += vpart[((long long)s * n_fourier_blocks + j) * 6 + c];
+      for (int j = threadIdx.x; j < ea.n_fourier_blocks; j += blockDim.x)
+        v += ea.vpart[((long long)s * ea.n_fourier_blocks + j) * 6 + c];
       v = block_sum(v, red);
       if (threadIdx.x == 0)
-        vout[6 * s + c] = sys[s].prefactor * (v + vloc[6 * s + c] + (c < 3 ? consts[2 * s + 1] : 0.0));
+        ea.vout[6 * s + c] = sys[s].prefactor * (v + ea.vloc[6 * s + c] + (c < 3 ? ea.consts[2 * s + 1] : 0.0));
     }
   }
+}
+
+// One CTA per system.
+static __global__ void __launch_bounds__(1024) k_energy(const SysDesc* __restrict__ sys, const EnergyArgs ea,
+                                                        const double* __restrict__ partials, int n_chunks) {
+  __shared__ double red[32];
+  energy_of_system(blockIdx.x, sys, ea, partials, n_chunks, red);
 }
 
 }  // namespace espk

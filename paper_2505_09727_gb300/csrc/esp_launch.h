@@ -46,10 +46,11 @@ struct Launch {
                                    uint32_t* ccount, uint32_t* cstart, uint32_t* ctiles, int2* cmap,
                                    int2* catoms, long long cmap_cap, bool half, long long n_atoms, int stage,
                                    int* err, cudaStream_t st, double* vloc = nullptr, bool tri = false);
+  // ea.ticket set: the last CTA also combines the energies (no launch_energy)
   static cudaError_t finalize(const SysDesc* sys, const int2* chunks, int n_chunks, const void* atoms,
                               const uint32_t* perm, const void* far, const void* nearres,
                               void* forces, void* pot, bool out_double, double* partials,
-                              cudaStream_t st);
+                              cudaStream_t st, const EnergyArgs& ea = EnergyArgs{});
   static cudaError_t convert_charges(const void* src, bool src_double, real* dst, long long n,
                                      cudaStream_t st);
   // Exclusions of one system: inv[perm[s]] = s, then every pair (caller
