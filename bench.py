@@ -441,7 +441,7 @@ def run_gpu(args, world, rank, local):
                                                    kernel=esp.ESP_KERNEL_GAUSS, window=esp.ESP_WINDOW_BSPLINE)
         extras["batched"] = batched(args, local, stream, flush)
         extras["served"] = served(args, local)
-        extras["large"] = large(args, local, stream, flush)
+        extras["large"] = large(args, local, stream, flush, peaks_gpu)
         # a triclinic cell: the same water density in a truncated
         # octahedron; last, and guarded, so that it cannot cost the lines above
         try:
@@ -507,9 +507,10 @@ def time_steps(step, stream, steps: int, flush) -> list:
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
-def single_variant(args, local, stream, flush, s, tolerance=None, ref=None, **opts):
+def single_variant(args, local, stream, flush, s, tolerance=None, ref=None, peaks_gpu=None, **opts):
     """atoms/s of the single-system path with other plan options (and the
-    error of its last step against `ref`)."""
+    error of its last step against `ref`); with peaks_gpu, also its
+    serialised phase times and every phase against the measured peaks."""
     import torch
     from paper_2505_09727_gb300 import esp
     dev = torch.device("cuda", local)
@@ -527,11 +528,27 @@ def single_variant(args, local, stream, flush, s, tolerance=None, ref=None, **op
     for _ in range(3):
         step()
     ms = time_steps(step, stream, max(3, min(args.steps, 20)), flush)
+    phases = None
+    if peaks_gpu is not None:
+        # second pass: phases serialised and bracketed by CUDA events
+        esp.esp_set_timing(h, 2)
+        phases = {k: 0.0 for k in esp.PHASES}
+        n_ph = max(3, min(args.steps, 10))
+        for _ in range(n_ph):
+            flush.zero_()
+            step()
+            for k, v in esp.esp_phase_times(h).items():
+                phases[k] += v / n_ph
+        torch.cuda.synchronize(dev)
+        esp.esp_set_timing(h, 0)
     esp.esp_destroy(h)
     t = statistics.median(ms)
     out = {"value": s.n / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "n_f": info["n_f"], "P": info["P"],
            "window": ("pswf", "bspline")[info["window"]], "diff": ("ad", "ik")[info["diff"]],
            "tolerance": tol, "steps": len(ms)}
+    if phases is not None:
+        out["phases_ms"] = {k: round(v, 5) for k, v in phases.items()}
+        out["phase_roofline"] = phase_rooflines(phases, info, s.n, s.L, peaks_gpu)
     if ref is not None:
         out["delta"] = stated_error(f.cpu().numpy(), float(e.cpu()[0]), ref, tol)
     return out
@@ -630,13 +647,16 @@ LARGE = dict(workload="spce_water_1e6_molecules", molecules=1_000_000, atoms=3_0
              r_c_nm=1.0, tolerance=1e-5, seed=2505)
 
 
-def large(args, local, stream, flush):
+def large(args, local, stream, flush, peaks_gpu=None):
     """3e6-atom water box at 1e-5: PSWF split against the Gaussian split on
-    the same machinery (the grid ratio is the method's point)."""
+    the same machinery (the grid ratio is the method's point); the PSWF
+    solve's phases against the measured peaks (n_f = 144, P = 8: the grid
+    is 12 MB, so the spread and gather tiles come from L2 and HBM)."""
     from paper_2505_09727_gb300 import inputs
     s = inputs.spce_water(LARGE["molecules"], seed=LARGE["seed"])
     ref = reference_solve(s, local, stream)
-    pswf = single_variant(args, local, stream, flush, s, tolerance=LARGE["tolerance"], ref=ref)
+    pswf = single_variant(args, local, stream, flush, s, tolerance=LARGE["tolerance"], ref=ref,
+                          peaks_gpu=peaks_gpu)
     gauss = single_variant(args, local, stream, flush, s, tolerance=LARGE["tolerance"], ref=ref, kernel=1)
     return {"value": pswf["value"], "unit": UNIT, "pswf": pswf, "gaussian": gauss,
             "grid_points_ratio": (gauss["n_f"] / pswf["n_f"]) ** 3, "speedup_vs_gaussian": pswf["value"] / gauss["value"],

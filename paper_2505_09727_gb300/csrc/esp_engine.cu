@@ -645,7 +645,8 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   rec(p, 8, st);
   // join and finish
   if (!serial) ESP_CU(cudaStreamWaitEvent(st, p->ev_join, 0));
-  // per-atom totals; the finalize kernel's last CTA combines the energies
+  // per-atom totals; for one or two systems the finalize kernel's last CTA
+  // combines the energies (one launch less), for more a CTA per system does
   espk::EnergyArgs ea;
   ea.nsys = p->nsys;
   ea.fourier = p->d_fourier;
@@ -657,10 +658,15 @@ esp_status launch_compute(esp_plan_s* p, void* outF, void* outU, bool out_double
   ea.vpart = p->d_vpart;
   ea.vloc = p->d_vloc;
   ea.vout = p->d_vout;
-  ea.ticket = p->d_ticket;
+  const bool fused_energy = p->nsys <= 2;
+  ea.ticket = fused_energy ? p->d_ticket : nullptr;
   ESP_CU(L::finalize(p->d_desc, p->d_chunks, p->n_chunks, p->d_atoms, p->d_perm,
                      atom_outputs ? p->d_far : nullptr, p->d_near,
                      outF, outU, out_double, p->d_partials, st, ea));
+  if (!fused_energy)
+    ESP_CU(espk::launch_energy(p->d_desc, p->nsys, p->d_fourier, p->F, p->d_partials, p->n_chunks,
+                               p->d_chunk_first, p->d_consts, p->d_eout, outE, st, p->d_vpart, p->d_vloc,
+                               p->d_vout));
   p->computed = true;
   rec(p, 11, st);
   return ESP_OK;
