@@ -216,6 +216,28 @@ struct EnergyArgs {
   unsigned* ticket = nullptr;
 };
 
+// Exact float -> double by bit manipulation (the double has the float's
+// value: sign, exponent rebiased, significand widened; a subnormal float
+// becomes a normal double), without an FP64 conversion instruction (FP64
+// units are scarce on this GPU).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  unsigned long long r;
+  if (e == 0xffu) {
+    r = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);            // inf, NaN
+  } else if (e != 0u) {
+    r = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0u) {
+    r = sign;                                                                 // +-0
+  } else {
+    const int lz = __clz((int)m) - 8;                   // top bit of m moves to bit 23
+    const unsigned long long mm = (unsigned long long)((m << lz) & 0x7fffffu);
+    r = sign | ((unsigned long long)(897 - lz) << 52) | (mm << 29);
+  }
+  return __longlong_as_double((long long)r);
+}
 // --------------------------------------------------------------- reductions
 __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -30,7 +30,10 @@ struct esp_md_s {
   bool have_forces = false;
   double* d_x = nullptr;
   double* d_v = nullptr;
-  double* d_f = nullptr;
+  double* d_f = nullptr;           // forces of the solve (Coulomb)
+  double* d_f2 = nullptr;          // bonded and Lennard-Jones forces
+  cudaStream_t st3 = nullptr;      // the bonded and Lennard-Jones terms, beside the solve
+  cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
   double* d_e = nullptr;           // energies [(capacity) x 4]
   double* d_ecur = nullptr;        // energies of the step in progress (Coulomb, bonded, LJ, kinetic)
   int* d_row = nullptr;            // next row of d_e the step writes
@@ -62,6 +65,8 @@ esp_status md_fail(esp_status s, const std::string& msg) {
 
 struct MdConst {
   double dt, k_bond, r0, k_angle, theta0, sigma2, eps4, rc2, shift, inv_mO, inv_mH, L, inv_L;
+  double mO, mH;                                              // masses (kinetic energy)
+  float k_bond_f, r0_f, k_angle_f, theta0_f, L_f, inv_L_f;   // FP32 copies (FP32 bonded terms)
   int n_mol, nc;
 };
 
@@ -86,33 +91,49 @@ __device__ void block_add(double v, double* out) {
   }
 }
 
+// The FP32 sum of v over the block added to *out with one FP64 atomic.
+__device__ void block_add_f(float v, double* out) {
+  __shared__ float redf[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) redf[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? redf[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(out, espk::f32_to_f64(v));
+  }
+}
+
 __device__ __forceinline__ double inv_mass(const MdConst& C, long long i) { return i % 3 == 0 ? C.inv_mO : C.inv_mH; }
 
-// v += dt F / 2m; r += dt v
+// v += dt F / 2m; r += dt v (F = f + f2)
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const double* __restrict__ f,
-                             MdConst C, long long n) {
+                             const double* __restrict__ f2, MdConst C, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double h = 0.5 * C.dt * inv_mass(C, i);
   for (int a = 0; a < 3; ++a) {
-    const double vv = v[3 * i + a] + h * f[3 * i + a];
+    const double vv = v[3 * i + a] + h * (f[3 * i + a] + f2[3 * i + a]);
     v[3 * i + a] = vv;
     x[3 * i + a] += C.dt * vv;
   }
 }
 
-// v += dt F / 2m (scale 1) or nothing (scale 0); the kinetic energy added to *ek
-__global__ void k_kick(double* __restrict__ v, const double* __restrict__ f, MdConst C, long long n, double scale,
-                       double* __restrict__ ek) {
+// v += dt F / 2m (scale 1) or nothing (scale 0), F = f + f2; the kinetic
+// energy added to *ek
+__global__ void k_kick(double* __restrict__ v, const double* __restrict__ f, const double* __restrict__ f2,
+                       MdConst C, long long n, double scale, double* __restrict__ ek) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < n) {
-    const double im = inv_mass(C, i);
+    const bool is_o = i % 3 == 0;
+    const double im = is_o ? C.inv_mO : C.inv_mH, mass = is_o ? C.mO : C.mH;
     const double h = 0.5 * C.dt * im * scale;
     for (int a = 0; a < 3; ++a) {
-      const double vv = v[3 * i + a] + h * f[3 * i + a];
+      const double vv = v[3 * i + a] + h * (f[3 * i + a] + f2[3 * i + a]);
       v[3 * i + a] = vv;
-      e += 0.5 * vv * vv / im;
+      e += 0.5 * mass * vv * vv;                       // (no FP64 division)
     }
   }
   block_add(e, ek);
@@ -130,42 +151,84 @@ __global__ void k_commit(double* __restrict__ ecur, double* __restrict__ e, int*
   }
 }
 
-// Bonds and angle of one molecule per thread, added to f; energy to *eb.
+// Bonds and angle of one molecule per thread, stored into f (the first
+// writer of the step's bonded and Lennard-Jones forces); energy to *eb.
+// F32 (FP32 plans): the O-H differences in FP64, the rest in FP32 (FP64
+// units are scarce on this GPU; the FP32 Coulomb forces set the precision of
+// such a step).
+template <bool F32>
 __global__ void k_bonded(const double* __restrict__ x, double* __restrict__ f, MdConst C, double* __restrict__ eb) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0;
-  if (m < C.n_mol) {
-    const double* o = x + 9ll * m;
-    double d[2][3], r[2];
-    double fh[2][3];
-    for (int k = 0; k < 2; ++k) {
-      for (int a = 0; a < 3; ++a) d[k][a] = wrap_d(o[3 * (k + 1) + a] - o[a], C.L, C.inv_L);
-      r[k] = sqrt(d[k][0] * d[k][0] + d[k][1] * d[k][1] + d[k][2] * d[k][2]);
-      const double dr = r[k] - C.r0;
-      e += 0.5 * C.k_bond * dr * dr;
-      for (int a = 0; a < 3; ++a) fh[k][a] = -C.k_bond * dr / r[k] * d[k][a];
+  if constexpr (F32) {
+    float e = 0.f;
+    if (m < C.n_mol) {
+      const double* o = x + 9ll * m;
+      float d[2][3], r[2], fh[2][3];
+      for (int k = 0; k < 2; ++k) {
+        for (int a = 0; a < 3; ++a) {
+          const float t = (float)(o[3 * (k + 1) + a] - o[a]);
+          d[k][a] = t - C.L_f * rintf(t * C.inv_L_f);
+        }
+        r[k] = sqrtf(d[k][0] * d[k][0] + d[k][1] * d[k][1] + d[k][2] * d[k][2]);
+        const float dr = r[k] - C.r0_f;
+        e += 0.5f * C.k_bond_f * dr * dr;
+        for (int a = 0; a < 3; ++a) fh[k][a] = -C.k_bond_f * dr / r[k] * d[k][a];
+      }
+      float c = (d[0][0] * d[1][0] + d[0][1] * d[1][1] + d[0][2] * d[1][2]) / (r[0] * r[1]);
+      c = fminf(1.f, fmaxf(-1.f, c));
+      const float th = acosf(c);
+      const float sn = sqrtf(fmaxf(1.f - c * c, 1e-30f));
+      const float de = C.k_angle_f * (th - C.theta0_f);
+      e += 0.5f * C.k_angle_f * (th - C.theta0_f) * (th - C.theta0_f);
+      for (int a = 0; a < 3; ++a) {
+        const float dtu = -(d[1][a] / (r[0] * r[1]) - c / (r[0] * r[0]) * d[0][a]) / sn;
+        const float dtv = -(d[0][a] / (r[0] * r[1]) - c / (r[1] * r[1]) * d[1][a]) / sn;
+        fh[0][a] -= de * dtu;
+        fh[1][a] -= de * dtv;
+      }
+      double* fo = f + 9ll * m;
+      for (int a = 0; a < 3; ++a) {
+        fo[3 + a] = espk::f32_to_f64(fh[0][a]);
+        fo[6 + a] = espk::f32_to_f64(fh[1][a]);
+        fo[a] = espk::f32_to_f64(-(fh[0][a] + fh[1][a]));
+      }
     }
-    double c = (d[0][0] * d[1][0] + d[0][1] * d[1][1] + d[0][2] * d[1][2]) / (r[0] * r[1]);
-    c = fmin(1.0, fmax(-1.0, c));
-    const double th = acos(c);
-    const double s = sqrt(fmax(1.0 - c * c, 1e-300));
-    const double de = C.k_angle * (th - C.theta0);
-    e += 0.5 * C.k_angle * (th - C.theta0) * (th - C.theta0);
-    // d theta / d u = -(v / (|u||v|) - cos u / |u|^2) / sin theta, likewise for v
-    for (int a = 0; a < 3; ++a) {
-      const double dtu = -(d[1][a] / (r[0] * r[1]) - c / (r[0] * r[0]) * d[0][a]) / s;
-      const double dtv = -(d[0][a] / (r[0] * r[1]) - c / (r[1] * r[1]) * d[1][a]) / s;
-      fh[0][a] -= de * dtu;
-      fh[1][a] -= de * dtv;
+    block_add_f(e, eb);
+  } else {
+    double e = 0.0;
+    if (m < C.n_mol) {
+      const double* o = x + 9ll * m;
+      double d[2][3], r[2];
+      double fh[2][3];
+      for (int k = 0; k < 2; ++k) {
+        for (int a = 0; a < 3; ++a) d[k][a] = wrap_d(o[3 * (k + 1) + a] - o[a], C.L, C.inv_L);
+        r[k] = sqrt(d[k][0] * d[k][0] + d[k][1] * d[k][1] + d[k][2] * d[k][2]);
+        const double dr = r[k] - C.r0;
+        e += 0.5 * C.k_bond * dr * dr;
+        for (int a = 0; a < 3; ++a) fh[k][a] = -C.k_bond * dr / r[k] * d[k][a];
+      }
+      double c = (d[0][0] * d[1][0] + d[0][1] * d[1][1] + d[0][2] * d[1][2]) / (r[0] * r[1]);
+      c = fmin(1.0, fmax(-1.0, c));
+      const double th = acos(c);
+      const double sn = sqrt(fmax(1.0 - c * c, 1e-300));
+      const double de = C.k_angle * (th - C.theta0);
+      e += 0.5 * C.k_angle * (th - C.theta0) * (th - C.theta0);
+      // d theta / d u = -(v / (|u||v|) - cos u / |u|^2) / sin theta, likewise for v
+      for (int a = 0; a < 3; ++a) {
+        const double dtu = -(d[1][a] / (r[0] * r[1]) - c / (r[0] * r[0]) * d[0][a]) / sn;
+        const double dtv = -(d[0][a] / (r[0] * r[1]) - c / (r[1] * r[1]) * d[1][a]) / sn;
+        fh[0][a] -= de * dtu;
+        fh[1][a] -= de * dtv;
+      }
+      double* fo = f + 9ll * m;
+      for (int a = 0; a < 3; ++a) {
+        fo[3 + a] = fh[0][a];
+        fo[6 + a] = fh[1][a];
+        fo[a] = -(fh[0][a] + fh[1][a]);
+      }
     }
-    double* fo = f + 9ll * m;
-    for (int a = 0; a < 3; ++a) {
-      fo[3 + a] += fh[0][a];
-      fo[6 + a] += fh[1][a];
-      fo[a] -= fh[0][a] + fh[1][a];
-    }
+    block_add(e, eb);
   }
-  block_add(e, eb);
 }
 
 __device__ __forceinline__ int lj_cell_axis(double s, int nc) {
@@ -229,9 +292,11 @@ template <typename real> struct LjC {
         shift((real)C.shift) {}
 };
 
+// One candidate pair; the O itself (self) and pairs outside (0, r_c)
+// contribute nothing.
 template <typename real, bool CELLS>
 __device__ __forceinline__ void lj_pair(const real* xi, const OPos<real>& pj, const real* sh, const LjC<real>& C,
-                                        real* fi, real& e) {
+                                        bool self, real* fi, real& e) {
   const real xj[3] = {pj.x, pj.y, pj.z};
   real d[3];
   for (int a = 0; a < 3; ++a) {
@@ -240,7 +305,7 @@ __device__ __forceinline__ void lj_pair(const real* xi, const OPos<real>& pj, co
     else d[a] = t - C.L * rint(t * C.inv_L);
   }
   const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  if (r2 >= C.rc2 || r2 <= real(0)) return;
+  if (self || r2 >= C.rc2 || r2 <= real(0)) return;
   const real inv_r2 = real(1) / r2;
   const real s2 = C.sigma2 * inv_r2, s6 = s2 * s2 * s2;
   e += real(0.5) * (C.eps4 * (s6 * s6 - s6) - C.shift);   // every pair is met from both sides
@@ -276,8 +341,7 @@ __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restri
       // the three z-neighbouring cells of a column (nx, ny) are consecutive in
       // cell order: one range, or two where the column wraps in z
       auto sweep = [&](uint32_t b, uint32_t e2, const real* sh) {
-        for (uint32_t s = b + lane; s < e2; s += 32)
-          if (s != (uint32_t)w) lj_pair<real, true>(xi, op[s], sh, LC, fi, e);
+        for (uint32_t s = b + lane; s < e2; s += 32) lj_pair<real, true>(xi, op[s], sh, LC, s == (uint32_t)w, fi, e);
       };
       for (int ox = -1; ox <= 1; ++ox)
         for (int oy = -1; oy <= 1; ++oy) {
@@ -297,8 +361,7 @@ __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restri
           }
         }
     } else {
-      for (int s = lane; s < C.n_mol; s += 32)
-        if (s != w) lj_pair<real, false>(xi, op[s], nullptr, LC, fi, e);
+      for (int s = lane; s < C.n_mol; s += 32) lj_pair<real, false>(xi, op[s], nullptr, LC, s == w, fi, e);
     }
     for (int o = 16; o > 0; o >>= 1) {
       fi[0] += __shfl_xor_sync(0xffffffffu, fi[0], o);
@@ -307,12 +370,14 @@ __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restri
     }
     if (lane == 0) {
       double* fo = f + 9ll * m;
-      fo[0] += (double)fi[0];
-      fo[1] += (double)fi[1];
-      fo[2] += (double)fi[2];
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (sizeof(real) == 4) fo[c] += espk::f32_to_f64(fi[c]);
+        else fo[c] += (double)fi[c];
+      }
     }
   }
-  block_add((double)e, el);
+  if constexpr (sizeof(real) == 4) block_add_f(e, el);
+  else block_add(e, el);
 }
 
 MdConst make_const(const esp_md_s* md) {
@@ -330,24 +395,39 @@ MdConst make_const(const esp_md_s* md) {
   C.shift = 4.0 * p.lj_epsilon * (sr6 * sr6 - sr6);
   C.inv_mO = 1.0 / p.mass_O;
   C.inv_mH = 1.0 / p.mass_H;
+  C.mO = p.mass_O;
+  C.mH = p.mass_H;
   C.L = md->L;
   C.inv_L = 1.0 / md->L;
   C.n_mol = md->n_mol;
   C.nc = md->nc;
+  C.k_bond_f = (float)C.k_bond;
+  C.r0_f = (float)C.r0;
+  C.k_angle_f = (float)C.k_angle;
+  C.theta0_f = (float)C.theta0;
+  C.L_f = (float)C.L;
+  C.inv_L_f = (float)C.inv_L;
   return C;
 }
 
 int blocks_of(long long n) { return (int)std::max<long long>(1, (n + 255) / 256); }
 
-// Forces and potential energies at the current positions into d_f and
-// e[0..2] (Coulomb, bonded, Lennard-Jones; e zeroed by the caller).
-// Forces at the current positions; energies to e[0] (Coulomb, written), e[1]
-// (bonded) and e[2] (Lennard-Jones), both added.
-esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st) {
+// Forces at the current positions: the solve's into d_f, the bonded and
+// Lennard-Jones terms into d_f2 on a second stream while the solve runs;
+// energies to e[0] (Coulomb, written), e[1] (bonded) and e[2]
+// (Lennard-Jones), both added. st waits for both.
+esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st_main) {
+  MD_CU(cudaEventRecord(md->ev_fork3, st_main));
+  MD_CU(cudaStreamWaitEvent(md->st3, md->ev_fork3, 0));
   esp_status s = esp_step(md->plan, md->d_x, e, md->d_f, nullptr, ESP_DEVICE);
   if (s != ESP_OK) return s;
+  cudaStream_t st = md->st3;
   const MdConst C = make_const(md);
-  k_bonded<<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_f, C, e + 1);
+  // the bonded kernel stores every atom's d_f2; Lennard-Jones adds to the O's
+  if (md->fp32)
+    k_bonded<true><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_f2, C, e + 1);
+  else
+    k_bonded<false><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_f2, C, e + 1);
   if (md->nc >= 3) {
     const long long ncell = (long long)md->nc * md->nc * md->nc;
     MD_CU(cudaMemsetAsync(md->d_count, 0, ncell * sizeof(uint32_t), st));
@@ -361,13 +441,15 @@ esp_status md_forces(esp_md_s* md, double* e, cudaStream_t st) {
   if (md->fp32) {
     auto* op = reinterpret_cast<OPos<float>*>(md->d_opos);
     k_lj_pack<float><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, C, op);
-    k_lj<float><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f, e + 2);
+    k_lj<float><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f2, e + 2);
   } else {
     auto* op = reinterpret_cast<OPos<double>*>(md->d_opos);
     k_lj_pack<double><<<blocks_of(md->n_mol), 256, 0, st>>>(md->d_x, md->d_sorted, use_cells, md->n_mol, C, op);
-    k_lj<double><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f, e + 2);
+    k_lj<double><<<wb, 256, 0, st>>>(op, md->d_cell, md->d_start, C, md->d_f2, e + 2);
   }
   MD_CU(cudaGetLastError());
+  MD_CU(cudaEventRecord(md->ev_join3, st));
+  MD_CU(cudaStreamWaitEvent(st_main, md->ev_join3, 0));
   return ESP_OK;
 }
 
@@ -387,6 +469,15 @@ void md_release(esp_md_s* md) {
   md->allocs.clear();
 }
 
+void md_streams_release(esp_md_s* md) {
+  if (md->st3) cudaStreamSynchronize(md->st3);
+  if (md->ev_fork3) cudaEventDestroy(md->ev_fork3);
+  if (md->ev_join3) cudaEventDestroy(md->ev_join3);
+  if (md->st3) cudaStreamDestroy(md->st3);
+  md->ev_fork3 = md->ev_join3 = nullptr;
+  md->st3 = nullptr;
+}
+
 struct MdDevice {
   int prev = 0;
   explicit MdDevice(int dev) {
@@ -400,10 +491,10 @@ struct MdDevice {
 esp_status md_step(esp_md_s* md, cudaStream_t st) {
   const MdConst C = make_const(md);
   const int nb = blocks_of(md->n_atoms);
-  k_kick_drift<<<nb, 256, 0, st>>>(md->d_x, md->d_v, md->d_f, C, md->n_atoms);
+  k_kick_drift<<<nb, 256, 0, st>>>(md->d_x, md->d_v, md->d_f, md->d_f2, C, md->n_atoms);
   esp_status s = md_forces(md, md->d_ecur, st);
   if (s != ESP_OK) return s;
-  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 1.0, md->d_ecur + 3);
+  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, md->d_f2, C, md->n_atoms, 1.0, md->d_ecur + 3);
   k_commit<<<1, 32, 0, st>>>(md->d_ecur, md->d_e, md->d_row, md->e_cap);
   MD_CU(cudaGetLastError());
   return ESP_OK;
@@ -484,7 +575,8 @@ esp_status esp_md_create(esp_plan_t plan, const esp_md_params* params, const dou
   const size_t n3 = (size_t)md->n_atoms * 3;
   esp_status st = ESP_OK;
   if ((st = md_alloc(md, &md->d_x, n3)) != ESP_OK || (st = md_alloc(md, &md->d_v, n3)) != ESP_OK ||
-      (st = md_alloc(md, &md->d_f, n3)) != ESP_OK || (st = md_alloc(md, &md->d_ecur, 4)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_f, n3)) != ESP_OK || (st = md_alloc(md, &md->d_f2, n3)) != ESP_OK ||
+      (st = md_alloc(md, &md->d_ecur, 4)) != ESP_OK ||
       (st = md_alloc(md, &md->d_row, 1)) != ESP_OK ||
       (st = md_alloc(md, &md->d_cell, (size_t)md->n_mol)) != ESP_OK ||
       (st = md_alloc(md, &md->d_sorted, (size_t)md->n_mol)) != ESP_OK ||
@@ -523,6 +615,15 @@ esp_status esp_md_create(esp_plan_t plan, const esp_md_params* params, const dou
     delete md;
     return md_fail(ESP_ERR_CUDA, "copy of the initial state failed");
   }
+  if (cudaStreamCreateWithFlags(&md->st3, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&md->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&md->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    md_streams_release(md);
+    md_release(md);
+    delete md;
+    return md_fail(ESP_ERR_CUDA, "stream/event creation failed");
+  }
   *out = md;
   return ESP_OK;
 }
@@ -555,7 +656,7 @@ esp_status esp_md_run(esp_md_t md, int n_steps, double* energies) {
   } else {
     MD_CU(cudaMemcpyAsync(md->d_ecur, md->e_now, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
   }
-  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, C, md->n_atoms, 0.0, md->d_ecur + 3);
+  k_kick<<<nb, 256, 0, st>>>(md->d_v, md->d_f, md->d_f2, C, md->n_atoms, 0.0, md->d_ecur + 3);
   k_commit<<<1, 32, 0, st>>>(md->d_ecur, md->d_e, md->d_row, md->e_cap);
   MD_CU(cudaGetLastError());
   if (n_steps > 0) {
@@ -589,6 +690,7 @@ esp_status esp_md_destroy(esp_md_t md) {
     cudaStream_t st = espe::plan_stream(md->plan);
     if (st) cudaStreamSynchronize(st);
     drop_graph(md);
+    md_streams_release(md);
     md_release(md);
     // the intramolecular exclusions belong to the MD state, not to the plan
     esp_set_exclusions(md->plan, nullptr, 0);
