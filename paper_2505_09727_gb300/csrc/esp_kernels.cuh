@@ -596,6 +596,14 @@ __global__ void __launch_bounds__(256) k_spread_warps(
   }
 }
 
+// Knuth's TwoSum: hi + lo += t with the rounding error of the sum kept in lo.
+__device__ __forceinline__ void acc_two_sum(float& hi, float& lo, float t) {
+  const float s = hi + t;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (t - bp);
+  hi = s;
+}
+
 // A4: influence scale fused with the spectral energy (Eq. pk). Grid-stride
 // over the half spectrum [kz][ky][kx], kx in [0, n_f/2]; blockIdx.y = system.
 template <typename real>
@@ -611,13 +619,11 @@ __global__ void __launch_bounds__(256) k_scale(
   const real* G = tabs + S.tab0;
   const real* W = G + S.gsize;
   const real* H = W + (half + 1);                 // virial table: p'_k over the window factors
-  double e = 0.0;
+  double e = 0.0;                                 // FP64 plans
+  float e_hi = 0.f, e_lo = 0.f;                   // FP32 plans: error-free (hi, lo) sum
   double vir[6] = {0, 0, 0, 0, 0, 0};             // xx, yy, zz, xy, xz, yz
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(idx % nh);
-    const long long r = idx / nh;
-    const int kyi = (int)(r % n), kzi = (int)(r / n);
+  // one mode; kx, kyi, kzi its half-spectrum indices
+  auto mode = [&](long long idx, int kx, int kyi, int kzi) {
     const int ky = kyi < half ? kyi : kyi - n;
     const int kz = kzi < half ? kzi : kzi - n;
     const int m = kx * kx + ky * ky + kz * kz;
@@ -625,9 +631,14 @@ __global__ void __launch_bounds__(256) k_scale(
     const long long gi = S.tri ? idx : (long long)m;
     const real p = __ldg(G + gi) * __ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz));
     typename Types<real>::cplx v = sp[idx];
-    const double wgt = (kx == 0 || kx == half) ? 1.0 : 2.0;
-    e += wgt * (double)p * ((double)v.x * v.x + (double)v.y * v.y);
+    const bool edge = kx == 0 || kx == half;
+    if constexpr (sizeof(real) == 4) {
+      acc_two_sum(e_hi, e_lo, (edge ? 1.f : 2.f) * p * fmaf(v.x, v.x, v.y * v.y));
+    } else {
+      e += (edge ? 1.0 : 2.0) * (double)p * ((double)v.x * v.x + (double)v.y * v.y);
+    }
     if (vpart && m > 0) {
+      const double wgt = edge ? 1.0 : 2.0;
       // virial of the mode: 1/2 |bh|^2 W W W [G delta + H k k^T / |k|^2]
       const double a = 0.5 * wgt * (double)(__ldg(W + kx) * __ldg(W + abs(ky)) * __ldg(W + abs(kz))) *
                        ((double)v.x * v.x + (double)v.y * v.y);
@@ -663,7 +674,23 @@ __global__ void __launch_bounds__(256) k_scale(
       o[spec_total] = make_cplx<real>(-v.y * sy, v.x * sy);
       o[2 * spec_total] = make_cplx<real>(-v.y * sz, v.x * sz);
     }
+  };
+  if (total < (1ll << 31)) {
+    // 32-bit index arithmetic (64-bit division is slow)
+    const uint32_t t32 = (uint32_t)total, unh = (uint32_t)nh, un = (uint32_t)n;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t32; idx += gridDim.x * blockDim.x) {
+      const uint32_t r = idx / unh;
+      const uint32_t kzi = r / un;
+      mode(idx, (int)(idx - r * unh), (int)(r - kzi * un), (int)kzi);
+    }
+  } else {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+      const long long r = idx / nh;
+      mode(idx, (int)(idx % nh), (int)(r % n), (int)(r / n));
+    }
   }
+  if constexpr (sizeof(real) == 4) e = f32_to_f64(e_hi) + f32_to_f64(e_lo);
   e = block_sum(e, red);
   if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * e;
   if (vpart) {
