@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
   static_assert(!(TRI && VIR), "no virial on a triclinic cell");
   constexpr int kClusterWarps = WARPS;
   __shared__ ClusterSmem<HALF> smem_all[kClusterWarps];
+  __shared__ int next_cluster;                      // the block's next cluster (offset from g_begin)
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -138,7 +139,17 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_near_cluster(
     }
   };
 
-  for (long long g = g_begin + wib; g < g_end; g += kClusterWarps) {
+  // the warps take the block's clusters in order from a shared counter, so
+  // a warp that meets cheap clusters takes more of them (no tail of one
+  // warp working while the others wait for the block to end)
+  if (threadIdx.x == 0) next_cluster = 0;
+  __syncthreads();
+  for (;;) {
+    int take = 0;
+    if (lane == 0) take = atomicAdd(&next_cluster, 1);
+    take = __shfl_sync(full, take, 0);
+    const long long g = g_begin + take;
+    if (g >= g_end) break;
     const int2 cm = cmap[g];
     if constexpr (VIR) {
       if (cm.x != vsys) {
