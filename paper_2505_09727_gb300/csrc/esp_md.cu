@@ -41,6 +41,7 @@ struct esp_md_s {
   cudaGraph_t graph = nullptr;     // one velocity-Verlet step, replayed n times
   cudaGraphExec_t gexec = nullptr;
   const double* graph_e = nullptr; // the d_e the graph was captured with
+  long long graph_cap = 0;         // and its row capacity (a reallocation may return the same address)
   double e_now[4] = {0, 0, 0, 0};  // energies at the current positions
   uint32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_tiles = nullptr, *d_cursor = nullptr,
            *d_sorted = nullptr;
@@ -338,26 +339,43 @@ __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restri
       const int cz = k % nc, cy = (k / nc) % nc, cx = k / (nc * nc);
       auto wrap = [&](int u) { return u < 0 ? u + nc : (u >= nc ? u - nc : u); };
       auto shift = [&](int u) { return u < 0 ? LC.L : (u >= nc ? -LC.L : real(0)); };
-      // the three z-neighbouring cells of a column (nx, ny) are consecutive in
-      // cell order: one range, or two where the column wraps in z
+      // the z-neighbouring cells of a column (nx, ny) are consecutive in cell
+      // order: one range, or two where the column wraps in z
       auto sweep = [&](uint32_t b, uint32_t e2, const real* sh) {
         for (uint32_t s = b + lane; s < e2; s += 32) lj_pair<real, true>(xi, op[s], sh, LC, s == (uint32_t)w, fi, e);
       };
+      // the O's place in its cell; a column whose xy gap from the O is >= the
+      // cutoff is skipped, and a column's z range keeps the cells the cutoff
+      // sphere reaches over that gap (a small margin keeps the cull
+      // conservative where the FP64 cell and the wrapped position disagree
+      // by a rounding)
+      const real cw = LC.L / (real)nc, margin = real(1e-4) * cw;
+      const real fx = xi[0] - (real)cx * cw, fy = xi[1] - (real)cy * cw, fz = xi[2] - (real)cz * cw;
+      auto gap = [&](int o, real f) {
+        const real g = o == 0 ? real(0) : (o < 0 ? f : cw - f);
+        return g > margin ? g - margin : real(0);
+      };
+      const real glo = gap(-1, fz), ghi = gap(1, fz);
       for (int ox = -1; ox <= 1; ++ox)
         for (int oy = -1; oy <= 1; ++oy) {
+          const real gx = gap(ox, fx), gy = gap(oy, fy);
+          const real h2 = LC.rc2 - gx * gx - gy * gy;
+          if (h2 <= real(0)) continue;
+          const int lo = glo * glo < h2 ? cz - 1 : cz;
+          const int hi = ghi * ghi < h2 ? cz + 1 : cz;
           const int ux = cx + ox, uy = cy + oy;
           const int col = (wrap(ux) * nc + wrap(uy)) * nc;
           real sh[3] = {shift(ux), shift(uy), real(0)};
-          if (cz == 0) {
-            sweep(start[col], start[col + 2], sh);                 // cells 0, 1
+          if (lo < 0) {
+            sweep(start[col], start[col + hi + 1], sh);            // cells 0 ... hi
             sh[2] = LC.L;
             sweep(start[col + nc - 1], start[col + nc], sh);       // cell nc - 1, one period down
-          } else if (cz == nc - 1) {
-            sweep(start[col + nc - 2], start[col + nc], sh);       // cells nc - 2, nc - 1
+          } else if (hi >= nc) {
+            sweep(start[col + lo], start[col + nc], sh);           // cells lo ... nc - 1
             sh[2] = -LC.L;
             sweep(start[col], start[col + 1], sh);                 // cell 0, one period up
           } else {
-            sweep(start[col + cz - 1], start[col + cz + 2], sh);   // cells cz - 1 ... cz + 1
+            sweep(start[col + lo], start[col + hi + 1], sh);       // cells lo ... hi
           }
         }
     } else {
@@ -506,12 +524,13 @@ void drop_graph(esp_md_s* md) {
   md->gexec = nullptr;
   md->graph = nullptr;
   md->graph_e = nullptr;
+  md->graph_cap = 0;
 }
 
 // The step as a CUDA graph on the plan's stream (captured once per energy
 // buffer; the solve inside is launched directly into the capture).
 esp_status md_graph(esp_md_s* md, cudaStream_t st) {
-  if (md->gexec && md->graph_e == md->d_e) return ESP_OK;
+  if (md->gexec && md->graph_e == md->d_e && md->graph_cap == md->e_cap) return ESP_OK;
   drop_graph(md);
   MD_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   esp_status s = md_step(md, st);
@@ -525,6 +544,7 @@ esp_status md_graph(esp_md_s* md, cudaStream_t st) {
   md->graph = g;
   MD_CU(cudaGraphInstantiate(&md->gexec, g, 0));
   md->graph_e = md->d_e;
+  md->graph_cap = md->e_cap;
   return ESP_OK;
 }
 

@@ -9,6 +9,7 @@
 * FP32 plans: the total energy stays within 2% of the kinetic energy over 40
   steps (the velocity-Verlet error of the flexible model at this step is a
   few tenths of a percent).
+* Consecutive runs of growing length fill every energy row.
 * Argument checks.
 Collected last (test_zz_*): the newest GPU path.
 """
@@ -67,6 +68,28 @@ def test_fp32_energy_is_conserved(esp):
     tot = e.sum(axis=1)
     assert np.all(np.isfinite(e))
     assert np.max(np.abs(tot - tot[0])) <= 0.02 * np.mean(e[:, 3])
+
+
+def test_consecutive_runs_fill_every_energy_row(esp):
+    """Runs of growing length on one MD state (each one reallocates the
+    energy rows, possibly at the same address): every row of every run is
+    written, and a run's first row carries the previous run's last one. A
+    step graph replayed with a smaller row capacity than the run's left the
+    last rows at zero."""
+    s = inputs.spce_water(300, seed=11)
+    v = inputs.water_velocities(300, 300.0, seed=11)
+    with esp.Plan(s.L, s.n, 1e-4, r_c=0.9, prefactor=esp.MD_PREFACTOR) as p:
+        p.set_charges(s.q)
+        with esp.MD(p.handle, s.pos, v, dt=5e-4, lj_cutoff=0.6) as sim:
+            prev = None
+            for n in (3, 5, 2, 8):
+                e = sim.run(n)
+                assert e.shape == (n + 1, 4)
+                # Coulomb, Lennard-Jones and kinetic energies are never zero here
+                assert np.all(e[:, 0] != 0.0) and np.all(e[:, 2] != 0.0) and np.all(e[:, 3] > 0.0), (n, e)
+                if prev is not None:
+                    assert np.array_equal(e[0, :3], prev[-1, :3])
+                prev = e
 
 
 def test_md_arguments(esp):
