@@ -4,8 +4,9 @@
 // shifted to zero there. Molecules are consecutive (O, H, H) triples of the
 // plan's atoms; positions, velocities and forces stay on the device in FP64,
 // caller order. One step: kick + drift, esp_step on the device positions
-// (sort and compute replayed as one graph), bonded and Lennard-Jones forces
-// added to the ESP forces, kick with the kinetic energy summed.
+// (sort and compute replayed as one graph) and, beside it on a second
+// stream, the bonded and Lennard-Jones forces into a second buffer, then the
+// kick on their sum with the kinetic energy summed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -318,8 +319,9 @@ __device__ __forceinline__ void lj_pair(const real* xi, const OPos<real>& pj, co
 
 // O-O Lennard-Jones, one warp per O (taken in cell order, so the warps of a
 // block read the same neighbouring cells): the lanes stride over the
-// candidates of the 27 neighbouring cells (cell edge >= cutoff), or of every
-// O when there are fewer than 3 cells per axis; sums over the warp.
+// candidates of the neighbouring cells (cell edge >= cutoff) that the cutoff
+// sphere reaches, or of every O when there are fewer than 3 cells per axis;
+// sums over the warp.
 template <typename real>
 __global__ void k_lj(const OPos<real>* __restrict__ op, const uint32_t* __restrict__ cell,
                      const uint32_t* __restrict__ start, MdConst C, double* __restrict__ f,
